@@ -1,0 +1,505 @@
+/*
+ * Plain FP64 CPU oracle of Cosm (Collective Switched Motion).
+ *
+ * TEST INFRASTRUCTURE. Only the tests, the smoke check and the CPU-baseline
+ * leg of the bench may load this library. It shares no code, header, table or
+ * helper with the CUDA path.
+ *
+ * It follows the paper's statement of the method step by step, in the
+ * paper's order, without blocking, fusion or reordering:
+ *   - Ising/Max-Cut form: eq. (1) and Appendix A (w_ij = -J_ij).
+ *   - Circular variables: x_i in [0, 360) degrees, held here in turns
+ *     (x_turn = x_deg / 360), modular updates (Section II-A).
+ *   - Pair update: eqs. (4)-(6), applied to the minimum angular difference
+ *     (Fig. 1 caption), with the biased sign of eq. (4).
+ *   - Sequential conflict-free search: eqs. (9)-(12), colours in order.
+ *   - Dual window twist: Section II-D and Alg. 1 (every DWTperiod sweeps).
+ *   - Step schedule: linear ramp alpha_0 -> 0, constant within a sweep
+ *     (Section II-B, Appendix B, Table IX).
+ *   - Binarization with equally spaced bisectors over a semicircle and the
+ *     best cut (Alg. 1, Appendix B: 100 bisectors spaced 1.8 degrees).
+ *   - Greedy edge colouring (Section II-B) and the regular lattice pattern.
+ * Readings taken where the paper is silent are listed with each function.
+ *
+ * Random numbers: Philox4x32-10 written from Salmon, Moraes, Dror and Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3" (SC'11).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon et al. 2011): 10 rounds of the 4x32 Philox S-box    */
+/* with multipliers 0xD2511F53 / 0xCD9E8D57 and Weyl key increments          */
+/* 0x9E3779B9 / 0xBB67AE85 (golden ratio and sqrt(3)-1).                     */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* 24-bit uniform in [0,1): top 24 bits of a Philox word, exact in FP32. */
+static double orc_u24(uint32_t word) { return (double)(word >> 8) * 0x1p-24; }
+
+/* Random initial state (Alg. 1 "Set x_i random"): key = (seed low, seed
+ * high), counter = (vertex/4, replica, 0, 0); vertex v takes word v mod 4. */
+void orc_init_phases(int32_t n, uint64_t seed, int64_t replica, double *x)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    for (int32_t v = 0; v < n; ++v) {
+        uint32_t ctr[4] = {(uint32_t)(v >> 2), (uint32_t)replica, 0u, 0u};
+        uint32_t o[4];
+        orc_philox4x32_10(ctr, key, o);
+        x[v] = orc_u24(o[v & 3]);
+    }
+}
+
+/* DWT reference angle theta_ref for sweep s of a replica (Alg. 1: "Select
+ * random reference angle"; Section II-E: one global random value per DWT
+ * event): key = seed, counter = (s, replica, 0, 1); theta = top 24 bits of
+ * word 0, in turns. */
+double orc_theta(uint64_t seed, int64_t replica, int64_t sweep)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)sweep, (uint32_t)replica, 0u, 1u};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return orc_u24(o[0]);
+}
+
+/* Step schedule (Section II-B; Table IX: initial alpha_0, final 0; updated
+ * once per sweep, constant within it). Reading: alpha_s = alpha_0 (S-s)/(S-1)
+ * for s = 1..S, so alpha_1 = alpha_0 and alpha_S = 0; a single-sweep run
+ * uses alpha_0. */
+double orc_alpha(int64_t s, int64_t S, double alpha0)
+{
+    if (S <= 1) return alpha0;
+    return alpha0 * (double)(S - s) / (double)(S - 1);
+}
+
+/* Modular wrap onto [0,1) (Section II-A: "updates use modular arithmetic").
+ * A result that rounds to 1.0 is the same point as 0.0 and becomes 0.0. */
+double orc_wrap(double y)
+{
+    double r = y - floor(y);
+    if (r >= 1.0) r = 0.0;
+    return r;
+}
+
+/* Biased sign of eq. (4) applied to the minimum angular difference
+ * (Fig. 1 caption): d = ((x_i - x_j + 1/2) mod 1) - 1/2 in [-1/2, 1/2);
+ * +1 when d >= 0, -1 when d < 0. Equivalently +1 iff frac(x_i - x_j) < 1/2.
+ * Exactly opposite points (d = -1/2) give -1. */
+int orc_sgn_b(double xi, double xj)
+{
+    double f = (xi - xj) - floor(xi - xj);
+    return (f < 0.5) ? 1 : -1;
+}
+
+/* Distance of the minimum angular difference from the two switching points
+ * of eq. (4), d = 0 and d = -1/2; used to flag near-ties, where an FP32 and
+ * an FP64 evaluation may legitimately take different branches. */
+static double orc_tie_distance(double xi, double xj)
+{
+    double f = (xi - xj) - floor(xi - xj); /* in [0,1] */
+    double a = fabs(f);
+    double b = fabs(f - 0.5);
+    double c = fabs(f - 1.0);
+    double m = a < b ? a : b;
+    return m < c ? m : c;
+}
+
+/* IEEE 754 binary16 round-to-nearest-even of a value with |y| <= 1/2:
+ * 10 fraction bits in normal binades (exponent >= -14), quantum 2^-24 in
+ * the subnormal range. */
+double orc_round_binary16(double y)
+{
+    if (y == 0.0) return y;
+    int E;
+    frexp(y, &E);             /* |y| = f 2^E, f in [1/2, 1): binade exponent E-1 */
+    int e = E - 1;
+    if (e < -14) e = -14;     /* subnormals share the quantum of the lowest binade */
+    double q = ldexp(1.0, e - 10);
+    return nearbyint(y / q) * q; /* default rounding mode: to nearest, ties to even */
+}
+
+/* Storage rounding: 0 = none (FP64), 1 = binary16 of the phase's
+ * representative in [-1/2, 1/2). The result is returned in [0,1). */
+static double orc_store(double x, int32_t storage)
+{
+    if (storage != 1) return x;
+    double g = (x >= 0.5) ? x - 1.0 : x;
+    g = orc_round_binary16(g);
+    return (g < 0.0) ? g + 1.0 : g;
+}
+
+/* Dual-window membership (Section II-D, Alg. 1): two windows of width W
+ * (turns) centred at theta and theta + 1/2, half-open [c - W/2, c + W/2).
+ * Evaluated exactly on q = floor(x 2^32), qt = theta 2^32:
+ *   ((q - qt + QW/2) mod 2^31) < QW,   QW = round(W 2^32).
+ * Returns 1 inside, 0 outside; *dist gets the distance (turns) to the
+ * nearest window edge. */
+static int orc_in_window(double x, double theta, double W, double *dist)
+{
+    uint64_t QW = (uint64_t)floor(W * 4294967296.0 + 0.5);
+    uint64_t Qh = QW >> 1;
+    uint32_t q = (uint32_t)(uint64_t)floor(x * 4294967296.0);
+    uint32_t qt = (uint32_t)(uint64_t)floor(theta * 4294967296.0);
+    uint32_t rel = (uint32_t)(q - qt + (uint32_t)Qh) & 0x7FFFFFFFu;
+    if (dist) {
+        double r = (double)rel * 0x1p-32;           /* in [0, 1/2) */
+        double w = (double)QW * 0x1p-32;
+        double d1 = fabs(r - w), d2 = fabs(r), d3 = fabs(0.5 - r);
+        double m = d1 < d2 ? d1 : d2;
+        *dist = m < d3 ? m : d3;
+    }
+    return (uint64_t)rel < QW ? 1 : 0;
+}
+
+int orc_in_window_q(double x, double theta, double W) { return orc_in_window(x, theta, W, 0); }
+
+#define ORC_NO_DWT 1
+#define ORC_NO_SCS 2
+
+/*
+ * One sweep of Alg. 1 on one replica, in place.
+ *   Colour-major edge lists: colour c owns edges [off[c], off[c+1]); each
+ *   edge (src < dst) with Max-Cut weight w = -J (Appendix A).
+ *   Pair update, eq. (6) with J = -w, in turns:
+ *     s = sgn_b(x_i - x_j);  x_i <- wrap(x_i - alpha J s);  x_j <- wrap(x_j + alpha J s)
+ *   Sub-sweeps in colour order 1..C (eqs. (11)-(12)); edges of one colour are
+ *   a matching, so their order inside the colour does not matter.
+ *   With flag NO_SCS the sweep is one simultaneous generalized-gradient step
+ *   over all edges (eq. (8)), the ablation "without SCS" of Table VII.
+ *   Then, when sweep % dwt_period == 0 and DWT is on, every phase inside the
+ *   dual windows moves by +dwt_ratio * alpha (Section II-D; one direction).
+ * Near-ties: an edge whose angular difference is within tie_eps of 0 or 1/2
+ * when processed, and a phase within tie_eps of a window edge, are recorded
+ * in ties[] (edge e as e, vertex v as m + v). force[], when given, has m + n
+ * entries: 0 = natural branch, +1/-1 = forced sign (edges) or forced
+ * inside/outside (vertices).
+ * Returns the number of near-ties found (ties[] holds at most max_ties).
+ */
+int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
+                  const int32_t *dst, const int32_t *w, double *x, double alpha,
+                  int64_t sweep, int32_t dwt_period, double dwt_ratio, double window,
+                  uint64_t seed, int64_t replica, int32_t flags, int32_t storage,
+                  const int8_t *force, double tie_eps, int64_t *ties, int64_t max_ties)
+{
+    int64_t m = off[C];
+    int64_t nt = 0;
+    if (!(flags & ORC_NO_SCS)) {
+        for (int32_t c = 0; c < C; ++c) {
+            for (int64_t e = off[c]; e < off[c + 1]; ++e) {
+                int32_t i = src[e], j = dst[e];
+                double J = -(double)w[e];
+                int s = orc_sgn_b(x[i], x[j]);
+                if (tie_eps > 0.0 && orc_tie_distance(x[i], x[j]) < tie_eps) {
+                    if (nt < max_ties && ties) ties[nt] = e;
+                    ++nt;
+                }
+                if (force && force[e]) s = force[e];
+                double xi = x[i] - alpha * J * (double)s;
+                double xj = x[j] + alpha * J * (double)s;
+                x[i] = orc_store(orc_wrap(xi), storage);
+                x[j] = orc_store(orc_wrap(xj), storage);
+            }
+        }
+    } else {
+        double *dx = (double *)calloc((size_t)n, sizeof(double));
+        if (!dx) return -1;
+        for (int64_t e = 0; e < m; ++e) {
+            int32_t i = src[e], j = dst[e];
+            double J = -(double)w[e];
+            int s = orc_sgn_b(x[i], x[j]);
+            if (tie_eps > 0.0 && orc_tie_distance(x[i], x[j]) < tie_eps) {
+                if (nt < max_ties && ties) ties[nt] = e;
+                ++nt;
+            }
+            if (force && force[e]) s = force[e];
+            dx[i] -= alpha * J * (double)s;
+            dx[j] += alpha * J * (double)s;
+        }
+        for (int32_t v = 0; v < n; ++v) x[v] = orc_store(orc_wrap(x[v] + dx[v]), storage);
+        free(dx);
+    }
+    if (!(flags & ORC_NO_DWT) && dwt_period > 0 && (sweep % dwt_period) == 0) {
+        double theta = orc_theta(seed, replica, sweep);
+        double step = dwt_ratio * alpha;
+        for (int32_t v = 0; v < n; ++v) {
+            double dist = 1.0;
+            int in = orc_in_window(x[v], theta, window, &dist);
+            if (tie_eps > 0.0 && dist < tie_eps) {
+                if (nt < max_ties && ties) ties[nt] = m + v;
+                ++nt;
+            }
+            if (force && force[m + v]) in = force[m + v] > 0;
+            if (in) x[v] = orc_store(orc_wrap(x[v] + step), storage);
+        }
+    }
+    return nt;
+}
+
+/* Bisector binarization and exact cut (Alg. 1 final loop; Appendix B: P
+ * bisectors spaced over a semicircle). Reading: bisector p sits at
+ * B_p = floor(p 2^31 / P) on the 2^32 circle; s_v = +1 iff
+ * ((q_v - B_p) mod 2^32) < 2^31 with q_v = floor(x_v 2^32).
+ * cut_p = sum_e w_e [s_i != s_j] (Max-Cut form, Appendix A), in int64.
+ * Writes all P cuts when cuts != NULL; returns the index of the best cut
+ * (ties -> smallest p) and the spins of that bisector when spins != NULL. */
+int32_t orc_binarize(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                     const int32_t *w, const double *x, int32_t P, int64_t *cuts,
+                     int64_t *best_cut, int8_t *spins)
+{
+    uint32_t *q = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n > 0 ? n : 1));
+    int8_t *s = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!q || !s) { free(q); free(s); return -1; }
+    for (int32_t v = 0; v < n; ++v) q[v] = (uint32_t)(uint64_t)floor(x[v] * 4294967296.0);
+    int32_t best_p = 0;
+    int64_t best = INT64_MIN;
+    for (int32_t p = 0; p < P; ++p) {
+        uint32_t B = (uint32_t)(((uint64_t)p << 31) / (uint64_t)P);
+        for (int32_t v = 0; v < n; ++v) s[v] = ((uint32_t)(q[v] - B) < 0x80000000u) ? 1 : -1;
+        int64_t cut = 0;
+        for (int64_t e = 0; e < m; ++e)
+            if (s[src[e]] != s[dst[e]]) cut += (int64_t)w[e];
+        if (cuts) cuts[p] = cut;
+        if (cut > best) { best = cut; best_p = p; }
+    }
+    if (spins) {
+        uint32_t B = (uint32_t)(((uint64_t)best_p << 31) / (uint64_t)P);
+        for (int32_t v = 0; v < n; ++v) spins[v] = ((uint32_t)(q[v] - B) < 0x80000000u) ? 1 : -1;
+    }
+    if (best_cut) *best_cut = best;
+    free(q); free(s);
+    return best_p;
+}
+
+/* Cut of a spin assignment (Appendix A) and Ising energy eq. (1) with h = 0:
+ * H = -sum J s_i s_j = sum w s_i s_j. */
+int64_t orc_cut(int64_t m, const int32_t *src, const int32_t *dst, const int32_t *w, const int8_t *s)
+{
+    int64_t cut = 0;
+    for (int64_t e = 0; e < m; ++e)
+        if (s[src[e]] != s[dst[e]]) cut += (int64_t)w[e];
+    return cut;
+}
+
+int64_t orc_energy(int64_t m, const int32_t *src, const int32_t *dst, const int32_t *w, const int8_t *s)
+{
+    int64_t H = 0;
+    for (int64_t e = 0; e < m; ++e) H += (int64_t)w[e] * (int64_t)s[src[e]] * (int64_t)s[dst[e]];
+    return H;
+}
+
+/* One full trial of Alg. 1 for one replica: random x, sweeps 1..S with the
+ * schedule, DWT and the bisector readout. x (n) receives the final phases,
+ * cuts (P, optional) the bisector cuts; returns the best cut. */
+int64_t orc_trial(int32_t n, int32_t C, const int64_t *off, const int32_t *src, const int32_t *dst,
+                  const int32_t *w, int64_t S, double alpha0, int32_t dwt_period, double dwt_ratio,
+                  double window, int32_t P, uint64_t seed, int64_t replica, int32_t flags,
+                  int32_t storage, double *x, int8_t *spins, int32_t *best_p)
+{
+    orc_init_phases(n, seed, replica, x);
+    for (int32_t v = 0; v < n; ++v) x[v] = orc_store(x[v], storage);
+    for (int64_t s = 1; s <= S; ++s) {
+        double a = orc_alpha(s, S, alpha0);
+        orc_sweep(n, C, off, src, dst, w, x, a, s, dwt_period, dwt_ratio, window, seed, replica,
+                  flags, storage, 0, 0.0, 0, 0);
+    }
+    int64_t best = 0;
+    int32_t bp = orc_binarize(n, off[C], src, dst, w, x, P, 0, &best, spins);
+    if (best_p) *best_p = bp;
+    return best;
+}
+
+/* Many replicas over host threads (replicas are independent trials). */
+typedef struct {
+    int32_t n, C; const int64_t *off; const int32_t *src, *dst, *w;
+    int64_t S; double alpha0; int32_t dwt_period; double dwt_ratio, window; int32_t P;
+    uint64_t seed; int32_t flags, storage;
+    int64_t r0, r1, stride; int64_t *cuts; int32_t *best_p; double *x_out;
+} orc_job;
+
+static void *orc_worker(void *arg)
+{
+    orc_job *j = (orc_job *)arg;
+    double *x = (double *)malloc(sizeof(double) * (size_t)(j->n > 0 ? j->n : 1));
+    if (!x) return 0;
+    for (int64_t r = j->r0; r < j->r1; r += j->stride) {
+        int32_t bp = 0;
+        j->cuts[r] = orc_trial(j->n, j->C, j->off, j->src, j->dst, j->w, j->S, j->alpha0,
+                               j->dwt_period, j->dwt_ratio, j->window, j->P, j->seed, r,
+                               j->flags, j->storage, x, 0, &bp);
+        if (j->best_p) j->best_p[r] = bp;
+        if (j->x_out) memcpy(j->x_out + (size_t)r * (size_t)j->n, x, sizeof(double) * (size_t)j->n);
+    }
+    free(x);
+    return 0;
+}
+
+int32_t orc_trials(int32_t n, int32_t C, const int64_t *off, const int32_t *src, const int32_t *dst,
+                   const int32_t *w, int64_t S, double alpha0, int32_t dwt_period, double dwt_ratio,
+                   double window, int32_t P, uint64_t seed, int64_t replicas, int32_t flags,
+                   int32_t storage, int32_t threads, int64_t *cuts, int32_t *best_p, double *x_out)
+{
+    if (threads < 1) threads = 1;
+    if (threads > replicas) threads = (int32_t)(replicas > 0 ? replicas : 1);
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    orc_job *jobs = (orc_job *)malloc(sizeof(orc_job) * (size_t)threads);
+    if (!th || !jobs) { free(th); free(jobs); return -1; }
+    for (int32_t t = 0; t < threads; ++t) {
+        orc_job j = {n, C, off, src, dst, w, S, alpha0, dwt_period, dwt_ratio, window, P,
+                     seed, flags, storage, t, replicas, threads, cuts, best_p, x_out};
+        jobs[t] = j;
+        pthread_create(&th[t], 0, orc_worker, &jobs[t]);
+    }
+    for (int32_t t = 0; t < threads; ++t) pthread_join(th[t], 0);
+    free(th); free(jobs);
+    return threads;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Edge colourings (Alg. 1 line "Assign a proper edge coloring")             */
+/* ------------------------------------------------------------------------ */
+
+/* Greedy heuristic of Section II-B: loop over the edges in order and give
+ * each the lowest colour not yet used at either endpoint. Returns C. */
+int32_t orc_color_greedy(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int32_t *color)
+{
+    int32_t *deg = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
+    if (!deg) return -1;
+    int32_t D = 0;
+    for (int64_t e = 0; e < m; ++e) { deg[src[e]]++; deg[dst[e]]++; }
+    for (int32_t v = 0; v < n; ++v) if (deg[v] > D) D = deg[v];
+    free(deg);
+    int32_t K = 2 * D; /* greedy never needs more than 2D-1 colours */
+    if (K < 1) K = 1;
+    uint8_t *used = (uint8_t *)calloc((size_t)n * (size_t)K, 1);
+    if (!used && n > 0) return -1;
+    int32_t C = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t i = src[e], j = dst[e];
+        int32_t c = 0;
+        while (used[(size_t)i * K + c] || used[(size_t)j * K + c]) ++c;
+        color[e] = c;
+        used[(size_t)i * K + c] = 1;
+        used[(size_t)j * K + c] = 1;
+        if (c + 1 > C) C = c + 1;
+    }
+    free(used);
+    return C;
+}
+
+/* Regular 4-colour pattern of a 2D torus with even sides (Section II-B,
+ * Appendix B): colour 0/1 = horizontal edges leaving an even/odd column,
+ * colour 2/3 = vertical edges leaving an even/odd row. Vertex v = r L2 + c.
+ * Returns 4, or -1 if an edge is not a torus edge or a side is odd. */
+int32_t orc_color_torus2d(int32_t L1, int32_t L2, int64_t m, const int32_t *src, const int32_t *dst,
+                          int32_t *color)
+{
+    if (L1 < 4 || L2 < 4 || (L1 & 1) || (L2 & 1)) return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t a = src[e], b = dst[e];
+        int32_t ra = a / L2, ca = a % L2, rb = b / L2, cb = b % L2;
+        if (ra == rb && (ca + 1) % L2 == cb) color[e] = (ca & 1);
+        else if (ra == rb && (cb + 1) % L2 == ca) color[e] = (cb & 1);
+        else if (ca == cb && (ra + 1) % L1 == rb) color[e] = 2 + (ra & 1);
+        else if (ca == cb && (rb + 1) % L1 == ra) color[e] = 2 + (rb & 1);
+        else return -1;
+    }
+    return 4;
+}
+
+/* 3D torus, six colours: axis a (0,1,2) and parity of the lower end's
+ * coordinate along a. Vertex v = (i L2 + j) L3 + k. */
+int32_t orc_color_torus3d(int32_t L1, int32_t L2, int32_t L3, int64_t m, const int32_t *src,
+                          const int32_t *dst, int32_t *color)
+{
+    int32_t L[3] = {L1, L2, L3};
+    for (int a = 0; a < 3; ++a) if (L[a] < 4 || (L[a] & 1)) return -1;
+    for (int64_t e = 0; e < m; ++e) {
+        int32_t u[2] = {src[e], dst[e]};
+        int32_t co[2][3];
+        for (int t = 0; t < 2; ++t) {
+            co[t][2] = u[t] % L3;
+            co[t][1] = (u[t] / L3) % L2;
+            co[t][0] = u[t] / (L2 * L3);
+        }
+        int found = 0;
+        for (int a = 0; a < 3 && !found; ++a) {
+            int same = 1;
+            for (int b = 0; b < 3; ++b) if (b != a && co[0][b] != co[1][b]) same = 0;
+            if (!same) continue;
+            if ((co[0][a] + 1) % L[a] == co[1][a]) { color[e] = 2 * a + (co[0][a] & 1); found = 1; }
+            else if ((co[1][a] + 1) % L[a] == co[0][a]) { color[e] = 2 * a + (co[1][a] & 1); found = 1; }
+        }
+        if (!found) return -1;
+    }
+    return 6;
+}
+
+/* Partition check (Section II-C: E = E_1 u ... u E_C, each E_c a matching):
+ * returns 0 if every edge has a colour in [0,C) and no vertex meets two
+ * edges of one colour; 1 if a colour is out of range; 2 if a colour class
+ * is not a matching. */
+int32_t orc_validate_partition(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                               int32_t C, const int32_t *color)
+{
+    if (C < 0) return 1;
+    uint8_t *seen = (uint8_t *)calloc((size_t)n * (size_t)(C > 0 ? C : 1), 1);
+    if (!seen && n > 0) return -1;
+    int32_t rc = 0;
+    for (int64_t e = 0; e < m && rc == 0; ++e) {
+        int32_t c = color[e];
+        if (c < 0 || c >= C) { rc = 1; break; }
+        size_t a = (size_t)src[e] * (size_t)C + (size_t)c;
+        size_t b = (size_t)dst[e] * (size_t)C + (size_t)c;
+        if (seen[a] || seen[b]) { rc = 2; break; }
+        seen[a] = seen[b] = 1;
+    }
+    free(seen);
+    return rc;
+}
+
+/* Exhaustive Max-Cut for small n (n <= 26): every assignment with s_0 = +1
+ * (a global flip leaves the cut unchanged). Returns the optimum cut and one
+ * optimal assignment. */
+int64_t orc_bruteforce_maxcut(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                              const int32_t *w, int8_t *best_spins)
+{
+    if (n <= 0) return 0;
+    if (n > 26) return INT64_MIN;
+    int8_t *s = (int8_t *)malloc((size_t)n);
+    if (!s) return INT64_MIN;
+    int64_t best = INT64_MIN;
+    uint64_t total = (uint64_t)1 << (n - 1);
+    for (uint64_t mask = 0; mask < total; ++mask) {
+        s[0] = 1;
+        for (int32_t v = 1; v < n; ++v) s[v] = ((mask >> (v - 1)) & 1u) ? -1 : 1;
+        int64_t cut = orc_cut(m, src, dst, w, s);
+        if (cut > best) {
+            best = cut;
+            if (best_spins) memcpy(best_spins, s, (size_t)n);
+        }
+    }
+    free(s);
+    return best;
+}
