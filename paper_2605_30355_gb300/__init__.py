@@ -1,0 +1,287 @@
+"""Cosm (Collective Switched Motion) on GB300: thin Python binding.
+
+Every call marshals arguments into the C ABI of ``include/cosm.h`` implemented
+by the in-tree CUDA library ``libcosm.so`` (built by ``build.py``); all steps of
+the solver run in that library's kernels. There is no CPU fallback: importing
+this package raises if the library is missing, and device calls raise if
+the CUDA runtime reports an error.
+
+PyTorch is optional plumbing: a ``torch.cuda.Stream`` may be passed wherever a
+stream is accepted, and device tensors may be passed as output buffers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcosm.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_NOT_A_MATCHING = -2
+ERR_PARTITION = -3
+ERR_TOO_LARGE = -4
+ERR_CUDA = -5
+ERR_TIMEOUT = -6
+ERR_STATE = -7
+ERR_NOMEM = -8
+
+F32 = 0
+F16 = 1
+NO_DWT = 1
+NO_SCS = 2
+
+#: every symbol include/cosm.h declares
+EXPORTS = (
+    "cosm_default_params", "cosm_create", "cosm_destroy", "cosm_run", "cosm_sync", "cosm_get_best",
+    "cosm_get_replica_cuts", "cosm_get_state", "cosm_set_state", "cosm_step", "cosm_readout",
+    "cosm_solve", "cosm_layout", "cosm_color_greedy", "cosm_color_misra_gries",
+    "cosm_color_torus2d", "cosm_color_torus3d", "cosm_validate_partition", "cosm_probe_smem",
+    "cosm_last_error",
+)
+
+
+class CosmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cosm error {code}: {msg}")
+        self.code = code
+
+
+class GraphDesc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("m", C.c_int64), ("src", C.c_void_p), ("dst", C.c_void_p),
+                ("w", C.c_void_p), ("n_colors", C.c_int32), ("color", C.c_void_p),
+                ("dims", C.c_int32 * 3)]
+
+
+class Params(C.Structure):
+    _fields_ = [("alpha0_deg", C.c_double), ("dwt_ratio", C.c_double), ("dwt_period", C.c_int32),
+                ("window_deg", C.c_double), ("n_bisectors", C.c_int32), ("storage", C.c_int32),
+                ("flags", C.c_int32), ("reserved", C.c_int32)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libcosm.so is not built ({LIB_PATH}); run paper_2605_30355_gb300/build.py "
+                          "or __graft_entry__.build()")
+    L = C.CDLL(LIB_PATH)
+    P, i32, i64, u64 = C.c_void_p, C.c_int32, C.c_int64, C.c_uint64
+    sig = {
+        "cosm_default_params": (None, [P]),
+        "cosm_create": (C.c_int, [P, P, P]),
+        "cosm_destroy": (None, [P]),
+        "cosm_run": (C.c_int, [P, i64, i32, u64, P]),
+        "cosm_sync": (C.c_int, [P]),
+        "cosm_get_best": (C.c_int, [P, P, P, P, P]),
+        "cosm_get_replica_cuts": (C.c_int, [P, P, P]),
+        "cosm_get_state": (C.c_int, [P, P]),
+        "cosm_set_state": (C.c_int, [P, P, i32, u64]),
+        "cosm_step": (C.c_int, [P, i64, C.c_float, P]),
+        "cosm_readout": (C.c_int, [P, P]),
+        "cosm_solve": (C.c_int, [P, P, i64, i32, u64, P, P, P, P]),
+        "cosm_layout": (C.c_int, [P, P]),
+        "cosm_color_greedy": (C.c_int, [i32, i64, P, P, P, P]),
+        "cosm_color_misra_gries": (C.c_int, [i32, i64, P, P, P, P]),
+        "cosm_color_torus2d": (C.c_int, [i32, i32, i64, P, P, P]),
+        "cosm_color_torus3d": (C.c_int, [i32, i32, i32, i64, P, P, P]),
+        "cosm_validate_partition": (C.c_int, [i32, i64, P, P, i32, P]),
+        "cosm_probe_smem": (C.c_int, [i32, P, P]),
+        "cosm_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    return L
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise CosmError(rc, _lib.cosm_last_error().decode())
+    return rc
+
+
+def _p(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return C.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if hasattr(s, "cuda_stream"):
+        return C.c_void_p(s.cuda_stream)
+    return C.c_void_p(int(s))
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _lib.cosm_default_params(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise TypeError(f"unknown parameter {k}")
+        setattr(p, k, v)
+    return p
+
+
+def _desc(n, src, dst, w, color=None, n_colors=0, dims=()):
+    keep = [_i32(src), _i32(dst), _i32(w)]
+    d = GraphDesc()
+    d.n = int(n)
+    d.m = int(keep[0].shape[0])
+    d.src, d.dst, d.w = (k.ctypes.data for k in keep)
+    if color is not None:
+        keep.append(_i32(color))
+        d.color = keep[-1].ctypes.data
+        d.n_colors = int(n_colors)
+    dd = list(dims) + [0] * (3 - len(dims))
+    d.dims = (C.c_int32 * 3)(*dd[:3])
+    return d, keep
+
+
+class Solver:
+    """One instance on the current CUDA device (cosm_create ... cosm_destroy)."""
+
+    def __init__(self, n, src, dst, w, color=None, n_colors=0, dims=(), params=None, **kw):
+        self.params = params if params is not None else default_params(**kw)
+        desc, keep = _desc(n, src, dst, w, color, n_colors, dims)
+        h = C.c_void_p()
+        _check(_lib.cosm_create(C.byref(desc), C.byref(self.params), C.byref(h)))
+        self._h = h
+        self.n = int(n)
+        self.replicas = 0
+
+    @classmethod
+    def from_instance(cls, inst, color=None, n_colors=0, use_dims=True, **kw):
+        return cls(inst.n, inst.src, inst.dst, inst.w, color, n_colors,
+                   inst.dims if use_dims else (), **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cosm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, sweeps, replicas, seed, stream=None):
+        self.replicas = int(replicas)
+        _check(_lib.cosm_run(self._h, int(sweeps), int(replicas), int(seed), _stream(stream)))
+
+    def sync(self):
+        _check(_lib.cosm_sync(self._h))
+
+    def best(self, spins_out=None):
+        cut, en, rep = C.c_int64(), C.c_int64(), C.c_int32()
+        spins = spins_out if spins_out is not None else np.zeros(self.n, dtype=np.int8)
+        _check(_lib.cosm_get_best(self._h, C.byref(cut), C.byref(en), C.byref(rep), _p(spins)))
+        return int(cut.value), int(en.value), int(rep.value), spins
+
+    def replica_cuts(self):
+        cuts = np.zeros(self.replicas, dtype=np.int64)
+        bps = np.zeros(self.replicas, dtype=np.int32)
+        _check(_lib.cosm_get_replica_cuts(self._h, _p(cuts), _p(bps)))
+        return cuts, bps
+
+    def get_state(self):
+        x = np.zeros((self.replicas, self.n), dtype=np.float64)
+        _check(_lib.cosm_get_state(self._h, _p(x)))
+        return x
+
+    def set_state(self, phases, seed=0):
+        x = np.ascontiguousarray(phases, dtype=np.float64)
+        self.replicas = int(x.shape[0])
+        _check(_lib.cosm_set_state(self._h, _p(x), self.replicas, int(seed)))
+
+    def step(self, sweep, alpha, stream=None):
+        _check(_lib.cosm_step(self._h, int(sweep), float(alpha), _stream(stream)))
+
+    def readout(self, stream=None):
+        _check(_lib.cosm_readout(self._h, _stream(stream)))
+
+    def layout(self):
+        out = (C.c_int32 * 8)()
+        _check(_lib.cosm_layout(self._h, out))
+        keys = ("K", "threads", "smem", "occupancy", "lattice", "grid", "launches", "colors")
+        return dict(zip(keys, list(out)))
+
+
+def solve(n, src, dst, w, sweeps, replicas, seed, color=None, n_colors=0, dims=(), params=None,
+          replica_cuts=False, **kw):
+    """One-shot host-buffer call (cosm_solve): returns (cut, energy, spins, cuts|None)."""
+    prm = params if params is not None else default_params(**kw)
+    desc, keep = _desc(n, src, dst, w, color, n_colors, dims)
+    cut, en = C.c_int64(), C.c_int64()
+    spins = np.zeros(int(n), dtype=np.int8)
+    cuts = np.zeros(int(replicas), dtype=np.int64) if replica_cuts else None
+    _check(_lib.cosm_solve(C.byref(desc), C.byref(prm), int(sweeps), int(replicas), int(seed),
+                           C.byref(cut), C.byref(en), _p(spins), _p(cuts)))
+    return int(cut.value), int(en.value), spins, cuts
+
+
+def probe_smem(iters=4096):
+    """Measured shared-memory read bandwidth: (bytes per SM clock, device GB/s)."""
+    bpc, gbps = C.c_double(), C.c_double()
+    _check(_lib.cosm_probe_smem(int(iters), C.byref(bpc), C.byref(gbps)))
+    return float(bpc.value), float(gbps.value)
+
+
+def color_greedy(n, src, dst):
+    src, dst = _i32(src), _i32(dst)
+    col = np.zeros(src.shape[0], dtype=np.int32)
+    nc = C.c_int32()
+    _check(_lib.cosm_color_greedy(int(n), src.shape[0], _p(src), _p(dst), _p(col), C.byref(nc)))
+    return col, int(nc.value)
+
+
+def color_misra_gries(n, src, dst):
+    src, dst = _i32(src), _i32(dst)
+    col = np.zeros(src.shape[0], dtype=np.int32)
+    nc = C.c_int32()
+    _check(_lib.cosm_color_misra_gries(int(n), src.shape[0], _p(src), _p(dst), _p(col), C.byref(nc)))
+    return col, int(nc.value)
+
+
+def color_torus2d(L1, L2, src, dst):
+    src, dst = _i32(src), _i32(dst)
+    col = np.zeros(src.shape[0], dtype=np.int32)
+    _check(_lib.cosm_color_torus2d(int(L1), int(L2), src.shape[0], _p(src), _p(dst), _p(col)))
+    return col, 4
+
+
+def color_torus3d(L1, L2, L3, src, dst):
+    src, dst = _i32(src), _i32(dst)
+    col = np.zeros(src.shape[0], dtype=np.int32)
+    _check(_lib.cosm_color_torus3d(int(L1), int(L2), int(L3), src.shape[0], _p(src), _p(dst), _p(col)))
+    return col, 6
+
+
+def validate_partition(n, src, dst, n_colors, color) -> int:
+    src, dst, color = _i32(src), _i32(dst), _i32(color)
+    return int(_lib.cosm_validate_partition(int(n), src.shape[0], _p(src), _p(dst), int(n_colors),
+                                            _p(color)))
+
+
+__all__ = ["Solver", "solve", "default_params", "color_greedy", "color_misra_gries",
+           "color_torus2d", "color_torus3d", "validate_partition", "CosmError", "EXPORTS"]

@@ -1,0 +1,118 @@
+// Internal declarations shared by the host runtime and the CUDA kernels.
+#pragma once
+
+#include <stdint.h>
+#include <vector_types.h>
+
+#include <string>
+#include <vector>
+
+namespace cosm {
+
+constexpr int kMaxColors = 64;
+constexpr int kMaxBisectors = 256;
+constexpr int kMaxVertices = 65536;
+
+// Work segment of one CTA: sweeps [s_begin, s_end] (1-based, inclusive) of
+// one replica tile. A CTA runs its segments in order.
+enum SegFlags : int32_t {
+    SEG_INIT = 1,     // draw initial phases (Philox) instead of loading state
+    SEG_LOAD = 2,     // load the tile's state from global memory
+    SEG_WAIT = 4,     // wait until ready[tile] >= s_begin - 1 before loading
+    SEG_STORE = 8,    // store the tile's state to global memory at the end
+    SEG_SIGNAL = 16,  // publish ready[tile] = s_end after storing
+    SEG_READOUT = 32  // bisector readout after the last sweep
+};
+
+struct Segment {
+    int32_t tile;
+    int32_t flags;
+    int64_t s_begin;
+    int64_t s_end;
+};
+
+struct KernelArgs {
+    int32_t n;            // vertices (slots)
+    int32_t C;            // colours
+    int32_t off[kMaxColors + 1];  // colour offsets into ij / w
+    const uint32_t *ij;   // edge records: slot(src) | slot(dst) << 16, colour-major
+    const int8_t *w;      // Max-Cut weights, colour-major
+    const int32_t *orig_of;  // slot -> original vertex id (Philox init key)
+    void *state;          // [tiles][n_pad][K] phases in the storage type
+    int64_t state_tile_stride;  // elements of the storage type per tile
+    const float2 *alpha_tab;    // (alpha_s, dwt_step_s) for s = alpha_base ..
+    int64_t alpha_base;
+    int64_t S;            // sweeps of the trial (readout after sweep S)
+    uint64_t seed;
+    int32_t replicas;     // valid replicas
+    int32_t dwt_period;   // 0 = off
+    float window;         // DWT window width in turns
+    int32_t flags;        // COSM_NO_DWT | COSM_NO_SCS
+    int32_t P;            // bisectors
+    const Segment *segs;  // all segments
+    const int32_t *seg_off;  // CTA b runs segs[seg_off[b] .. seg_off[b+1])
+    int32_t *ready;       // per tile: last sweep whose state is published
+    int32_t *err;         // device error word (1 = wait timeout)
+    uint64_t wait_limit_ns;
+    int64_t *cut;         // [replicas] best cut
+    int32_t *bestp;       // [replicas] best bisector
+};
+
+struct LaunchCfg {
+    int storage;   // 0 f32, 1 f16
+    int K;         // replicas per tile
+    int threads;   // threads per CTA
+    int grid;      // CTAs
+    size_t smem;   // dynamic shared bytes
+    bool cooperative;
+};
+
+// Shared-memory bytes for a tile and the resident CTAs per SM for a config.
+// accum selects the simultaneous-update (NO_SCS) kernel with per-vertex
+// accumulators in shared memory.
+size_t sweep_smem_bytes(int storage, int K, int n, int P, bool accum);
+int sweep_occupancy(int storage, int K, bool accum, int threads, size_t smem);
+int sweep_launch(const LaunchCfg &cfg, bool accum, const KernelArgs &a, void *stream);
+
+// Finalisation: best replica (max cut, ties -> lowest index), energy, spins.
+struct FinalArgs {
+    int32_t n;
+    int32_t replicas;
+    int32_t K;
+    int32_t storage;
+    int32_t P;
+    int64_t W;            // total weight
+    const void *state;
+    int64_t state_tile_stride;
+    const int32_t *orig_of;
+    const int64_t *cut;
+    const int32_t *bestp;
+    int64_t *best;        // [0] cut, [1] energy, [2] replica
+    int8_t *spins;        // n, original vertex order
+};
+int finalize_launch(const FinalArgs &a, void *stream);
+
+// Host-side graph tools (cosm_graph.cpp).
+struct Graph {
+    int32_t n = 0;
+    int64_t m = 0;
+    std::vector<int32_t> src, dst, w, color;
+    int32_t C = 0;
+    int32_t dims[3] = {0, 0, 0};
+};
+
+int validate_graph(const Graph &g, std::string &why);
+int validate_partition(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int32_t C,
+                       const int32_t *color, std::string &why);
+int color_greedy(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int32_t *color,
+                 int32_t *C);
+int color_misra_gries(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, int32_t *color,
+                      int32_t *C);
+int color_torus2d(int32_t L1, int32_t L2, int64_t m, const int32_t *src, const int32_t *dst,
+                  int32_t *color);
+int color_torus3d(int32_t L1, int32_t L2, int32_t L3, int64_t m, const int32_t *src,
+                  const int32_t *dst, int32_t *color);
+// Vertex -> slot relabel for shared-memory locality (lattice sublattices).
+bool lattice_relabel(const Graph &g, std::vector<int32_t> &slot_of, std::string &why);
+
+}  // namespace cosm

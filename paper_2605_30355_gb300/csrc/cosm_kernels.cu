@@ -1,0 +1,586 @@
+// CUDA kernels of Cosm for sm_103a.
+//
+// One CTA owns a tile of K replicas and keeps all their phases resident in
+// shared memory, interleaved [slot][replica], for a whole segment of sweeps.
+// A sub-sweep (one colour, a matching: Section II-C) maps edges to threads;
+// no vertex repeats inside a colour, so the read-modify-write of both
+// endpoints needs no atomics, and one __syncthreads separates colours.
+// The DWT (Section II-D), the step schedule and the bisector readout with
+// exact integer cuts (Alg. 1) are fused into the same kernel.
+//
+// Phase representation: turns, held as the representative g in [-1/2, 1/2]
+// (g = x for x < 1/2, g = x - 1 otherwise). Every wrap is then
+// g - rint(g), which is exact in binary32; rint uses the 1.5 * 2^23 addend
+// (valid for |g| < 2^22), so the hot loop is plain FP32 adds.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <limits.h>
+#include <stdint.h>
+#include <string.h>
+
+#include "../../include/cosm.h"
+#include "cosm_internal.h"
+
+namespace cosm {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll 1
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// Top 24 bits of a word as a turn in [0,1), mapped to its representative in
+// [-1/2, 1/2); exact in FP32.
+__device__ __forceinline__ float u24_centered(uint32_t word)
+{
+    const float x = (float)(word >> 8) * 0x1p-24f;
+    return x >= 0.5f ? x - 1.0f : x;
+}
+
+// DWT reference angle for (seed, replica, sweep): counter (s, r, 0, 1).
+__device__ __forceinline__ float dwt_theta(uint64_t seed, uint32_t replica, int64_t sweep)
+{
+    uint32_t c[4] = {(uint32_t)sweep, replica, 0u, 1u};
+    philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    return (float)(c[0] >> 8) * 0x1p-24f;  // [0, 1), exact
+}
+
+// ---------------------------------------------------------------- arithmetic
+__device__ __forceinline__ float rint_fast(float v)
+{
+    return __fadd_rn(__fadd_rn(v, 12582912.0f), -12582912.0f);
+}
+__device__ __forceinline__ float wrap_c(float v) { return __fadd_rn(v, -rint_fast(v)); }
+
+// q = floor(x 2^32) mod 2^32 of the turn x represented by g (exact).
+__device__ __forceinline__ uint32_t phase_q(float g)
+{
+    return (uint32_t)(unsigned long long)__float2ll_rd(g * 4294967296.0f);
+}
+
+// ---------------------------------------------------------------- storage
+template <int K>
+__device__ __forceinline__ void ldk(const float *p, float (&x)[K])
+{
+    if constexpr (K == 1) {
+        x[0] = p[0];
+    } else if constexpr (K == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        x[0] = v.x; x[1] = v.y;
+    } else {
+        static_assert(K == 4, "K");
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+    }
+}
+template <int K>
+__device__ __forceinline__ void stk(float *p, const float (&x)[K])
+{
+    if constexpr (K == 1) {
+        p[0] = x[0];
+    } else if constexpr (K == 2) {
+        *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+    } else {
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    }
+}
+__device__ __forceinline__ float2 h2_to_f2(uint32_t u)
+{
+    __half2 h;
+    memcpy(&h, &u, 4);
+    return __half22float2(h);
+}
+__device__ __forceinline__ uint32_t f2_to_h2(float a, float b)
+{
+    const __half2 h = __floats2half2_rn(a, b);
+    uint32_t u;
+    memcpy(&u, &h, 4);
+    return u;
+}
+template <int K>
+__device__ __forceinline__ void ldk(const __half *p, float (&x)[K])
+{
+    if constexpr (K == 2) {
+        const float2 f = h2_to_f2(*reinterpret_cast<const uint32_t *>(p));
+        x[0] = f.x; x[1] = f.y;
+    } else if constexpr (K == 4) {
+        const uint2 u = *reinterpret_cast<const uint2 *>(p);
+        float2 f = h2_to_f2(u.x); x[0] = f.x; x[1] = f.y;
+        f = h2_to_f2(u.y); x[2] = f.x; x[3] = f.y;
+    } else {
+        static_assert(K == 8, "K");
+        const uint4 u = *reinterpret_cast<const uint4 *>(p);
+        float2 f = h2_to_f2(u.x); x[0] = f.x; x[1] = f.y;
+        f = h2_to_f2(u.y); x[2] = f.x; x[3] = f.y;
+        f = h2_to_f2(u.z); x[4] = f.x; x[5] = f.y;
+        f = h2_to_f2(u.w); x[6] = f.x; x[7] = f.y;
+    }
+}
+template <int K>
+__device__ __forceinline__ void stk(__half *p, const float (&x)[K])
+{
+    if constexpr (K == 2) {
+        *reinterpret_cast<uint32_t *>(p) = f2_to_h2(x[0], x[1]);
+    } else if constexpr (K == 4) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(f2_to_h2(x[0], x[1]), f2_to_h2(x[2], x[3]));
+    } else {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(f2_to_h2(x[0], x[1]), f2_to_h2(x[2], x[3]),
+                                                   f2_to_h2(x[4], x[5]), f2_to_h2(x[6], x[7]));
+    }
+}
+
+__host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~size_t(15); }
+
+template <typename Store, int K>
+__host__ __device__ constexpr size_t phase_bytes(int n)
+{
+    return round16((size_t)n * K * sizeof(Store));
+}
+
+// Shared layout: phases | NO_SCS accumulators (FP32, n*K) | readout
+// difference arrays (int32, K*(P+1)) | DWT angles (K floats).
+template <typename Store, int K>
+__host__ __device__ constexpr size_t smem_bytes(int n, int P, bool accum)
+{
+    return phase_bytes<Store, K>(n) + (accum ? round16((size_t)n * K * 4) : 0) +
+           round16((size_t)K * (P + 1) * 4) + round16((size_t)K * 4);
+}
+
+// ---------------------------------------------------------------- pair update
+// Eq. (6) with J = -w, on the minimum angular difference (eq. (4)):
+//   d = x_i - x_j; m = d - rint(d) in [-1/2, 1/2]; s = +1 if m >= 0 else -1
+//   x_i <- wrap(x_i + alpha w s); x_j <- wrap(x_j - alpha w s)
+template <int K>
+__device__ __forceinline__ void pair_update(float (&xi)[K], float (&xj)[K], float aw)
+{
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const float d = __fadd_rn(xi[r], -xj[r]);
+        const float m = __fadd_rn(d, -rint_fast(d));
+        const float st = (m >= 0.0f) ? aw : -aw;
+        xi[r] = wrap_c(__fadd_rn(xi[r], st));
+        xj[r] = wrap_c(__fadd_rn(xj[r], -st));
+    }
+}
+
+// ---------------------------------------------------------------- sweep kernel
+template <typename Store, int K, bool kAccum>
+__global__ void __launch_bounds__(512) sweep_kernel(const KernelArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Store *xs = reinterpret_cast<Store *>(smem);
+    const int n = a.n;
+    size_t off = phase_bytes<Store, K>(n);
+    float *acc = reinterpret_cast<float *>(smem + off);
+    if (kAccum) off += round16((size_t)n * K * 4);
+    int *D = reinterpret_cast<int *>(smem + off);
+    off += round16((size_t)K * (a.P + 1) * 4);
+    float *th = reinterpret_cast<float *>(smem + off);
+    __shared__ int s_skip;
+
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int P = a.P;
+    const bool dwt_on = !(a.flags & 1) && a.dwt_period > 0;
+    const float W2 = 2.0f * a.window, hw = 0.5f * a.window;
+    const size_t vec_bytes = phase_bytes<Store, K>(n);
+
+    for (int si = a.seg_off[blockIdx.x]; si < a.seg_off[blockIdx.x + 1]; ++si) {
+        const Segment sg = a.segs[si];
+        Store *gst = reinterpret_cast<Store *>(a.state) + (size_t)sg.tile * a.state_tile_stride;
+        const uint32_t rep0 = (uint32_t)sg.tile * K;
+
+        // ---- wait for the previous segment of this tile (bounded)
+        if (tid == 0) {
+            s_skip = 0;
+            if (sg.flags & SEG_WAIT) {
+                const int need = (int)(sg.s_begin - 1);
+                unsigned long long t0, t;
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+                while (atomicAdd(&a.ready[sg.tile], 0) < need) {
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+                    if (t - t0 > a.wait_limit_ns) {
+                        atomicExch(a.err, 1);
+                        s_skip = 1;
+                        break;
+                    }
+                    __nanosleep(2000);
+                }
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (s_skip) continue;
+
+        // ---- initial phases (Alg. 1: random x) or load the tile's state
+        if (sg.flags & SEG_INIT) {
+            const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+            for (int k = tid; k < n * K; k += nt) {
+                const int v = k / K, r = k % K;
+                const uint32_t ov = (uint32_t)a.orig_of[v];
+                uint32_t c[4] = {ov >> 2, rep0 + (uint32_t)r, 0u, 0u};
+                philox4x32_10(c, k0, k1);
+                const uint32_t lo = (ov & 1) ? c[1] : c[0], hi = (ov & 1) ? c[3] : c[2];
+                const float g = u24_centered((ov & 2) ? hi : lo);
+                if constexpr (sizeof(Store) == 4) xs[k] = g;
+                else xs[k] = __float2half_rn(g);
+            }
+        } else if (sg.flags & SEG_LOAD) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(gst);
+            uint4 *dst = reinterpret_cast<uint4 *>(xs);
+            for (size_t k = tid; k < vec_bytes / 16; k += nt) dst[k] = __ldcg(src + k);
+        }
+        __syncthreads();
+
+        // ---- sweeps
+        int phase = dwt_on ? (int)(sg.s_begin % a.dwt_period) : 1;
+        for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
+            const float2 at = __ldg(a.alpha_tab + (s - a.alpha_base));
+            const bool dwt = dwt_on && phase == 0;
+            if (dwt && tid < K) th[tid] = dwt_theta(a.seed, rep0 + tid, s);
+            if (!kAccum) {
+                // sequential conflict-free search: colours in order (eq. (11))
+                for (int c = 0; c < a.C; ++c) {
+                    const int e1 = a.off[c + 1];
+                    for (int e = a.off[c] + tid; e < e1; e += nt) {
+                        const uint32_t rec = __ldg(a.ij + e);
+                        const float aw = at.x * (float)__ldg(a.w + e);
+                        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+                        float xi[K], xj[K];
+                        ldk<K>(xs + (size_t)i * K, xi);
+                        ldk<K>(xs + (size_t)j * K, xj);
+                        pair_update<K>(xi, xj, aw);
+                        stk<K>(xs + (size_t)i * K, xi);
+                        stk<K>(xs + (size_t)j * K, xj);
+                    }
+                    __syncthreads();
+                }
+            } else {
+                // simultaneous generalized-gradient step over all edges (eq. (8))
+                for (int k = tid; k < n * K; k += nt) acc[k] = 0.0f;
+                __syncthreads();
+                for (int c = 0; c < a.C; ++c) {
+                    const int e1 = a.off[c + 1];
+                    for (int e = a.off[c] + tid; e < e1; e += nt) {
+                        const uint32_t rec = __ldg(a.ij + e);
+                        const float aw = at.x * (float)__ldg(a.w + e);
+                        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+                        float xi[K], xj[K];
+                        ldk<K>(xs + (size_t)i * K, xi);
+                        ldk<K>(xs + (size_t)j * K, xj);
+#pragma unroll
+                        for (int r = 0; r < K; ++r) {
+                            const float d = __fadd_rn(xi[r], -xj[r]);
+                            const float m = __fadd_rn(d, -rint_fast(d));
+                            const float st = (m >= 0.0f) ? aw : -aw;
+                            acc[(size_t)i * K + r] += st;
+                            acc[(size_t)j * K + r] -= st;
+                        }
+                    }
+                    __syncthreads();  // a colour is a matching: no two threads share a vertex
+                }
+                for (int v = tid; v < n; v += nt) {
+                    float x[K];
+                    ldk<K>(xs + (size_t)v * K, x);
+#pragma unroll
+                    for (int r = 0; r < K; ++r) x[r] = wrap_c(__fadd_rn(x[r], acc[(size_t)v * K + r]));
+                    stk<K>(xs + (size_t)v * K, x);
+                }
+                __syncthreads();
+            }
+            if (dwt) {
+                if (a.C == 0) __syncthreads();
+                // dual window twist: windows [th - W/2, th + W/2) and its antipode;
+                // inside <=> ((x - th + W/2) mod 1/2) < W
+                const float step = at.y;
+                for (int v = tid; v < n; v += nt) {
+                    float x[K];
+                    ldk<K>(xs + (size_t)v * K, x);
+#pragma unroll
+                    for (int r = 0; r < K; ++r) {
+                        const float y = 2.0f * __fadd_rn(__fadd_rn(x[r], -th[r]), hw);
+                        const float u = __fadd_rn(y, -rint_fast(y));
+                        const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
+                        if (in) x[r] = wrap_c(__fadd_rn(x[r], step));
+                    }
+                    stk<K>(xs + (size_t)v * K, x);
+                }
+                __syncthreads();
+            }
+            if (dwt_on && ++phase == a.dwt_period) phase = 0;
+        }
+
+        // ---- bisector readout with exact integer cuts (Alg. 1 final loop)
+        if (sg.flags & SEG_READOUT) {
+            for (int k = tid; k < K * (P + 1); k += nt) D[k] = 0;
+            __syncthreads();
+            int base[K];
+#pragma unroll
+            for (int r = 0; r < K; ++r) base[r] = 0;
+            const int m = a.off[a.C];
+            for (int e = tid; e < m; e += nt) {
+                const uint32_t rec = __ldg(a.ij + e);
+                const int wv = (int)__ldg(a.w + e);
+                const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+                float xi[K], xj[K];
+                ldk<K>(xs + (size_t)i * K, xi);
+                ldk<K>(xs + (size_t)j * K, xj);
+#pragma unroll
+                for (int r = 0; r < K; ++r) {
+                    // spin of v at bisector p: [p < f_v] xor h_v, with h_v the top bit
+                    // of q_v and f_v = #{p : floor(p 2^31 / P) <= q_v mod 2^31}
+                    const uint32_t qi = phase_q(xi[r]), qj = phase_q(xj[r]);
+                    const int fi = (int)(((uint64_t)((qi & 0x7FFFFFFFu) + 1u) * (uint64_t)P +
+                                          0x7FFFFFFFull) >> 31);
+                    const int fj = (int)(((uint64_t)((qj & 0x7FFFFFFFu) + 1u) * (uint64_t)P +
+                                          0x7FFFFFFFull) >> 31);
+                    const int lo = min(fi, fj), hi = max(fi, fj);
+                    int *Dr = D + r * (P + 1);
+                    if ((qi >> 31) == (qj >> 31)) {
+                        if (lo < hi) {  // cut for p in [lo, hi)
+                            atomicAdd(Dr + lo, wv);
+                            atomicAdd(Dr + hi, -wv);
+                        }
+                    } else {  // cut for p in [0, lo) and [hi, P)
+                        base[r] += wv;
+                        if (lo < P) atomicAdd(Dr + lo, -wv);
+                        if (hi < P) atomicAdd(Dr + hi, wv);
+                    }
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < K; ++r) {
+                int b = base[r];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+                if ((tid & 31) == 0 && b) atomicAdd(D + r * (P + 1), b);
+            }
+            __syncthreads();
+            if (tid < K && rep0 + tid < (uint32_t)a.replicas) {
+                const int *Dr = D + tid * (P + 1);
+                long long accv = 0, best = LLONG_MIN;
+                int bp = 0;
+                for (int p = 0; p < P; ++p) {
+                    accv += Dr[p];
+                    if (accv > best) { best = accv; bp = p; }
+                }
+                a.cut[rep0 + tid] = best;
+                a.bestp[rep0 + tid] = bp;
+            }
+        }
+
+        // ---- store / publish the tile's state
+        if (sg.flags & SEG_STORE) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(xs);
+            uint4 *dst = reinterpret_cast<uint4 *>(gst);
+            for (size_t k = tid; k < vec_bytes / 16; k += nt) __stcg(dst + k, src[k]);
+            __threadfence();
+        }
+        __syncthreads();
+        if ((sg.flags & SEG_SIGNAL) && tid == 0) atomicExch(&a.ready[sg.tile], (int)sg.s_end);
+    }
+}
+
+// ---------------------------------------------------------------- finalize
+__global__ void __launch_bounds__(1024) finalize_kernel(const FinalArgs a)
+{
+    __shared__ long long s_cut[1024];
+    __shared__ int s_rep[1024];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    long long best = LLONG_MIN;
+    int br = 0x7FFFFFFF;
+    for (int r = tid; r < a.replicas; r += nt) {
+        const long long c = a.cut[r];
+        if (c > best || (c == best && r < br)) { best = c; br = r; }
+    }
+    s_cut[tid] = best;
+    s_rep[tid] = br;
+    __syncthreads();
+    for (int o = nt / 2; o > 0; o >>= 1) {
+        if (tid < o) {
+            const long long c = s_cut[tid + o];
+            const int r = s_rep[tid + o];
+            if (c > s_cut[tid] || (c == s_cut[tid] && r < s_rep[tid])) {
+                s_cut[tid] = c;
+                s_rep[tid] = r;
+            }
+        }
+        __syncthreads();
+    }
+    const int rb = s_rep[0];
+    const long long cb = s_cut[0];
+    if (tid == 0) {
+        a.best[0] = cb;
+        a.best[1] = a.W - 2 * cb;
+        a.best[2] = rb;
+    }
+    const int tile = rb / a.K, lane = rb % a.K;
+    const uint32_t B = (uint32_t)(((uint64_t)a.bestp[rb] << 31) / (uint64_t)a.P);
+    for (int v = tid; v < a.n; v += nt) {
+        const size_t idx = (size_t)tile * a.state_tile_stride + (size_t)v * a.K + lane;
+        float g;
+        if (a.storage == 0) g = reinterpret_cast<const float *>(a.state)[idx];
+        else g = __half2float(reinterpret_cast<const __half *>(a.state)[idx]);
+        const uint32_t q = phase_q(g);
+        a.spins[a.orig_of[v]] = ((uint32_t)(q - B) < 0x80000000u) ? 1 : -1;
+    }
+}
+
+// ---------------------------------------------------------------- host side
+template <typename Store, int K, bool A>
+static int launch_one(const LaunchCfg &cfg, const KernelArgs &a, void *stream)
+{
+    auto fn = sweep_kernel<Store, K, A>;
+    static size_t set_bytes = 0;
+    if (cfg.smem > 48 * 1024 && cfg.smem > set_bytes) {
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem) !=
+            cudaSuccess)
+            return -1;
+        set_bytes = cfg.smem;
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cfg.cooperative) {
+        void *args[] = {const_cast<KernelArgs *>(&a)};
+        return cudaLaunchCooperativeKernel((const void *)fn, dim3(cfg.grid), dim3(cfg.threads), args,
+                                           cfg.smem, st) == cudaSuccess ? 0 : -1;
+    }
+    fn<<<cfg.grid, cfg.threads, cfg.smem, st>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+template <typename Store, int K, bool A>
+static int occ_one(int threads, size_t smem)
+{
+    auto fn = sweep_kernel<Store, K, A>;
+    if (smem > 48 * 1024)
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess)
+        return 0;
+    return blocks;
+}
+
+#define COSM_DISPATCH(STORAGE, K, ACC, CALL)                                       \
+    do {                                                                           \
+        if ((STORAGE) == 0) {                                                      \
+            if ((K) == 1) { if (ACC) return CALL(float, 1, true); return CALL(float, 1, false); } \
+            if ((K) == 2) { if (ACC) return CALL(float, 2, true); return CALL(float, 2, false); } \
+            if ((K) == 4) { if (ACC) return CALL(float, 4, true); return CALL(float, 4, false); } \
+        } else {                                                                   \
+            if ((K) == 2) { if (ACC) return CALL(__half, 2, true); return CALL(__half, 2, false); } \
+            if ((K) == 4) { if (ACC) return CALL(__half, 4, true); return CALL(__half, 4, false); } \
+            if ((K) == 8) { if (ACC) return CALL(__half, 8, true); return CALL(__half, 8, false); } \
+        }                                                                          \
+    } while (0)
+
+size_t sweep_smem_bytes(int storage, int K, int n, int P, bool accum)
+{
+#define SMEM_CALL(T, KK, A) smem_bytes<T, KK>(n, P, A)
+    COSM_DISPATCH(storage, K, accum, SMEM_CALL);
+#undef SMEM_CALL
+    return 0;
+}
+
+int sweep_occupancy(int storage, int K, bool accum, int threads, size_t smem)
+{
+#define OCC_CALL(T, KK, A) occ_one<T, KK, A>(threads, smem)
+    COSM_DISPATCH(storage, K, accum, OCC_CALL);
+#undef OCC_CALL
+    return 0;
+}
+
+int sweep_launch(const LaunchCfg &cfg, bool accum, const KernelArgs &a, void *stream)
+{
+#define LAUNCH_CALL(T, KK, A) launch_one<T, KK, A>(cfg, a, stream)
+    COSM_DISPATCH(cfg.storage, cfg.K, accum, LAUNCH_CALL);
+#undef LAUNCH_CALL
+    return -1;
+}
+
+int finalize_launch(const FinalArgs &a, void *stream)
+{
+    finalize_kernel<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace cosm
+
+// ---------------------------------------------------------------- SMEM probe
+namespace cosm {
+
+// Shared-memory read bandwidth: every thread streams 16-byte words from a
+// conflict-free pattern; thread 0 records the SM clocks spent.
+__global__ void __launch_bounds__(1024) smem_probe_kernel(int iters, unsigned long long *clk,
+                                                          uint32_t *sink)
+{
+    __shared__ uint4 buf[4096];
+    const int tid = threadIdx.x;
+    for (int k = tid; k < 4096; k += blockDim.x) buf[k] = make_uint4(k, k + 1, k + 2, k + 3);
+    __syncthreads();
+    unsigned long long t0 = clock64();
+    uint32_t acc = 0;
+    int idx = tid;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const uint4 v = buf[(idx + u * 512) & 4095];
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+        idx += 7;
+    }
+    __syncthreads();
+    unsigned long long t1 = clock64();
+    if (tid == 0) atomicMax(clk, t1 - t0);
+    if (acc == 0xFFFFFFFFu) sink[0] = acc;
+}
+
+}  // namespace cosm
+
+extern "C" int cosm_probe_smem(int32_t iters, double *bytes_per_clk_per_sm, double *gbps)
+{
+    using namespace cosm;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return COSM_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    unsigned long long *clk = nullptr;
+    uint32_t *sink = nullptr;
+    if (cudaMalloc(&clk, 8) != cudaSuccess || cudaMalloc(&sink, 4) != cudaSuccess) return COSM_ERR_NOMEM;
+    cudaMemset(clk, 0, 8);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int threads = 1024, blocks = 2 * sms;
+    smem_probe_kernel<<<blocks, threads>>>(iters / 4 + 1, clk, sink);  // warm-up
+    cudaMemset(clk, 0, 8);
+    cudaEventRecord(e0);
+    smem_probe_kernel<<<blocks, threads>>>(iters, clk, sink);
+    cudaEventRecord(e1);
+    cudaError_t err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    unsigned long long cycles = 0;
+    cudaMemcpy(&cycles, clk, 8, cudaMemcpyDeviceToHost);
+    cudaFree(clk);
+    cudaFree(sink);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (err != cudaSuccess) return COSM_ERR_CUDA;
+    const double bytes_per_cta = (double)threads * iters * 8 * 16;
+    // two CTAs share an SM; clk is the longest CTA's span
+    if (bytes_per_clk_per_sm) *bytes_per_clk_per_sm = 2.0 * bytes_per_cta / (double)cycles;
+    if (gbps) *gbps = bytes_per_cta * blocks / (ms * 1e-3) / 1e9;
+    return COSM_OK;
+}

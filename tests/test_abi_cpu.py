@@ -1,0 +1,91 @@
+"""CPU checks of the C ABI library: it loads, exports every symbol that
+include/cosm.h declares, and its host-side colourers and partition checks
+agree with the oracle's (bit-exact for the deterministic ones)."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import instances
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def cosm():
+    from paper_2605_30355_gb300 import build
+    build.build()
+    import paper_2605_30355_gb300 as cosm
+    return cosm
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "cosm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(cosm_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported(cosm):
+    names = _declared()
+    assert len(names) >= 19
+    assert sorted(cosm.EXPORTS) == names
+    out = subprocess.run(["nm", "-D", "--defined-only", cosm.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (cosm_[a-z0-9_]+)\b", out))
+    for name in names:
+        assert name in exported, name
+        assert getattr(cosm.lib(), name)
+
+
+def test_default_params_are_the_paper_settings(cosm):
+    p = cosm.default_params()
+    assert (p.alpha0_deg, p.dwt_ratio, p.dwt_period, p.window_deg, p.n_bisectors) == (14.0, 0.5, 3, 90.0, 100)
+
+
+def test_greedy_colouring_matches_oracle(cosm, orc):
+    for inst in (instances.random_regular(2000, 3, 1), instances.random_regular(2000, 4, 2),
+                 instances.sparse_gnm(3000, 7500, 3), instances.torus2d(10, 12, 4)):
+        a, ca = cosm.color_greedy(inst.n, inst.src, inst.dst)
+        b, cb = orc.color_greedy(inst.n, inst.src, inst.dst)
+        assert ca == cb and np.array_equal(a, b)
+
+
+def test_misra_gries_uses_at_most_delta_plus_one(cosm, orc):
+    for inst in (instances.random_regular(4000, 3, 5), instances.random_regular(4000, 4, 6),
+                 instances.sparse_gnm(2000, 6000, 7), instances.torus3d(4, 4, 6, 8)):
+        col, C = cosm.color_misra_gries(inst.n, inst.src, inst.dst)
+        delta = np.bincount(np.concatenate([inst.src, inst.dst]), minlength=inst.n).max()
+        assert C <= delta + 1
+        assert orc.validate_partition(inst.n, inst.src, inst.dst, C, col) == 0
+
+
+def test_lattice_colourings_match_oracle(cosm, orc):
+    t2 = instances.torus2d(16, 20, 0)
+    a, _ = cosm.color_torus2d(16, 20, t2.src, t2.dst)
+    b, _ = orc.color_torus2d(16, 20, t2.src, t2.dst)
+    assert np.array_equal(a, b)
+    t3 = instances.torus3d(4, 6, 8, 1)
+    a, _ = cosm.color_torus3d(4, 6, 8, t3.src, t3.dst)
+    b, _ = orc.color_torus3d(4, 6, 8, t3.src, t3.dst)
+    assert np.array_equal(a, b)
+    with pytest.raises(cosm.CosmError):
+        cosm.color_torus2d(15, 20, t2.src, t2.dst)
+
+
+def test_partition_validator_agrees_with_oracle(cosm, orc):
+    inst = instances.sparse_gnm(300, 900, 9)
+    col, C = orc.color_greedy(inst.n, inst.src, inst.dst)
+    assert cosm.validate_partition(inst.n, inst.src, inst.dst, C, col) == 0
+    bad = col.copy()
+    # put two edges sharing a vertex into one colour
+    e0 = 0
+    v = inst.src[e0]
+    e1 = int(np.nonzero((inst.src == v) | (inst.dst == v))[0][1])
+    bad[e1] = bad[e0]
+    assert orc.validate_partition(inst.n, inst.src, inst.dst, C, bad) == 2
+    assert cosm.validate_partition(inst.n, inst.src, inst.dst, C, bad) == cosm.ERR_NOT_A_MATCHING
+    bad2 = col.copy()
+    bad2[3] = C
+    assert cosm.validate_partition(inst.n, inst.src, inst.dst, C, bad2) == cosm.ERR_PARTITION

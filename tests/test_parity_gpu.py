@@ -1,0 +1,284 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Bars: cuts, best bisectors and spins bit-exact on replayed states; initial
+phases bit-exact; one sweep from an identical state within 1e-5 rad (FP32
+storage) or 2e-3 rad (FP16 storage, against the oracle's binary16-storage
+mode), with near-ties allowed either branch.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import instances
+from parity_util import TOL_F16, TOL_F32, circ_rad, f16_exact_turns, one_sweep_error
+
+pytestmark = pytest.mark.gpu
+
+A14 = 14.0 / 360.0
+
+
+@pytest.fixture(scope="module")
+def cosm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2605_30355_gb300 import build
+    build.build()
+    import paper_2605_30355_gb300 as cosm
+    return cosm
+
+
+def _solver(cosm, orc, inst, storage=0, use_dims=True, color=None, C=0, **kw):
+    if color is None:
+        color, C = orc.color_instance(inst)
+    s = cosm.Solver.from_instance(inst, color=color, n_colors=C, use_dims=use_dims,
+                                  storage=storage, **kw)
+    g = orc.ColouredGraph(inst.n, inst.src, inst.dst, inst.w, color, C)
+    return s, g
+
+
+def _params_kw(s):
+    p = s.params
+    return dict(dwt_period=p.dwt_period, dwt_ratio=p.dwt_ratio, window=p.window_deg / 360.0,
+                flags=p.flags)
+
+
+CASES = [
+    ("torus16", lambda: instances.torus2d(16, 16, 0), True),
+    ("torus16_general", lambda: instances.torus2d(16, 16, 0), False),
+    ("torus_rect", lambda: instances.torus2d(12, 20, 3), True),
+    ("reg3", lambda: instances.random_regular(1000, 3, 1), False),
+    ("gnm_w3", lambda: instances.sparse_gnm(777, 2300, 2), False),
+    ("torus3d", lambda: instances.torus3d(4, 6, 8, 5), True),
+]
+
+
+@pytest.mark.parametrize("name,make,dims", CASES, ids=[c[0] for c in CASES])
+def test_initial_phases_bit_exact(cosm, orc, name, make, dims):
+    inst = make()
+    s, g = _solver(cosm, orc, inst, use_dims=dims, alpha0_deg=0.0)
+    s.run(1, 9, seed=1234)
+    x = s.get_state()
+    for r in range(9):
+        assert np.array_equal(x[r], orc.init_phases(inst.n, 1234, r)), r
+
+
+def test_initial_phases_f16_rounded(cosm, orc):
+    inst = instances.torus2d(16, 16, 0)
+    s, g = _solver(cosm, orc, inst, storage=1, alpha0_deg=0.0)
+    s.run(1, 6, seed=77)
+    x = s.get_state()
+    for r in range(6):
+        assert np.array_equal(x[r], f16_exact_turns(orc.init_phases(inst.n, 77, r)))
+
+
+@pytest.mark.parametrize("name,make,dims", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("sweep", [1, 3, 500, 999])
+def test_one_sweep_f32(cosm, orc, name, make, dims, sweep):
+    inst = make()
+    kw = {"dwt_ratio": 1.0} if name in ("reg3", "gnm_w3") else {}
+    s, g = _solver(cosm, orc, inst, use_dims=dims, **kw)
+    R = 13
+    x0 = np.stack([orc.init_phases(inst.n, 5, r) for r in range(R)])
+    s.set_state(x0, seed=5)
+    alpha = float(np.float32(orc.alpha(sweep, 1000, A14)))
+    s.step(sweep, alpha)
+    x1 = s.get_state()
+    total_ties = 0
+    for r in range(R):
+        err, nt = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=5, replica=r,
+                                  **_params_kw(s))
+        total_ties += nt
+        assert err <= TOL_F32, (r, err)
+    assert total_ties <= 0.001 * g.m * R
+
+
+@pytest.mark.parametrize("flags", [1, 2, 3])
+def test_one_sweep_ablation_flags(cosm, orc, flags):
+    inst = instances.random_regular(600, 4, 8)
+    s, g = _solver(cosm, orc, inst, use_dims=False, flags=flags, dwt_ratio=1.0)
+    R = 6
+    x0 = np.stack([orc.init_phases(inst.n, 9, r) for r in range(R)])
+    s.set_state(x0, seed=9)
+    alpha = float(np.float32(0.021))
+    for sweep in (2, 3):
+        s.set_state(x0, seed=9)
+        s.step(sweep, alpha)
+        x1 = s.get_state()
+        for r in range(R):
+            # eq. (8) sums per-vertex forces in FP32 in a different order than
+            # the oracle: a few ulps of the step
+            tol = TOL_F32 if not (flags & 2) else 1e-5
+            err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=9, replica=r,
+                                     **_params_kw(s))
+            assert err <= tol, (flags, sweep, r, err)
+
+
+@pytest.mark.parametrize("sweep", [2, 3, 6])
+def test_one_sweep_f16_storage(cosm, orc, sweep):
+    inst = instances.torus2d(16, 16, 1)
+    s, g = _solver(cosm, orc, inst, storage=1)
+    R = 8
+    x0 = np.stack([f16_exact_turns(orc.init_phases(inst.n, 3, r)) for r in range(R)])
+    s.set_state(x0, seed=3)
+    alpha = float(np.float32(orc.alpha(sweep, 100, A14)))
+    s.step(sweep, alpha)
+    x1 = s.get_state()
+    worst_pure = 0.0
+    for r in range(R):
+        err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=3, replica=r,
+                                 storage=orc.STORE_F16, **_params_kw(s))
+        assert err <= TOL_F16, (r, err)
+        xf, _ = orc.sweep(g, x0[r], alpha, sweep, seed=3, replica=r, **_params_kw(s))
+        worst_pure = max(worst_pure, float(circ_rad(xf, x1[r]).max()))
+    # against pure FP64 the error is a few binary16 quanta at most
+    assert worst_pure < 8 * 2 * np.pi * 2 ** -12
+
+
+@pytest.mark.parametrize("name,make,dims", CASES, ids=[c[0] for c in CASES])
+def test_readout_bit_exact_on_replayed_state(cosm, orc, name, make, dims):
+    inst = make()
+    s, g = _solver(cosm, orc, inst, use_dims=dims)
+    R = 11
+    rng = np.random.default_rng(4)
+    # random states, and clustered ones where bisectors matter
+    x = rng.integers(0, 2 ** 24, size=(R, inst.n)) / 2 ** 24
+    x[5:] = np.mod(np.round((0.3 + 0.5 * (rng.random((R - 5, inst.n)) < 0.5)
+                             + rng.normal(0, 0.01, (R - 5, inst.n))) * 2 ** 24) / 2 ** 24, 1.0)
+    s.set_state(x, seed=1)
+    s.readout()
+    cuts, bps = s.replica_cuts()
+    for r in range(R):
+        best, bp, allcuts, spins = orc.binarize(g, x[r])
+        assert cuts[r] == best and bps[r] == bp, r
+    cut, energy, rep, spins = s.best()
+    assert cut == cuts.max() and rep == int(np.argmax(cuts))
+    assert energy == inst.total_weight() - 2 * cut
+    _, _, _, ospins = orc.binarize(g, x[rep])
+    assert np.array_equal(spins, ospins)
+    assert orc.cut(inst.src, inst.dst, inst.w, spins) == cut
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_full_trial_cuts_bit_exact_on_final_state(cosm, orc, storage):
+    inst = instances.torus2d(16, 16, 0)
+    s, g = _solver(cosm, orc, inst, storage=storage)
+    s.run(1000, 64, seed=11)
+    cuts, bps = s.replica_cuts()
+    x = s.get_state()
+    for r in range(64):
+        best, bp, _, _ = orc.binarize(g, x[r])
+        assert cuts[r] == best and bps[r] == bp
+    cut, energy, rep, spins = s.best()
+    assert orc.cut(inst.src, inst.dst, inst.w, spins) == cut == cuts.max()
+    assert energy == orc.energy(inst.src, inst.dst, inst.w, spins)
+
+
+def test_solution_quality_matches_oracle_distribution(cosm, orc):
+    # distributional parity: FP32 GPU and FP64 oracle reach the same best cut
+    inst = instances.torus2d(16, 16, 0)
+    s, g = _solver(cosm, orc, inst)
+    s.run(1000, 64, seed=2)
+    gcuts, _ = s.replica_cuts()
+    ocuts, *_ = orc.trials(g, 1000, 64, seed=2)
+    assert gcuts.max() == ocuts.max()
+    assert abs(gcuts.mean() - ocuts.mean()) < 3.0
+
+
+def test_planted_optimum_reached(cosm, orc):
+    inst = instances.gauge_planted(instances.torus2d(32, 32, 3), 4)
+    s, g = _solver(cosm, orc, inst)
+    s.run(2000, 64, seed=3)
+    cut, energy, rep, spins = s.best()
+    assert cut == inst.meta["opt_cut"]
+    assert energy == inst.meta["ground_energy"]
+
+
+def test_layouts_agree_bit_exact(cosm, orc):
+    # lattice relabel vs plain layout, and replicas per CTA, give the same trial
+    inst = instances.torus2d(16, 16, 6)
+    col, C = orc.color_instance(inst)
+    res = []
+    for dims, K in ((True, 1), (False, 1), (True, 2), (False, 4)):
+        os.environ["COSM_K"] = str(K)
+        try:
+            s, _ = _solver(cosm, orc, inst, use_dims=dims, color=col, C=C)
+            s.run(300, 10, seed=8)
+            res.append((s.replica_cuts()[0], s.get_state()))
+        finally:
+            del os.environ["COSM_K"]
+    for cuts, x in res[1:]:
+        assert np.array_equal(cuts, res[0][0])
+        assert np.array_equal(x, res[0][1])
+
+
+def test_chunked_schedule_matches_single_segment(cosm, orc):
+    # more tiles than resident CTAs: the wrap-around schedule splits trials
+    # across CTAs through global memory, which must not change any result
+    inst = instances.random_regular(500, 3, 2)
+    col, C = orc.color_greedy(inst.n, inst.src, inst.dst)
+    ref = None
+    for cap in (0, 7):
+        if cap:
+            os.environ["COSM_GRID_CAP"] = str(cap)
+        try:
+            s, _ = _solver(cosm, orc, inst, use_dims=False, color=col, C=C, dwt_ratio=1.0)
+            s.run(401, 37, seed=4)
+            out = (s.replica_cuts()[0], s.get_state(), s.layout())
+        finally:
+            os.environ.pop("COSM_GRID_CAP", None)
+        if ref is None:
+            ref = out
+        else:
+            assert out[2]["grid"] == 7
+            assert np.array_equal(out[0], ref[0])
+            assert np.array_equal(out[1], ref[1])
+
+
+def test_edge_cases(cosm, orc):
+    # single edge, odd n, one replica, one bisector, weights up to 127
+    s = cosm.Solver(3, [0], [2], [127], n_bisectors=1)
+    s.run(5, 1, seed=0)
+    cut, en, rep, spins = s.best()
+    assert cut in (0, 127) and rep == 0
+    # two-vertex FM, no DWT
+    s = cosm.Solver(2, [0], [1], [-1], flags=cosm.NO_DWT)
+    s.set_state(np.array([[0.30, 0.20]]))
+    s.step(1, 0.01)
+    np.testing.assert_allclose(s.get_state()[0], [0.29, 0.21], atol=1e-7)
+    # invalid inputs are rejected before any device work
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(3, [0, 0], [1, 1], [1, 1])          # duplicate edge
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(3, [1], [0], [1])                   # not canonical
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(3, [0, 1], [1, 2], [1, 1], color=[0, 0], n_colors=1)  # not a matching
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(3, [0], [1], [0])                   # zero weight
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(100000, [0], [1], [1])              # too many vertices
+    inst = instances.torus2d(16, 16, 0)
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(inst.n, inst.src, inst.dst, inst.w, dims=(16, 15))
+
+
+def test_full_size_workload_sampled(cosm, orc):
+    # the 20k-spin torus at the bench's launch configuration (1024 replicas),
+    # short trial; sampled replicas checked against the oracle
+    inst = instances.torus2d(100, 200, 0)
+    s, g = _solver(cosm, orc, inst)
+    s.run(60, 1024, seed=21)
+    cuts, bps = s.replica_cuts()
+    x = s.get_state()
+    for r in (0, 1, 511, 1000, 1023):
+        best, bp, _, _ = orc.binarize(g, x[r])
+        assert cuts[r] == best and bps[r] == bp
+    # one more sweep from the exported state, sampled replicas
+    alpha = float(np.float32(0.013))
+    s.step(61, alpha)
+    x1 = s.get_state()
+    kw = _params_kw(s)
+    for r in (3, 700):
+        err, _ = one_sweep_error(orc, g, x[r], x1[r], alpha, 61, seed=21, replica=r, **kw)
+        assert err <= TOL_F32
