@@ -99,11 +99,23 @@ def _load():
     return L
 
 
-_lib = _load()
+class _Lazy:
+    """Loads libcosm.so on first use; raises ImportError if it is not built."""
+
+    _handle = None
+
+    def __getattr__(self, name):
+        if _Lazy._handle is None:
+            _Lazy._handle = _load()
+        return getattr(_Lazy._handle, name)
+
+
+_lib = _Lazy()
 
 
 def lib():
-    return _lib
+    _lib.cosm_last_error  # force the load
+    return _Lazy._handle
 
 
 def _check(rc):
