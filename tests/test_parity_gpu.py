@@ -125,15 +125,17 @@ def test_one_sweep_f16_storage(cosm, orc, sweep):
     alpha = float(np.float32(orc.alpha(sweep, 100, A14)))
     s.step(sweep, alpha)
     x1 = s.get_state()
-    worst_pure = 0.0
+    far = []
     for r in range(R):
         err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=3, replica=r,
                                  storage=orc.STORE_F16, **_params_kw(s))
         assert err <= TOL_F16, (r, err)
+        # against pure FP64 (no storage rounding) most phases stay within a few
+        # binary16 quanta; a rounding can flip a sign decision near a tie, which
+        # moves a few phases by a whole step, so this is a distribution bound
         xf, _ = orc.sweep(g, x0[r], alpha, sweep, seed=3, replica=r, **_params_kw(s))
-        worst_pure = max(worst_pure, float(circ_rad(xf, x1[r]).max()))
-    # against pure FP64 the error is a few binary16 quanta at most
-    assert worst_pure < 8 * 2 * np.pi * 2 ** -12
+        far.append(float((circ_rad(xf, x1[r]) > 8 * 2 * np.pi * 2 ** -12).mean()))
+    assert np.mean(far) < 0.02
 
 
 @pytest.mark.parametrize("name,make,dims", CASES, ids=[c[0] for c in CASES])
