@@ -56,9 +56,17 @@ struct KernelArgs {
     uint64_t wait_limit_ns;
     int64_t *cut;         // [replicas] best cut
     int32_t *bestp;       // [replicas] best bisector
+    // 2D lattice mode: Q = n/4 slots per sublattice, Wd = L2/2 columns, and
+    // wbits bit (p*Q + f) = 1 when edge f of pass p has w = -1
+    const uint32_t *wbits;
+    int32_t Q;
+    int32_t Wd;
 };
 
+enum KernelMode { MODE_GENERAL_ = 0, MODE_ACCUM_ = 1, MODE_LATTICE2D_ = 2 };
+
 struct LaunchCfg {
+    int mode;      // KernelMode
     int storage;   // 0 f32, 1 f16
     int K;         // replicas per tile
     int threads;   // threads per CTA
@@ -68,11 +76,11 @@ struct LaunchCfg {
 };
 
 // Shared-memory bytes for a tile and the resident CTAs per SM for a config.
-// accum selects the simultaneous-update (NO_SCS) kernel with per-vertex
-// accumulators in shared memory.
-size_t sweep_smem_bytes(int storage, int K, int n, int P, bool accum);
-int sweep_occupancy(int storage, int K, bool accum, int threads, size_t smem);
-int sweep_launch(const LaunchCfg &cfg, bool accum, const KernelArgs &a, void *stream);
+// mode: general edge lists, simultaneous update (NO_SCS, per-vertex
+// accumulators in shared memory) or the implicit-index 2D lattice.
+size_t sweep_smem_bytes(int storage, int K, int n, int P, int mode);
+int sweep_occupancy(int storage, int K, int mode, int threads, size_t smem);
+int sweep_launch(const LaunchCfg &cfg, const KernelArgs &a, void *stream);
 
 // Finalisation: best replica (max cut, ties -> lowest index), energy, spins.
 struct FinalArgs {

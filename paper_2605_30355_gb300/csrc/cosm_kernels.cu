@@ -175,220 +175,379 @@ __device__ __forceinline__ void pair_update(float (&xi)[K], float (&xj)[K], floa
     }
 }
 
+// ---------------------------------------------------------------- DWT
+// Dual window twist (Section II-D): windows [th - W/2, th + W/2) and their
+// antipode; x is inside iff ((x - th + W/2) mod 1/2) < W. With y = 2x + c,
+// c = 2 (W/2 - th) precomputed per replica, the test is frac(y) < 2W.
+template <int K>
+__device__ __forceinline__ void dwt_apply(float (&x)[K], const float *thc, float W2, float step)
+{
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const float y = fmaf(2.0f, x[r], thc[r]);
+        const float u = __fadd_rn(y, -rint_fast(y));
+        const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
+        if (in) x[r] = wrap_c(__fadd_rn(x[r], step));
+    }
+}
+
+// ---------------------------------------------------------------- segments
+// Shared-memory layout of one tile and the per-segment prologue (bounded
+// wait, init or load) and epilogue (readout, store, publish).
+template <typename Store, int K>
+struct Tile {
+    Store *xs;     // [n][K] phases
+    float *acc;    // [n][K] NO_SCS accumulators (mode 1 only)
+    int *D;        // [K][P+1] readout difference arrays
+    float *thc;    // [K] DWT offsets 2 (W/2 - theta)
+    size_t vec_bytes;
+};
+
+template <typename Store, int K>
+__device__ __forceinline__ Tile<Store, K> carve(unsigned char *smem, int n, int P, bool accum)
+{
+    Tile<Store, K> t;
+    t.xs = reinterpret_cast<Store *>(smem);
+    t.vec_bytes = phase_bytes<Store, K>(n);
+    size_t off = t.vec_bytes;
+    t.acc = reinterpret_cast<float *>(smem + off);
+    if (accum) off += round16((size_t)n * K * 4);
+    t.D = reinterpret_cast<int *>(smem + off);
+    off += round16((size_t)K * (P + 1) * 4);
+    t.thc = reinterpret_cast<float *>(smem + off);
+    return t;
+}
+
+// Returns false when the bounded wait gave up (the error word is set).
+template <typename Store, int K>
+__device__ bool seg_begin(const KernelArgs &a, const Segment &sg, const Tile<Store, K> &t, int *s_skip)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) {
+        *s_skip = 0;
+        if (sg.flags & SEG_WAIT) {
+            const int need = (int)(sg.s_begin - 1);
+            unsigned long long t0, t1;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+            while (atomicAdd(&a.ready[sg.tile], 0) < need) {
+                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                if (t1 - t0 > a.wait_limit_ns) {
+                    atomicExch(a.err, 1);
+                    *s_skip = 1;
+                    break;
+                }
+                __nanosleep(2000);
+            }
+            __threadfence();
+        }
+    }
+    __syncthreads();
+    if (*s_skip) return false;
+    const Store *gst = reinterpret_cast<const Store *>(a.state) + (size_t)sg.tile * a.state_tile_stride;
+    if (sg.flags & SEG_INIT) {
+        // Alg. 1 "Set x_i random": Philox keyed by seed, counter (v/4, r, 0, 0)
+        const uint32_t rep0 = (uint32_t)sg.tile * K;
+        const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
+        for (int k = tid; k < a.n * K; k += nt) {
+            const int v = k / K, r = k % K;
+            const uint32_t ov = (uint32_t)a.orig_of[v];
+            uint32_t c[4] = {ov >> 2, rep0 + (uint32_t)r, 0u, 0u};
+            philox4x32_10(c, k0, k1);
+            const uint32_t lo = (ov & 1) ? c[1] : c[0], hi = (ov & 1) ? c[3] : c[2];
+            const float g = u24_centered((ov & 2) ? hi : lo);
+            if constexpr (sizeof(Store) == 4) t.xs[k] = g;
+            else t.xs[k] = __float2half_rn(g);
+        }
+    } else if (sg.flags & SEG_LOAD) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(gst);
+        uint4 *dst = reinterpret_cast<uint4 *>(t.xs);
+        for (size_t k = tid; k < t.vec_bytes / 16; k += nt) dst[k] = __ldcg(src + k);
+    }
+    __syncthreads();
+    return true;
+}
+
+// Bisector readout with exact integer cuts (Alg. 1 final loop). Spin of v
+// at bisector p is [p < f_v] xor h_v, with h_v the top bit of
+// q_v = floor(x_v 2^32) and f_v = #{p : floor(p 2^31 / P) <= q_v mod 2^31};
+// an edge is therefore cut on one interval of p or on its complement, which
+// a difference array over p accumulates exactly.
+template <typename Store, int K>
+__device__ void seg_readout(const KernelArgs &a, const Segment &sg, const Tile<Store, K> &t)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, P = a.P;
+    const uint32_t rep0 = (uint32_t)sg.tile * K;
+    for (int k = tid; k < K * (P + 1); k += nt) t.D[k] = 0;
+    __syncthreads();
+    int base[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) base[r] = 0;
+    const int m = a.off[a.C];
+    for (int e = tid; e < m; e += nt) {
+        const uint32_t rec = __ldg(a.ij + e);
+        const int wv = (int)__ldg(a.w + e);
+        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+        float xi[K], xj[K];
+        ldk<K>(t.xs + (size_t)i * K, xi);
+        ldk<K>(t.xs + (size_t)j * K, xj);
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const uint32_t qi = phase_q(xi[r]), qj = phase_q(xj[r]);
+            const int fi = (int)(((uint64_t)((qi & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
+            const int fj = (int)(((uint64_t)((qj & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
+            const int lo = min(fi, fj), hi = max(fi, fj);
+            int *Dr = t.D + r * (P + 1);
+            if ((qi >> 31) == (qj >> 31)) {
+                if (lo < hi) {  // cut for p in [lo, hi)
+                    atomicAdd(Dr + lo, wv);
+                    atomicAdd(Dr + hi, -wv);
+                }
+            } else {  // cut for p in [0, lo) and [hi, P)
+                base[r] += wv;
+                if (lo < P) atomicAdd(Dr + lo, -wv);
+                if (hi < P) atomicAdd(Dr + hi, wv);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        int b = base[r];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+        if ((tid & 31) == 0 && b) atomicAdd(t.D + r * (P + 1), b);
+    }
+    __syncthreads();
+    if (tid < K && rep0 + tid < (uint32_t)a.replicas) {
+        const int *Dr = t.D + tid * (P + 1);
+        long long accv = 0, best = LLONG_MIN;
+        int bp = 0;
+        for (int p = 0; p < P; ++p) {
+            accv += Dr[p];
+            if (accv > best) { best = accv; bp = p; }
+        }
+        a.cut[rep0 + tid] = best;
+        a.bestp[rep0 + tid] = bp;
+    }
+}
+
+template <typename Store, int K>
+__device__ void seg_end(const KernelArgs &a, const Segment &sg, const Tile<Store, K> &t)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (sg.flags & SEG_READOUT) seg_readout<Store, K>(a, sg, t);
+    if (sg.flags & SEG_STORE) {
+        Store *gst = reinterpret_cast<Store *>(a.state) + (size_t)sg.tile * a.state_tile_stride;
+        const uint4 *src = reinterpret_cast<const uint4 *>(t.xs);
+        uint4 *dst = reinterpret_cast<uint4 *>(gst);
+        for (size_t k = tid; k < t.vec_bytes / 16; k += nt) __stcg(dst + k, src[k]);
+        __threadfence();
+    }
+    __syncthreads();
+    if ((sg.flags & SEG_SIGNAL) && tid == 0) atomicExch(&a.ready[sg.tile], (int)sg.s_end);
+}
+
+// ---------------------------------------------------------------- sub-sweeps
+// General graphs: colour c's edge records [off[c], off[c+1]) map to threads;
+// each thread takes kBatch edges at a time (edges of one colour share no
+// vertex, so all loads of a batch may precede its stores), which keeps
+// several edge-record loads in flight.
+constexpr int kBatch = 4;
+
+template <typename Store, int K>
+__device__ __forceinline__ void general_colour(const KernelArgs &a, Store *xs, int c, float alpha)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int e1 = a.off[c + 1];
+    for (int e0 = a.off[c] + tid; e0 < e1; e0 += kBatch * nt) {
+        uint32_t rec[kBatch];
+        float aw[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = e0 + u * nt;
+            rec[u] = e < e1 ? __ldg(a.ij + e) : 0u;
+            aw[u] = e < e1 ? alpha * (float)__ldg(a.w + e) : 0.0f;
+        }
+        float xi[kBatch][K], xj[kBatch][K];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (e0 + u * nt < e1) {
+                ldk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
+                ldk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) pair_update<K>(xi[u], xj[u], aw[u]);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (e0 + u * nt < e1) {
+                stk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
+                stk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+            }
+        }
+    }
+}
+
+// 2D torus in the sublattice layout (groups A = (even r, even c), B = (even,
+// odd), C = (odd, even), D = (odd, odd), Q = n/4 slots each, row-major with
+// Wd = L2/2 columns). The regular colouring pairs group gp slot f with group
+// gq slot q(f): q = f (kMode 0), the next column with a row wrap (kMode 1),
+// or the next row with a torus wrap (kMode 3). At a wrap the second vertex
+// has the smaller original id, so the two roles of eq. (6) swap. Edge
+// indices are implicit; the +-1 weights come from a per-thread bit mask
+// (bit k set: w = -1 for this thread's k-th edge of the pass).
+template <typename Store, int K, int kMode>
+__device__ __forceinline__ void lattice_pass(Store *xs, int gp, int gq, uint32_t wm, float alpha, int Q,
+                                             int Wd, int m0, int dm, bool dwt, const float *thc,
+                                             float W2, float step)
+{
+    const int nt = blockDim.x;
+    int m = m0;
+    for (int f = threadIdx.x; f < Q; f += nt) {
+        int q = f;
+        bool swp = false;
+        if (kMode == 1) {
+            const bool end = (m == Wd - 1);
+            q = end ? f + 1 - Wd : f + 1;
+            swp = end;
+            m += dm;
+            if (m >= Wd) m -= Wd;
+        } else if (kMode == 3) {
+            q = f + Wd;
+            swp = q >= Q;
+            if (swp) q -= Q;
+        }
+        const float aw = (wm & 1u) ? -alpha : alpha;
+        wm >>= 1;
+        int i = gp + f, j = gq + q;
+        if (swp) { const int tmp = i; i = j; j = tmp; }
+        float xi[K], xj[K];
+        ldk<K>(xs + (size_t)i * K, xi);
+        ldk<K>(xs + (size_t)j * K, xj);
+        pair_update<K>(xi, xj, aw);
+        if (dwt) {
+            dwt_apply<K>(xi, thc, W2, step);
+            dwt_apply<K>(xj, thc, W2, step);
+        }
+        stk<K>(xs + (size_t)i * K, xi);
+        stk<K>(xs + (size_t)j * K, xj);
+    }
+}
+
 // ---------------------------------------------------------------- sweep kernel
-template <typename Store, int K, bool kAccum>
+enum { MODE_GENERAL = 0, MODE_ACCUM = 1, MODE_LATTICE2D = 2 };
+
+template <typename Store, int K, int kMode>
 __global__ void __launch_bounds__(512) sweep_kernel(const KernelArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    Store *xs = reinterpret_cast<Store *>(smem);
-    const int n = a.n;
-    size_t off = phase_bytes<Store, K>(n);
-    float *acc = reinterpret_cast<float *>(smem + off);
-    if (kAccum) off += round16((size_t)n * K * 4);
-    int *D = reinterpret_cast<int *>(smem + off);
-    off += round16((size_t)K * (a.P + 1) * 4);
-    float *th = reinterpret_cast<float *>(smem + off);
     __shared__ int s_skip;
-
+    const Tile<Store, K> t = carve<Store, K>(smem, a.n, a.P, kMode == MODE_ACCUM);
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int P = a.P;
+    const int n = a.n;
     const bool dwt_on = !(a.flags & 1) && a.dwt_period > 0;
     const float W2 = 2.0f * a.window, hw = 0.5f * a.window;
-    const size_t vec_bytes = phase_bytes<Store, K>(n);
+
+    // lattice: this thread's weight bits for the 8 (colour, pair-set) passes
+    uint32_t wm[8];
+    int m0 = 0, dm = 0;
+    if (kMode == MODE_LATTICE2D) {
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            uint32_t bits = 0;
+            int k = 0;
+            for (int f = tid; f < a.Q; f += nt, ++k) {
+                const uint32_t idx = (uint32_t)(p * a.Q + f);
+                bits |= ((__ldg(a.wbits + (idx >> 5)) >> (idx & 31)) & 1u) << k;
+            }
+            wm[p] = bits;
+        }
+        m0 = tid % a.Wd;
+        dm = nt % a.Wd;
+    }
 
     for (int si = a.seg_off[blockIdx.x]; si < a.seg_off[blockIdx.x + 1]; ++si) {
         const Segment sg = a.segs[si];
-        Store *gst = reinterpret_cast<Store *>(a.state) + (size_t)sg.tile * a.state_tile_stride;
+        if (!seg_begin<Store, K>(a, sg, t, &s_skip)) continue;
         const uint32_t rep0 = (uint32_t)sg.tile * K;
-
-        // ---- wait for the previous segment of this tile (bounded)
-        if (tid == 0) {
-            s_skip = 0;
-            if (sg.flags & SEG_WAIT) {
-                const int need = (int)(sg.s_begin - 1);
-                unsigned long long t0, t;
-                asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-                while (atomicAdd(&a.ready[sg.tile], 0) < need) {
-                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-                    if (t - t0 > a.wait_limit_ns) {
-                        atomicExch(a.err, 1);
-                        s_skip = 1;
-                        break;
-                    }
-                    __nanosleep(2000);
-                }
-                __threadfence();
-            }
-        }
-        __syncthreads();
-        if (s_skip) continue;
-
-        // ---- initial phases (Alg. 1: random x) or load the tile's state
-        if (sg.flags & SEG_INIT) {
-            const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-            for (int k = tid; k < n * K; k += nt) {
-                const int v = k / K, r = k % K;
-                const uint32_t ov = (uint32_t)a.orig_of[v];
-                uint32_t c[4] = {ov >> 2, rep0 + (uint32_t)r, 0u, 0u};
-                philox4x32_10(c, k0, k1);
-                const uint32_t lo = (ov & 1) ? c[1] : c[0], hi = (ov & 1) ? c[3] : c[2];
-                const float g = u24_centered((ov & 2) ? hi : lo);
-                if constexpr (sizeof(Store) == 4) xs[k] = g;
-                else xs[k] = __float2half_rn(g);
-            }
-        } else if (sg.flags & SEG_LOAD) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(gst);
-            uint4 *dst = reinterpret_cast<uint4 *>(xs);
-            for (size_t k = tid; k < vec_bytes / 16; k += nt) dst[k] = __ldcg(src + k);
-        }
-        __syncthreads();
-
-        // ---- sweeps
         int phase = dwt_on ? (int)(sg.s_begin % a.dwt_period) : 1;
         for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
             const float2 at = __ldg(a.alpha_tab + (s - a.alpha_base));
             const bool dwt = dwt_on && phase == 0;
-            if (dwt && tid < K) th[tid] = dwt_theta(a.seed, rep0 + tid, s);
-            if (!kAccum) {
-                // sequential conflict-free search: colours in order (eq. (11))
-                for (int c = 0; c < a.C; ++c) {
-                    const int e1 = a.off[c + 1];
-                    for (int e = a.off[c] + tid; e < e1; e += nt) {
-                        const uint32_t rec = __ldg(a.ij + e);
-                        const float aw = at.x * (float)__ldg(a.w + e);
-                        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
-                        float xi[K], xj[K];
-                        ldk<K>(xs + (size_t)i * K, xi);
-                        ldk<K>(xs + (size_t)j * K, xj);
-                        pair_update<K>(xi, xj, aw);
-                        stk<K>(xs + (size_t)i * K, xi);
-                        stk<K>(xs + (size_t)j * K, xj);
+            if (dwt && tid < K)
+                t.thc[tid] = 2.0f * (hw - dwt_theta(a.seed, rep0 + tid, s));
+            if (kMode == MODE_LATTICE2D) {
+                const int Q = a.Q, Wd = a.Wd;
+                // colour 0: horizontal edges from even columns (A-B, C-D)
+                lattice_pass<Store, K, 0>(t.xs, 0, Q, wm[0], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
+                lattice_pass<Store, K, 0>(t.xs, 2 * Q, 3 * Q, wm[1], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
+                __syncthreads();
+                // colour 1: horizontal edges from odd columns (B-A, D-C)
+                lattice_pass<Store, K, 1>(t.xs, Q, 0, wm[2], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
+                lattice_pass<Store, K, 1>(t.xs, 3 * Q, 2 * Q, wm[3], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
+                __syncthreads();
+                // colour 2: vertical edges from even rows (A-C, B-D)
+                lattice_pass<Store, K, 0>(t.xs, 0, 2 * Q, wm[4], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
+                lattice_pass<Store, K, 0>(t.xs, Q, 3 * Q, wm[5], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
+                __syncthreads();
+                // colour 3: vertical edges from odd rows (C-A, D-B); every vertex
+                // meets exactly one of them, so the DWT is applied right here
+                lattice_pass<Store, K, 3>(t.xs, 2 * Q, 0, wm[6], at.x, Q, Wd, m0, dm, dwt, t.thc, W2, at.y);
+                lattice_pass<Store, K, 3>(t.xs, 3 * Q, Q, wm[7], at.x, Q, Wd, m0, dm, dwt, t.thc, W2, at.y);
+                __syncthreads();
+            } else {
+                if (kMode == MODE_GENERAL) {
+                    // sequential conflict-free search: colours in order (eq. (11))
+                    for (int c = 0; c < a.C; ++c) {
+                        general_colour<Store, K>(a, t.xs, c, at.x);
+                        __syncthreads();
+                    }
+                } else {
+                    // simultaneous generalized-gradient step over all edges (eq. (8))
+                    for (int k = tid; k < n * K; k += nt) t.acc[k] = 0.0f;
+                    __syncthreads();
+                    for (int c = 0; c < a.C; ++c) {
+                        const int e1 = a.off[c + 1];
+                        for (int e = a.off[c] + tid; e < e1; e += nt) {
+                            const uint32_t rec = __ldg(a.ij + e);
+                            const float aw = at.x * (float)__ldg(a.w + e);
+                            const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+                            float xi[K], xj[K];
+                            ldk<K>(t.xs + (size_t)i * K, xi);
+                            ldk<K>(t.xs + (size_t)j * K, xj);
+#pragma unroll
+                            for (int r = 0; r < K; ++r) {
+                                const float d = __fadd_rn(xi[r], -xj[r]);
+                                const float mm = __fadd_rn(d, -rint_fast(d));
+                                const float st = (mm >= 0.0f) ? aw : -aw;
+                                t.acc[(size_t)i * K + r] += st;
+                                t.acc[(size_t)j * K + r] -= st;
+                            }
+                        }
+                        __syncthreads();  // one colour is a matching: no shared vertex
+                    }
+                    for (int v = tid; v < n; v += nt) {
+                        float x[K];
+                        ldk<K>(t.xs + (size_t)v * K, x);
+#pragma unroll
+                        for (int r = 0; r < K; ++r) x[r] = wrap_c(__fadd_rn(x[r], t.acc[(size_t)v * K + r]));
+                        stk<K>(t.xs + (size_t)v * K, x);
                     }
                     __syncthreads();
                 }
-            } else {
-                // simultaneous generalized-gradient step over all edges (eq. (8))
-                for (int k = tid; k < n * K; k += nt) acc[k] = 0.0f;
-                __syncthreads();
-                for (int c = 0; c < a.C; ++c) {
-                    const int e1 = a.off[c + 1];
-                    for (int e = a.off[c] + tid; e < e1; e += nt) {
-                        const uint32_t rec = __ldg(a.ij + e);
-                        const float aw = at.x * (float)__ldg(a.w + e);
-                        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
-                        float xi[K], xj[K];
-                        ldk<K>(xs + (size_t)i * K, xi);
-                        ldk<K>(xs + (size_t)j * K, xj);
-#pragma unroll
-                        for (int r = 0; r < K; ++r) {
-                            const float d = __fadd_rn(xi[r], -xj[r]);
-                            const float m = __fadd_rn(d, -rint_fast(d));
-                            const float st = (m >= 0.0f) ? aw : -aw;
-                            acc[(size_t)i * K + r] += st;
-                            acc[(size_t)j * K + r] -= st;
-                        }
+                if (dwt) {
+                    if (a.C == 0) __syncthreads();
+                    for (int v = tid; v < n; v += nt) {
+                        float x[K];
+                        ldk<K>(t.xs + (size_t)v * K, x);
+                        dwt_apply<K>(x, t.thc, W2, at.y);
+                        stk<K>(t.xs + (size_t)v * K, x);
                     }
-                    __syncthreads();  // a colour is a matching: no two threads share a vertex
+                    __syncthreads();
                 }
-                for (int v = tid; v < n; v += nt) {
-                    float x[K];
-                    ldk<K>(xs + (size_t)v * K, x);
-#pragma unroll
-                    for (int r = 0; r < K; ++r) x[r] = wrap_c(__fadd_rn(x[r], acc[(size_t)v * K + r]));
-                    stk<K>(xs + (size_t)v * K, x);
-                }
-                __syncthreads();
-            }
-            if (dwt) {
-                if (a.C == 0) __syncthreads();
-                // dual window twist: windows [th - W/2, th + W/2) and its antipode;
-                // inside <=> ((x - th + W/2) mod 1/2) < W
-                const float step = at.y;
-                for (int v = tid; v < n; v += nt) {
-                    float x[K];
-                    ldk<K>(xs + (size_t)v * K, x);
-#pragma unroll
-                    for (int r = 0; r < K; ++r) {
-                        const float y = 2.0f * __fadd_rn(__fadd_rn(x[r], -th[r]), hw);
-                        const float u = __fadd_rn(y, -rint_fast(y));
-                        const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
-                        if (in) x[r] = wrap_c(__fadd_rn(x[r], step));
-                    }
-                    stk<K>(xs + (size_t)v * K, x);
-                }
-                __syncthreads();
             }
             if (dwt_on && ++phase == a.dwt_period) phase = 0;
         }
-
-        // ---- bisector readout with exact integer cuts (Alg. 1 final loop)
-        if (sg.flags & SEG_READOUT) {
-            for (int k = tid; k < K * (P + 1); k += nt) D[k] = 0;
-            __syncthreads();
-            int base[K];
-#pragma unroll
-            for (int r = 0; r < K; ++r) base[r] = 0;
-            const int m = a.off[a.C];
-            for (int e = tid; e < m; e += nt) {
-                const uint32_t rec = __ldg(a.ij + e);
-                const int wv = (int)__ldg(a.w + e);
-                const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
-                float xi[K], xj[K];
-                ldk<K>(xs + (size_t)i * K, xi);
-                ldk<K>(xs + (size_t)j * K, xj);
-#pragma unroll
-                for (int r = 0; r < K; ++r) {
-                    // spin of v at bisector p: [p < f_v] xor h_v, with h_v the top bit
-                    // of q_v and f_v = #{p : floor(p 2^31 / P) <= q_v mod 2^31}
-                    const uint32_t qi = phase_q(xi[r]), qj = phase_q(xj[r]);
-                    const int fi = (int)(((uint64_t)((qi & 0x7FFFFFFFu) + 1u) * (uint64_t)P +
-                                          0x7FFFFFFFull) >> 31);
-                    const int fj = (int)(((uint64_t)((qj & 0x7FFFFFFFu) + 1u) * (uint64_t)P +
-                                          0x7FFFFFFFull) >> 31);
-                    const int lo = min(fi, fj), hi = max(fi, fj);
-                    int *Dr = D + r * (P + 1);
-                    if ((qi >> 31) == (qj >> 31)) {
-                        if (lo < hi) {  // cut for p in [lo, hi)
-                            atomicAdd(Dr + lo, wv);
-                            atomicAdd(Dr + hi, -wv);
-                        }
-                    } else {  // cut for p in [0, lo) and [hi, P)
-                        base[r] += wv;
-                        if (lo < P) atomicAdd(Dr + lo, -wv);
-                        if (hi < P) atomicAdd(Dr + hi, wv);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < K; ++r) {
-                int b = base[r];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
-                if ((tid & 31) == 0 && b) atomicAdd(D + r * (P + 1), b);
-            }
-            __syncthreads();
-            if (tid < K && rep0 + tid < (uint32_t)a.replicas) {
-                const int *Dr = D + tid * (P + 1);
-                long long accv = 0, best = LLONG_MIN;
-                int bp = 0;
-                for (int p = 0; p < P; ++p) {
-                    accv += Dr[p];
-                    if (accv > best) { best = accv; bp = p; }
-                }
-                a.cut[rep0 + tid] = best;
-                a.bestp[rep0 + tid] = bp;
-            }
-        }
-
-        // ---- store / publish the tile's state
-        if (sg.flags & SEG_STORE) {
-            const uint4 *src = reinterpret_cast<const uint4 *>(xs);
-            uint4 *dst = reinterpret_cast<uint4 *>(gst);
-            for (size_t k = tid; k < vec_bytes / 16; k += nt) __stcg(dst + k, src[k]);
-            __threadfence();
-        }
-        __syncthreads();
-        if ((sg.flags & SEG_SIGNAL) && tid == 0) atomicExch(&a.ready[sg.tile], (int)sg.s_end);
+        seg_end<Store, K>(a, sg, t);
     }
 }
 
@@ -438,10 +597,10 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const FinalArgs a)
 }
 
 // ---------------------------------------------------------------- host side
-template <typename Store, int K, bool A>
+template <typename Store, int K, int M>
 static int launch_one(const LaunchCfg &cfg, const KernelArgs &a, void *stream)
 {
-    auto fn = sweep_kernel<Store, K, A>;
+    auto fn = sweep_kernel<Store, K, M>;
     static size_t set_bytes = 0;
     if (cfg.smem > 48 * 1024 && cfg.smem > set_bytes) {
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cfg.smem) !=
@@ -459,10 +618,10 @@ static int launch_one(const LaunchCfg &cfg, const KernelArgs &a, void *stream)
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-template <typename Store, int K, bool A>
+template <typename Store, int K, int M>
 static int occ_one(int threads, size_t smem)
 {
-    auto fn = sweep_kernel<Store, K, A>;
+    auto fn = sweep_kernel<Store, K, M>;
     if (smem > 48 * 1024)
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess)
@@ -473,39 +632,46 @@ static int occ_one(int threads, size_t smem)
     return blocks;
 }
 
-#define COSM_DISPATCH(STORAGE, K, ACC, CALL)                                       \
-    do {                                                                           \
-        if ((STORAGE) == 0) {                                                      \
-            if ((K) == 1) { if (ACC) return CALL(float, 1, true); return CALL(float, 1, false); } \
-            if ((K) == 2) { if (ACC) return CALL(float, 2, true); return CALL(float, 2, false); } \
-            if ((K) == 4) { if (ACC) return CALL(float, 4, true); return CALL(float, 4, false); } \
-        } else {                                                                   \
-            if ((K) == 2) { if (ACC) return CALL(__half, 2, true); return CALL(__half, 2, false); } \
-            if ((K) == 4) { if (ACC) return CALL(__half, 4, true); return CALL(__half, 4, false); } \
-            if ((K) == 8) { if (ACC) return CALL(__half, 8, true); return CALL(__half, 8, false); } \
-        }                                                                          \
+#define COSM_DISPATCH_M(T, KK, MODE, CALL)                 \
+    do {                                                   \
+        if ((MODE) == MODE_GENERAL) return CALL(T, KK, 0); \
+        if ((MODE) == MODE_ACCUM) return CALL(T, KK, 1);   \
+        if ((MODE) == MODE_LATTICE2D) return CALL(T, KK, 2); \
     } while (0)
 
-size_t sweep_smem_bytes(int storage, int K, int n, int P, bool accum)
+#define COSM_DISPATCH(STORAGE, K, MODE, CALL)                       \
+    do {                                                            \
+        if ((STORAGE) == 0) {                                       \
+            if ((K) == 1) COSM_DISPATCH_M(float, 1, MODE, CALL);    \
+            if ((K) == 2) COSM_DISPATCH_M(float, 2, MODE, CALL);    \
+            if ((K) == 4) COSM_DISPATCH_M(float, 4, MODE, CALL);    \
+        } else {                                                    \
+            if ((K) == 2) COSM_DISPATCH_M(__half, 2, MODE, CALL);   \
+            if ((K) == 4) COSM_DISPATCH_M(__half, 4, MODE, CALL);   \
+            if ((K) == 8) COSM_DISPATCH_M(__half, 8, MODE, CALL);   \
+        }                                                           \
+    } while (0)
+
+size_t sweep_smem_bytes(int storage, int K, int n, int P, int mode)
 {
-#define SMEM_CALL(T, KK, A) smem_bytes<T, KK>(n, P, A)
-    COSM_DISPATCH(storage, K, accum, SMEM_CALL);
+#define SMEM_CALL(T, KK, M) smem_bytes<T, KK>(n, P, (M) == MODE_ACCUM)
+    COSM_DISPATCH(storage, K, mode, SMEM_CALL);
 #undef SMEM_CALL
     return 0;
 }
 
-int sweep_occupancy(int storage, int K, bool accum, int threads, size_t smem)
+int sweep_occupancy(int storage, int K, int mode, int threads, size_t smem)
 {
-#define OCC_CALL(T, KK, A) occ_one<T, KK, A>(threads, smem)
-    COSM_DISPATCH(storage, K, accum, OCC_CALL);
+#define OCC_CALL(T, KK, M) occ_one<T, KK, M>(threads, smem)
+    COSM_DISPATCH(storage, K, mode, OCC_CALL);
 #undef OCC_CALL
     return 0;
 }
 
-int sweep_launch(const LaunchCfg &cfg, bool accum, const KernelArgs &a, void *stream)
+int sweep_launch(const LaunchCfg &cfg, const KernelArgs &a, void *stream)
 {
-#define LAUNCH_CALL(T, KK, A) launch_one<T, KK, A>(cfg, a, stream)
-    COSM_DISPATCH(cfg.storage, cfg.K, accum, LAUNCH_CALL);
+#define LAUNCH_CALL(T, KK, M) launch_one<T, KK, M>(cfg, a, stream)
+    COSM_DISPATCH(cfg.storage, cfg.K, cfg.mode, LAUNCH_CALL);
 #undef LAUNCH_CALL
     return -1;
 }
@@ -517,6 +683,7 @@ int finalize_launch(const FinalArgs &a, void *stream)
 }
 
 }  // namespace cosm
+
 
 // ---------------------------------------------------------------- SMEM probe
 namespace cosm {

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <unordered_map>
 #include <cstdlib>
 #include <cstring>
 #include <string>
@@ -69,6 +70,9 @@ struct cosm_handle {
     DevBuf<uint32_t> d_ij;
     DevBuf<int8_t> d_w;
     DevBuf<int32_t> d_orig;
+    int mode = MODE_GENERAL_;       // kernel variant
+    int32_t Q = 0, Wd = 0;          // 2D lattice geometry
+    DevBuf<uint32_t> d_wbits;       // 2D lattice weight bits
     // per run
     DevBuf<unsigned char> d_state;
     DevBuf<int64_t> d_cut;
@@ -193,7 +197,58 @@ extern "C" void cosm_destroy(cosm_handle *h)
     h->d_cut.release(); h->d_bestp.release(); h->d_alpha.release(); h->d_segs.release();
     h->d_segoff.release(); h->d_ready.release(); h->d_err.release(); h->d_best.release();
     h->d_spins.release();
+    h->d_wbits.release();
     delete h;
+}
+
+// The implicit-index 2D lattice kernel applies when the graph is an
+// even-sided torus given with the regular 4-colour pattern, all weights are
+// +-1 and the update is the sequential one. It walks eight passes (colour c,
+// pair-set ps) over sublattice slot pairs; this builds the weight bit of
+// every pass position from the edge list.
+static int setup_lattice2d(cosm_handle *h)
+{
+    const Graph &g = h->g;
+    h->mode = (h->prm.flags & COSM_NO_SCS) ? MODE_ACCUM_ : MODE_GENERAL_;
+    if (std::getenv("COSM_NO_LATTICE")) return COSM_OK;
+    if (!h->lattice || g.dims[2] != 0 || h->mode != MODE_GENERAL_ || h->C != 4) return COSM_OK;
+    for (int64_t e = 0; e < g.m; ++e)
+        if (g.w[(size_t)e] != 1 && g.w[(size_t)e] != -1) return COSM_OK;
+    std::vector<int32_t> pat((size_t)g.m);
+    if (color_torus2d(g.dims[0], g.dims[1], g.m, g.src.data(), g.dst.data(), pat.data()) != 0)
+        return COSM_OK;
+    if (pat != g.color) return COSM_OK;  // another colour order changes the dynamics
+    const int32_t Q = g.n / 4, Wd = g.dims[1] / 2;
+    std::unordered_map<int64_t, int32_t> wmap;
+    wmap.reserve((size_t)g.m * 2);
+    for (int64_t e = 0; e < g.m; ++e)
+        wmap[(int64_t)g.src[(size_t)e] * g.n + g.dst[(size_t)e]] = g.w[(size_t)e];
+    // (first group, second group, partner rule) of the eight passes
+    const int32_t pass[8][3] = {{0, 1, 0}, {2, 3, 0}, {1, 0, 1}, {3, 2, 1},
+                                {0, 2, 0}, {1, 3, 0}, {2, 0, 3}, {3, 1, 3}};
+    std::vector<uint32_t> bits(((size_t)8 * Q + 31) / 32, 0u);
+    for (int p = 0; p < 8; ++p) {
+        for (int32_t f = 0; f < Q; ++f) {
+            int32_t q = f;
+            if (pass[p][2] == 1) q = (f % Wd == Wd - 1) ? f + 1 - Wd : f + 1;
+            if (pass[p][2] == 3) q = (f + Wd) % Q;
+            const int32_t a = h->orig_of[(size_t)(pass[p][0] * Q + f)];
+            const int32_t b = h->orig_of[(size_t)(pass[p][1] * Q + q)];
+            auto it = wmap.find((int64_t)std::min(a, b) * g.n + std::max(a, b));
+            if (it == wmap.end()) return fail(COSM_ERR_INVALID_ARG, "lattice pass edge missing");
+            if (it->second == -1) {
+                const size_t idx = (size_t)p * Q + f;
+                bits[idx >> 5] |= 1u << (idx & 31);
+            }
+        }
+    }
+    int rc = h->d_wbits.ensure(bits.size());
+    if (rc) return rc;
+    CK(cudaMemcpy(h->d_wbits.p, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice));
+    h->Q = Q;
+    h->Wd = Wd;
+    h->mode = MODE_LATTICE2D_;
+    return COSM_OK;
 }
 
 extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm_handle **out)
@@ -281,6 +336,10 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
         cosm_destroy(h);
         return fail(COSM_ERR_CUDA, "copying the graph to the device failed");
     }
+    if ((rc = setup_lattice2d(h))) {
+        cosm_destroy(h);
+        return rc;
+    }
     *out = h;
     return COSM_OK;
 }
@@ -298,7 +357,7 @@ static int env_int(const char *name, int dflt)
 static int choose_layout(cosm_handle *h, int replicas)
 {
     const cosm_params &p = h->prm;
-    const bool accum = (p.flags & COSM_NO_SCS) != 0;
+    const int mode = h->mode;
     const int P = p.n_bisectors;
     int max_ec = 0;
     for (int c = 0; c < h->C; ++c) max_ec = std::max(max_ec, h->off[c + 1] - h->off[c]);
@@ -310,14 +369,18 @@ static int choose_layout(cosm_handle *h, int replicas)
     for (int k = 0; k < 3; ++k) {
         const int K = Ks[k];
         if (forceK && K != forceK) continue;
-        const size_t smem = sweep_smem_bytes(p.storage, K, h->g.n, P, accum);
+        const size_t smem = sweep_smem_bytes(p.storage, K, h->g.n, P, mode);
         if (smem > 227 * 1024) continue;
         int T = forceT ? forceT : std::min(1024, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
         if (!forceT && T > 512) T = 512;
-        int occ = sweep_occupancy(p.storage, K, accum, T, smem);
-        while (occ == 0 && T > 64 && !forceT) {
+        // the lattice kernel keeps one weight bit per pass item in a 32-bit
+        // register: at most 32 items per thread and pass
+        if (mode == MODE_LATTICE2D_ && !forceT) T = std::max(T, ((h->Q + 31) / 32 + 31) / 32 * 32);
+        if (mode == MODE_LATTICE2D_ && (h->Q + T - 1) / T > 32) continue;
+        int occ = sweep_occupancy(p.storage, K, mode, T, smem);
+        while (occ == 0 && T > 64 && !forceT && !(mode == MODE_LATTICE2D_ && (h->Q + T / 2 - 1) / (T / 2) > 32)) {
             T /= 2;
-            occ = sweep_occupancy(p.storage, K, accum, T, smem);
+            occ = sweep_occupancy(p.storage, K, mode, T, smem);
         }
         if (occ == 0) continue;
         const long tiles = (replicas + K - 1) / K;
@@ -335,7 +398,7 @@ static int choose_layout(cosm_handle *h, int replicas)
     h->K = bestK;
     h->threads = bestT;
     h->occupancy = bestOcc;
-    h->smem = sweep_smem_bytes(p.storage, bestK, h->g.n, P, accum);
+    h->smem = sweep_smem_bytes(p.storage, bestK, h->g.n, P, mode);
     const size_t esz = p.storage == COSM_F32 ? 4 : 2;
     h->tile_stride = (int64_t)(((size_t)h->g.n * bestK * esz + 15) / 16 * 16 / esz);
     return COSM_OK;
@@ -376,6 +439,9 @@ static KernelArgs base_args(cosm_handle *h)
     a.wait_limit_ns = (uint64_t)env_int("COSM_WAIT_LIMIT_S", 20) * 1000000000ull;
     a.cut = h->d_cut.p;
     a.bestp = h->d_bestp.p;
+    a.wbits = h->d_wbits.p;
+    a.Q = h->Q;
+    a.Wd = h->Wd;
     return a;
 }
 
@@ -519,9 +585,9 @@ extern "C" int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64
     a.S = sweeps;
     a.segs = h->d_segs.p;
     a.seg_off = h->d_segoff.p;
-    LaunchCfg cfg{h->prm.storage, h->K, h->threads, (int)(h->h_segoff.size() - 1), h->smem, waits};
+    LaunchCfg cfg{h->mode, h->prm.storage, h->K, h->threads, (int)(h->h_segoff.size() - 1), h->smem, waits};
     h->grid = cfg.grid;
-    if (sweep_launch(cfg, (h->prm.flags & COSM_NO_SCS) != 0, a, st))
+    if (sweep_launch(cfg, a, st))
         return fail(COSM_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(cudaGetLastError()));
     if ((rc = launch_finalize(h, st))) return rc;
     h->stream = st;
@@ -668,9 +734,9 @@ static int launch_on_state(cosm_handle *h, int32_t flags, int64_t s0, int64_t s1
     a.S = s1;
     a.segs = h->d_segs.p;
     a.seg_off = h->d_segoff.p;
-    LaunchCfg cfg{h->prm.storage, h->K, h->threads, (int)tiles, h->smem, false};
+    LaunchCfg cfg{h->mode, h->prm.storage, h->K, h->threads, (int)tiles, h->smem, false};
     h->grid = cfg.grid;
-    if (sweep_launch(cfg, (h->prm.flags & COSM_NO_SCS) != 0, a, st))
+    if (sweep_launch(cfg, a, st))
         return fail(COSM_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(cudaGetLastError()));
     h->stream = st;
     return COSM_OK;
@@ -719,7 +785,7 @@ extern "C" int cosm_layout(cosm_handle *h, int32_t out[8])
     out[1] = h->threads;
     out[2] = (int32_t)h->smem;
     out[3] = h->occupancy;
-    out[4] = h->lattice ? 1 : 0;
+    out[4] = h->mode == MODE_LATTICE2D_ ? 2 : (h->lattice ? 1 : 0);
     out[5] = h->grid;
     out[6] = h->launches;
     out[7] = h->C;
