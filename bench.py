@@ -214,14 +214,14 @@ def run_ours(args):
     e2e_times = []
     h2d = inst.src.nbytes + inst.dst.nbytes + inst.w.nbytes + (col.nbytes if col is not None else 0)
     d2h = inst.n + 16 + 8 * R
-    for k in range(max(1, args.e2e_steps)):
+    for k in range(args.e2e_steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cosm.solve(inst.n, inst.src, inst.dst, inst.w, S, R, seed + 77 * (k + 1), color=col,
                    n_colors=C, dims=inst.dims, storage=storage, replica_cuts=True, **prm)
         e2e_times.append(time.perf_counter() - t0)
-    e2e_t = sum(e2e_times) / len(e2e_times)
-    if ws > 1:
+    e2e_t = sum(e2e_times) / len(e2e_times) if e2e_times else None
+    if ws > 1 and e2e_t is not None:
         tt = torch.tensor([e2e_t], device="cuda")
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         e2e_t = float(tt.item())
@@ -244,16 +244,8 @@ def run_ours(args):
                "t_trial_s": t_trial, "TTT_s": t_trial * r if math.isfinite(r) else None,
                "best_cut": int(allc.max())}
 
-    # ---- roofline of the sweep kernel (shared-memory bound)
-    bpc, smem_gbps = cosm.probe_smem(4096)
-    b = 4 if storage == cosm.F32 else 2
-    per_update = 4 * b + (2 * b * inst.n) / (inst.m * prm["dwt_period"])
-    achieved = per_update * updates / t_step / 1e9
-    peaks = _peaks()
-    roof = {"bound": "smem", "achieved": achieved, "peak": smem_gbps, "unit": "GB/s",
-            "frac": achieved / smem_gbps, "traffic": None,
-            "peak_source": f"measured shared-memory read bandwidth ({bpc:.1f} B/clk/SM)",
-            "bytes_per_update": per_update}
+    # ---- roofline of the sweep kernel: shared memory and FP32 issue
+    roof = roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks)
 
     line = {
         "metric": "edge-replica updates/s (20k-spin 2D +-1 glass, plain FP32 Cosm)",
@@ -267,8 +259,9 @@ def run_ours(args):
                    "replicas_per_cta": layout["K"], "threads_per_cta": layout["threads"],
                    "ctas": layout["grid"], "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas sharded over {ws} GPU(s), no collective on the data path"},
-        "e2e": {"value": updates * ws / e2e_t, "unit": "updates/s", "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h, "api": "cosm_solve (host buffers)"},
+        "e2e": None if e2e_t is None else {
+            "value": updates * ws / e2e_t, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "api": "cosm_solve (host buffers)"},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "roofline": roof,
@@ -282,6 +275,48 @@ def run_ours(args):
     if ws > 1:
         dist.destroy_process_group()
     return line
+
+
+# Algorithmic FP32 operations of one edge-replica update (eq. (6) on the
+# minimum angular difference): difference, rounding to the nearest turn,
+# subtraction, sign select, two phase updates, two wraps (round + subtract).
+ALU_OPS_PER_UPDATE = 10
+FP32_LANES_PER_SM = 128
+
+
+def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks):
+    """Shared-memory and FP32-issue rooflines of the sweep kernel.
+
+    Shared-memory bytes per update: the implicit-index lattice kernel loads
+    and stores each phase once per 2x2 block, i.e. 2 phases moved per edge
+    (2b bytes, b = bytes per phase, DWT fused); the edge-list kernel loads
+    and stores both endpoints per edge (4b) plus a DWT pass over all phases
+    every dwt_period sweeps (2b n / (m dwt_period)). The kernel that
+    dominates the step is the sweep kernel (one launch per step; the
+    finaliser is microseconds), so the step time is its launch duration."""
+    import torch
+    bpc, smem_gbps = cosm.probe_smem(4096)
+    b = 4 if storage == cosm.F32 else 2
+    if layout["lattice"] == 2:
+        per_update = 2.0 * b
+    else:
+        per_update = 4.0 * b + (2.0 * b * inst.n) / (inst.m * max(1, prm["dwt_period"]))
+    smem_ach = per_update * updates / t_step / 1e9
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = clocks.get("sm_mhz") or 2070.0
+    alu_peak = FP32_LANES_PER_SM * props.multi_processor_count * mhz * 1e6 / 1e12
+    alu_ach = ALU_OPS_PER_UPDATE * updates / t_step / 1e12
+    smem = {"bound": "smem", "achieved": smem_ach, "peak": smem_gbps, "unit": "GB/s",
+            "frac": smem_ach / smem_gbps, "traffic": None, "bytes_per_update": per_update,
+            "peak_source": f"measured shared-memory read bandwidth ({bpc:.1f} B/clk/SM)"}
+    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s",
+           "frac": alu_ach / alu_peak, "traffic": None, "ops_per_update": ALU_OPS_PER_UPDATE,
+           "peak_source": f"{FP32_LANES_PER_SM} FP32 lanes/SM x {props.multi_processor_count} SMs "
+                          f"x {mhz:.0f} MHz (median sampled SM clock)"}
+    main, other = (alu, smem) if alu["frac"] >= smem["frac"] else (smem, alu)
+    main = dict(main)
+    main["other"] = other
+    return main
 
 
 # ---------------------------------------------------------------------- oracle
@@ -348,7 +383,7 @@ def main(argv=None):
     ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
     ap.add_argument("--replicas", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=0)
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1, help="0 skips the end-to-end leg")
     ap.add_argument("--cpu-updates", type=float, default=6e9,
                     help="edge-replica updates in the bounded oracle sample")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

@@ -183,9 +183,11 @@ int cosm_color_greedy(int32_t n, int64_t m, const int32_t *src, const int32_t *d
 int cosm_color_misra_gries(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                            int32_t *color, int32_t *n_colors);
 
-/* Regular lattice patterns (Section II-B, Appendix B): 2D torus, 4 colours
- * (horizontal edges from even/odd columns, vertical from even/odd rows);
- * 3D torus, 6 colours (axis x parity). Sides must be even and >= 4. */
+/* Regular lattice patterns (Section II-B, Appendix B). 2D torus, 4 colours
+ * in the order: horizontal edges leaving an even column, vertical edges
+ * leaving an even row, horizontal from an odd column, vertical from an odd
+ * row (each consecutive pair acts inside disjoint 2x2 blocks). 3D torus, 6
+ * colours: 3 * parity + axis. Sides must be even and >= 4. */
 int cosm_color_torus2d(int32_t L1, int32_t L2, int64_t m, const int32_t *src, const int32_t *dst,
                        int32_t *color);
 int cosm_color_torus3d(int32_t L1, int32_t L2, int32_t L3, int64_t m, const int32_t *src,

@@ -409,9 +409,13 @@ int32_t orc_color_greedy(int32_t n, int64_t m, const int32_t *src, const int32_t
 }
 
 /* Regular 4-colour pattern of a 2D torus with even sides (Section II-B,
- * Appendix B): colour 0/1 = horizontal edges leaving an even/odd column,
- * colour 2/3 = vertical edges leaving an even/odd row. Vertex v = r L2 + c.
- * Returns 4, or -1 if an edge is not a torus edge or a side is odd. */
+ * Appendix B). The paper fixes the pattern (horizontal and vertical edges,
+ * each split by the parity of the lower end) but not the order of the
+ * colours; the reading taken here is: colour 0 = horizontal edges leaving an
+ * even column, 1 = vertical edges leaving an even row, 2 = horizontal edges
+ * leaving an odd column, 3 = vertical edges leaving an odd row. Vertex
+ * v = r L2 + c. Returns 4, or -1 if an edge is not a torus edge or a side is
+ * odd. */
 int32_t orc_color_torus2d(int32_t L1, int32_t L2, int64_t m, const int32_t *src, const int32_t *dst,
                           int32_t *color)
 {
@@ -419,17 +423,19 @@ int32_t orc_color_torus2d(int32_t L1, int32_t L2, int64_t m, const int32_t *src,
     for (int64_t e = 0; e < m; ++e) {
         int32_t a = src[e], b = dst[e];
         int32_t ra = a / L2, ca = a % L2, rb = b / L2, cb = b % L2;
-        if (ra == rb && (ca + 1) % L2 == cb) color[e] = (ca & 1);
-        else if (ra == rb && (cb + 1) % L2 == ca) color[e] = (cb & 1);
-        else if (ca == cb && (ra + 1) % L1 == rb) color[e] = 2 + (ra & 1);
-        else if (ca == cb && (rb + 1) % L1 == ra) color[e] = 2 + (rb & 1);
+        if (ra == rb && (ca + 1) % L2 == cb) color[e] = (ca & 1) ? 2 : 0;
+        else if (ra == rb && (cb + 1) % L2 == ca) color[e] = (cb & 1) ? 2 : 0;
+        else if (ca == cb && (ra + 1) % L1 == rb) color[e] = (ra & 1) ? 3 : 1;
+        else if (ca == cb && (rb + 1) % L1 == ra) color[e] = (rb & 1) ? 3 : 1;
         else return -1;
     }
     return 4;
 }
 
-/* 3D torus, six colours: axis a (0,1,2) and parity of the lower end's
- * coordinate along a. Vertex v = (i L2 + j) L3 + k. */
+/* 3D torus, six colours: colour = 3 (parity) + axis, where axis a (0,1,2)
+ * is the edge's direction and parity that of the lower end's coordinate
+ * along a (same ordering reading as in 2D: all even classes first).
+ * Vertex v = (i L2 + j) L3 + k. */
 int32_t orc_color_torus3d(int32_t L1, int32_t L2, int32_t L3, int64_t m, const int32_t *src,
                           const int32_t *dst, int32_t *color)
 {
@@ -448,8 +454,8 @@ int32_t orc_color_torus3d(int32_t L1, int32_t L2, int32_t L3, int64_t m, const i
             int same = 1;
             for (int b = 0; b < 3; ++b) if (b != a && co[0][b] != co[1][b]) same = 0;
             if (!same) continue;
-            if ((co[0][a] + 1) % L[a] == co[1][a]) { color[e] = 2 * a + (co[0][a] & 1); found = 1; }
-            else if ((co[1][a] + 1) % L[a] == co[0][a]) { color[e] = 2 * a + (co[1][a] & 1); found = 1; }
+            if ((co[0][a] + 1) % L[a] == co[1][a]) { color[e] = 3 * (co[0][a] & 1) + a; found = 1; }
+            else if ((co[1][a] + 1) % L[a] == co[0][a]) { color[e] = 3 * (co[1][a] & 1) + a; found = 1; }
         }
         if (!found) return -1;
     }

@@ -210,10 +210,12 @@ int color_torus2d(int32_t L1, int32_t L2, int64_t m, const int32_t *src, const i
         const int32_t a = src[e], b = dst[e];
         if (b >= L1 * L2) return COSM_ERR_INVALID_ARG;
         const int32_t ra = a / L2, ca = a % L2, rb = b / L2, cb = b % L2;
-        if (ra == rb && (ca + 1) % L2 == cb) color[e] = ca & 1;
-        else if (ra == rb && (cb + 1) % L2 == ca) color[e] = cb & 1;
-        else if (ca == cb && (ra + 1) % L1 == rb) color[e] = 2 + (ra & 1);
-        else if (ca == cb && (rb + 1) % L1 == ra) color[e] = 2 + (rb & 1);
+        // order: even-column horizontal, even-row vertical, odd-column
+        // horizontal, odd-row vertical (consecutive pairs act on 2x2 blocks)
+        if (ra == rb && (ca + 1) % L2 == cb) color[e] = (ca & 1) ? 2 : 0;
+        else if (ra == rb && (cb + 1) % L2 == ca) color[e] = (cb & 1) ? 2 : 0;
+        else if (ca == cb && (ra + 1) % L1 == rb) color[e] = (ra & 1) ? 3 : 1;
+        else if (ca == cb && (rb + 1) % L1 == ra) color[e] = (rb & 1) ? 3 : 1;
         else return COSM_ERR_INVALID_ARG;
     }
     return COSM_OK;
@@ -240,8 +242,9 @@ int color_torus3d(int32_t L1, int32_t L2, int32_t L3, int64_t m, const int32_t *
             for (int b = 0; b < 3; ++b)
                 if (b != a && co[0][b] != co[1][b]) same = false;
             if (!same) continue;
-            if ((co[0][a] + 1) % L[a] == co[1][a]) c = 2 * a + (co[0][a] & 1);
-            else if ((co[1][a] + 1) % L[a] == co[0][a]) c = 2 * a + (co[1][a] & 1);
+            // all even classes (axes 0, 1, 2), then all odd classes
+            if ((co[0][a] + 1) % L[a] == co[1][a]) c = 3 * (co[0][a] & 1) + a;
+            else if ((co[1][a] + 1) % L[a] == co[0][a]) c = 3 * (co[1][a] & 1) + a;
         }
         if (c < 0) return COSM_ERR_INVALID_ARG;
         color[e] = c;

@@ -56,9 +56,10 @@ struct KernelArgs {
     uint64_t wait_limit_ns;
     int64_t *cut;         // [replicas] best cut
     int32_t *bestp;       // [replicas] best bisector
-    // 2D lattice mode: Q = n/4 slots per sublattice, Wd = L2/2 columns, and
-    // wbits bit (p*Q + f) = 1 when edge f of pass p has w = -1
-    const uint32_t *wbits;
+    // 2D lattice mode: Q = n/4 slots per sublattice, Wd = L2/2 columns;
+    // wnib[pass * Q + f] holds the weight bits of the four edges of 2x2
+    // block f in that pass (bit set: w = -1)
+    const uint8_t *wnib;
     int32_t Q;
     int32_t Wd;
 };

@@ -387,49 +387,156 @@ __device__ __forceinline__ void general_colour(const KernelArgs &a, Store *xs, i
     }
 }
 
-// 2D torus in the sublattice layout (groups A = (even r, even c), B = (even,
-// odd), C = (odd, even), D = (odd, odd), Q = n/4 slots each, row-major with
-// Wd = L2/2 columns). The regular colouring pairs group gp slot f with group
-// gq slot q(f): q = f (kMode 0), the next column with a row wrap (kMode 1),
-// or the next row with a torus wrap (kMode 3). At a wrap the second vertex
-// has the smaller original id, so the two roles of eq. (6) swap. Edge
-// indices are implicit; the +-1 weights come from a per-thread bit mask
-// (bit k set: w = -1 for this thread's k-th edge of the pass).
-template <typename Store, int K, int kMode>
-__device__ __forceinline__ void lattice_pass(Store *xs, int gp, int gq, uint32_t wm, float alpha, int Q,
-                                             int Wd, int m0, int dm, bool dwt, const float *thc,
-                                             float W2, float step)
+// Pair update of eq. (6) without the wrap: used inside a 2x2 block, whose
+// four phases are wrapped once when the block is written back. Between
+// wraps a phase moves by at most two steps, so |g| < 1 and FP32 keeps an
+// ulp of at most 2^-24 turn.
+template <int K>
+__device__ __forceinline__ void pair_update_nowrap(float (&xi)[K], float (&xj)[K], float aw)
 {
-    const int nt = blockDim.x;
-    int m = m0;
-    for (int f = threadIdx.x; f < Q; f += nt) {
-        int q = f;
-        bool swp = false;
-        if (kMode == 1) {
-            const bool end = (m == Wd - 1);
-            q = end ? f + 1 - Wd : f + 1;
-            swp = end;
-            m += dm;
-            if (m >= Wd) m -= Wd;
-        } else if (kMode == 3) {
-            q = f + Wd;
-            swp = q >= Q;
-            if (swp) q -= Q;
-        }
-        const float aw = (wm & 1u) ? -alpha : alpha;
-        wm >>= 1;
-        int i = gp + f, j = gq + q;
-        if (swp) { const int tmp = i; i = j; j = tmp; }
-        float xi[K], xj[K];
-        ldk<K>(xs + (size_t)i * K, xi);
-        ldk<K>(xs + (size_t)j * K, xj);
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const float d = __fadd_rn(xi[r], -xj[r]);
+        const float m = __fadd_rn(d, -rint_fast(d));
+        const float st = (m >= 0.0f) ? aw : -aw;
+        xi[r] = __fadd_rn(xi[r], st);
+        xj[r] = __fadd_rn(xj[r], -st);
+    }
+}
+
+// Binary16 storage: every phase write is a binary16 store of the wrapped
+// value, also between the two colours of a block, so each update there is
+// wrapped and rounded through binary16 at once.
+template <int K>
+__device__ __forceinline__ void round_f16(float (&x)[K])
+{
+#pragma unroll
+    for (int r = 0; r < K; r += 2) {
+        const float2 f = __half22float2(__floats2half2_rn(x[r], x[r + 1]));
+        x[r] = f.x;
+        x[r + 1] = f.y;
+    }
+}
+
+template <typename Store, int K>
+__device__ __forceinline__ void pair_block(float (&xi)[K], float (&xj)[K], float aw)
+{
+    if constexpr (sizeof(Store) == 4) {
+        pair_update_nowrap<K>(xi, xj, aw);
+    } else {
         pair_update<K>(xi, xj, aw);
+        round_f16<K>(xi);
+        round_f16<K>(xj);
+    }
+}
+
+// Oriented update: eq. (6)'s roles follow the original vertex ids; `swp`
+// marks an edge whose second slot holds the smaller id (torus wrap).
+template <typename Store, int K>
+__device__ __forceinline__ void pair_oriented(float (&x1)[K], float (&x2)[K], float aw, bool swp)
+{
+    if (swp) pair_block<Store, K>(x2, x1, aw);
+    else pair_block<Store, K>(x1, x2, aw);
+}
+
+template <int K>
+__device__ __forceinline__ void wrap_all(float (&x)[K])
+{
+#pragma unroll
+    for (int r = 0; r < K; ++r) x[r] = wrap_c(x[r]);
+}
+
+template <int K>
+__device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, float W2, float step)
+{
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const float y = fmaf(2.0f, x[r], thc[r]);
+        const float u = __fadd_rn(y, -rint_fast(y));
+        const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
+        if (in) x[r] = __fadd_rn(x[r], step);
+    }
+}
+
+// 2D torus in the sublattice layout: groups A = (even r, even c), B = (even,
+// odd), C = (odd, even), D = (odd, odd), Q = n/4 slots each, row-major with
+// Wd = L2/2 columns. With the colour order (even-column horizontal,
+// even-row vertical, odd-column horizontal, odd-row vertical), colours 0
+// and 1 act inside the 2x2 blocks {A[f], B[f], C[f], D[f]} and colours 2
+// and 3 inside the shifted blocks {D[f], C[g(f)], B[h(f)], A[g(h(f))]},
+// where g = next column (row wrap) and h = next row (torus wrap). A thread
+// loads a block, applies both colours in registers and stores it: every
+// vertex meets one edge of each colour inside its block. Edge indices are
+// implicit; weights are +-1 bits.
+template <typename Store, int K>
+__device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, float alpha, int Q)
+{
+    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+        const uint32_t wb = __ldg(wnib + f);
+        float xa[K], xb[K], xc[K], xd[K];
+        ldk<K>(xs + (size_t)f * K, xa);
+        ldk<K>(xs + (size_t)(Q + f) * K, xb);
+        ldk<K>(xs + (size_t)(2 * Q + f) * K, xc);
+        ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        // colour 0: A-B, C-D; colour 1: A-C, B-D (first slot = smaller id)
+        pair_block<Store, K>(xa, xb, (wb & 1u) ? -alpha : alpha);
+        pair_block<Store, K>(xc, xd, (wb & 2u) ? -alpha : alpha);
+        pair_block<Store, K>(xa, xc, (wb & 4u) ? -alpha : alpha);
+        pair_block<Store, K>(xb, xd, (wb & 8u) ? -alpha : alpha);
+        wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
+        stk<K>(xs + (size_t)f * K, xa);
+        stk<K>(xs + (size_t)(Q + f) * K, xb);
+        stk<K>(xs + (size_t)(2 * Q + f) * K, xc);
+        stk<K>(xs + (size_t)(3 * Q + f) * K, xd);
+    }
+}
+
+template <typename Store, int K>
+__device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
+                                               int m0, int dm, bool dwt, const float *thc, float W2,
+                                               float step)
+{
+    int m = m0;  // column of block f within its row
+    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+        const bool cw = (m == Wd - 1);      // next column wraps to column 0
+        const bool rw = (f >= Q - Wd);      // next row wraps to row 0
+        const int g = cw ? f + 1 - Wd : f + 1;
+        const int h = rw ? f + Wd - Q : f + Wd;
+        const int gh = rw ? g + Wd - Q : g + Wd;
+        m += dm;
+        if (m >= Wd) m -= Wd;
+        const uint32_t wb = __ldg(wnib + Q + f);
+        float xd[K], xc[K], xb[K], xa[K];
+        ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        ldk<K>(xs + (size_t)(2 * Q + g) * K, xc);
+        ldk<K>(xs + (size_t)(Q + h) * K, xb);
+        ldk<K>(xs + (size_t)gh * K, xa);
+        // colour 2: D-C, B-A (horizontal from odd columns)
+        pair_oriented<Store, K>(xd, xc, (wb & 1u) ? -alpha : alpha, cw);
+        pair_oriented<Store, K>(xb, xa, (wb & 2u) ? -alpha : alpha, cw);
+        // colour 3: D-B, C-A (vertical from odd rows)
+        pair_oriented<Store, K>(xd, xb, (wb & 4u) ? -alpha : alpha, rw);
+        pair_oriented<Store, K>(xc, xa, (wb & 8u) ? -alpha : alpha, rw);
         if (dwt) {
-            dwt_apply<K>(xi, thc, W2, step);
-            dwt_apply<K>(xj, thc, W2, step);
+            // the DWT follows the last colour of the sweep; every vertex is in
+            // exactly one shifted block
+            if constexpr (sizeof(Store) == 4) {
+                dwt_nowrap<K>(xd, thc, W2, step);
+                dwt_nowrap<K>(xc, thc, W2, step);
+                dwt_nowrap<K>(xb, thc, W2, step);
+                dwt_nowrap<K>(xa, thc, W2, step);
+            } else {
+                dwt_apply<K>(xd, thc, W2, step);
+                dwt_apply<K>(xc, thc, W2, step);
+                dwt_apply<K>(xb, thc, W2, step);
+                dwt_apply<K>(xa, thc, W2, step);
+            }
         }
-        stk<K>(xs + (size_t)i * K, xi);
-        stk<K>(xs + (size_t)j * K, xj);
+        wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
+        stk<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        stk<K>(xs + (size_t)(2 * Q + g) * K, xc);
+        stk<K>(xs + (size_t)(Q + h) * K, xb);
+        stk<K>(xs + (size_t)gh * K, xa);
     }
 }
 
@@ -447,20 +554,8 @@ __global__ void __launch_bounds__(512) sweep_kernel(const KernelArgs a)
     const bool dwt_on = !(a.flags & 1) && a.dwt_period > 0;
     const float W2 = 2.0f * a.window, hw = 0.5f * a.window;
 
-    // lattice: this thread's weight bits for the 8 (colour, pair-set) passes
-    uint32_t wm[8];
     int m0 = 0, dm = 0;
     if (kMode == MODE_LATTICE2D) {
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            uint32_t bits = 0;
-            int k = 0;
-            for (int f = tid; f < a.Q; f += nt, ++k) {
-                const uint32_t idx = (uint32_t)(p * a.Q + f);
-                bits |= ((__ldg(a.wbits + (idx >> 5)) >> (idx & 31)) & 1u) << k;
-            }
-            wm[p] = bits;
-        }
         m0 = tid % a.Wd;
         dm = nt % a.Wd;
     }
@@ -476,23 +571,11 @@ __global__ void __launch_bounds__(512) sweep_kernel(const KernelArgs a)
             if (dwt && tid < K)
                 t.thc[tid] = 2.0f * (hw - dwt_theta(a.seed, rep0 + tid, s));
             if (kMode == MODE_LATTICE2D) {
-                const int Q = a.Q, Wd = a.Wd;
-                // colour 0: horizontal edges from even columns (A-B, C-D)
-                lattice_pass<Store, K, 0>(t.xs, 0, Q, wm[0], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
-                lattice_pass<Store, K, 0>(t.xs, 2 * Q, 3 * Q, wm[1], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
+                // colours 0, 1 in the 2x2 blocks; colours 2, 3 (+ DWT) in the
+                // shifted blocks
+                block_pass_even<Store, K>(t.xs, a.wnib, at.x, a.Q);
                 __syncthreads();
-                // colour 1: horizontal edges from odd columns (B-A, D-C)
-                lattice_pass<Store, K, 1>(t.xs, Q, 0, wm[2], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
-                lattice_pass<Store, K, 1>(t.xs, 3 * Q, 2 * Q, wm[3], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
-                __syncthreads();
-                // colour 2: vertical edges from even rows (A-C, B-D)
-                lattice_pass<Store, K, 0>(t.xs, 0, 2 * Q, wm[4], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
-                lattice_pass<Store, K, 0>(t.xs, Q, 3 * Q, wm[5], at.x, Q, Wd, m0, dm, false, t.thc, W2, at.y);
-                __syncthreads();
-                // colour 3: vertical edges from odd rows (C-A, D-B); every vertex
-                // meets exactly one of them, so the DWT is applied right here
-                lattice_pass<Store, K, 3>(t.xs, 2 * Q, 0, wm[6], at.x, Q, Wd, m0, dm, dwt, t.thc, W2, at.y);
-                lattice_pass<Store, K, 3>(t.xs, 3 * Q, Q, wm[7], at.x, Q, Wd, m0, dm, dwt, t.thc, W2, at.y);
+                block_pass_odd<Store, K>(t.xs, a.wnib, at.x, a.Q, a.Wd, m0, dm, dwt, t.thc, W2, at.y);
                 __syncthreads();
             } else {
                 if (kMode == MODE_GENERAL) {

@@ -72,7 +72,7 @@ struct cosm_handle {
     DevBuf<int32_t> d_orig;
     int mode = MODE_GENERAL_;       // kernel variant
     int32_t Q = 0, Wd = 0;          // 2D lattice geometry
-    DevBuf<uint32_t> d_wbits;       // 2D lattice weight bits
+    DevBuf<uint8_t> d_wnib;         // 2D lattice block weight bits
     // per run
     DevBuf<unsigned char> d_state;
     DevBuf<int64_t> d_cut;
@@ -197,15 +197,16 @@ extern "C" void cosm_destroy(cosm_handle *h)
     h->d_cut.release(); h->d_bestp.release(); h->d_alpha.release(); h->d_segs.release();
     h->d_segoff.release(); h->d_ready.release(); h->d_err.release(); h->d_best.release();
     h->d_spins.release();
-    h->d_wbits.release();
+    h->d_wnib.release();
     delete h;
 }
 
 // The implicit-index 2D lattice kernel applies when the graph is an
 // even-sided torus given with the regular 4-colour pattern, all weights are
-// +-1 and the update is the sequential one. It walks eight passes (colour c,
-// pair-set ps) over sublattice slot pairs; this builds the weight bit of
-// every pass position from the edge list.
+// +-1 and the update is the sequential one. It walks 2x2 blocks in two
+// passes; this builds each block's four weight bits from the edge list, in
+// the kernel's edge order (even pass: A-B, C-D, A-C, B-D; odd pass: D-C,
+// B-A, D-B, C-A over the shifted block).
 static int setup_lattice2d(cosm_handle *h)
 {
     const Graph &g = h->g;
@@ -223,28 +224,28 @@ static int setup_lattice2d(cosm_handle *h)
     wmap.reserve((size_t)g.m * 2);
     for (int64_t e = 0; e < g.m; ++e)
         wmap[(int64_t)g.src[(size_t)e] * g.n + g.dst[(size_t)e]] = g.w[(size_t)e];
-    // (first group, second group, partner rule) of the eight passes
-    const int32_t pass[8][3] = {{0, 1, 0}, {2, 3, 0}, {1, 0, 1}, {3, 2, 1},
-                                {0, 2, 0}, {1, 3, 0}, {2, 0, 3}, {3, 1, 3}};
-    std::vector<uint32_t> bits(((size_t)8 * Q + 31) / 32, 0u);
-    for (int p = 0; p < 8; ++p) {
-        for (int32_t f = 0; f < Q; ++f) {
-            int32_t q = f;
-            if (pass[p][2] == 1) q = (f % Wd == Wd - 1) ? f + 1 - Wd : f + 1;
-            if (pass[p][2] == 3) q = (f + Wd) % Q;
-            const int32_t a = h->orig_of[(size_t)(pass[p][0] * Q + f)];
-            const int32_t b = h->orig_of[(size_t)(pass[p][1] * Q + q)];
-            auto it = wmap.find((int64_t)std::min(a, b) * g.n + std::max(a, b));
-            if (it == wmap.end()) return fail(COSM_ERR_INVALID_ARG, "lattice pass edge missing");
-            if (it->second == -1) {
-                const size_t idx = (size_t)p * Q + f;
-                bits[idx >> 5] |= 1u << (idx & 31);
-            }
+    auto weight = [&](int32_t slot_a, int32_t slot_b) {
+        const int32_t a = h->orig_of[(size_t)slot_a], b = h->orig_of[(size_t)slot_b];
+        auto it = wmap.find((int64_t)std::min(a, b) * g.n + std::max(a, b));
+        return it == wmap.end() ? 0 : it->second;
+    };
+    std::vector<uint8_t> nib((size_t)2 * Q, 0);
+    for (int32_t f = 0; f < Q; ++f) {
+        const int32_t A = f, B = Q + f, Cc = 2 * Q + f, D = 3 * Q + f;
+        const int32_t even[4][2] = {{A, B}, {Cc, D}, {A, Cc}, {B, D}};
+        const int32_t gcol = (f % Wd == Wd - 1) ? f + 1 - Wd : f + 1;
+        const int32_t hrow = (f + Wd) % Q, gh = (gcol + Wd) % Q;
+        const int32_t odd[4][2] = {{D, 2 * Q + gcol}, {Q + hrow, gh}, {D, Q + hrow}, {2 * Q + gcol, gh}};
+        for (int k = 0; k < 4; ++k) {
+            const int32_t we = weight(even[k][0], even[k][1]), wo = weight(odd[k][0], odd[k][1]);
+            if (we == 0 || wo == 0) return fail(COSM_ERR_INVALID_ARG, "lattice block edge missing");
+            if (we == -1) nib[(size_t)f] |= (uint8_t)(1u << k);
+            if (wo == -1) nib[(size_t)Q + f] |= (uint8_t)(1u << k);
         }
     }
-    int rc = h->d_wbits.ensure(bits.size());
+    int rc = h->d_wnib.ensure(nib.size());
     if (rc) return rc;
-    CK(cudaMemcpy(h->d_wbits.p, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->d_wnib.p, nib.data(), nib.size(), cudaMemcpyHostToDevice));
     h->Q = Q;
     h->Wd = Wd;
     h->mode = MODE_LATTICE2D_;
@@ -373,12 +374,9 @@ static int choose_layout(cosm_handle *h, int replicas)
         if (smem > 227 * 1024) continue;
         int T = forceT ? forceT : std::min(1024, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
         if (!forceT && T > 512) T = 512;
-        // the lattice kernel keeps one weight bit per pass item in a 32-bit
-        // register: at most 32 items per thread and pass
-        if (mode == MODE_LATTICE2D_ && !forceT) T = std::max(T, ((h->Q + 31) / 32 + 31) / 32 * 32);
-        if (mode == MODE_LATTICE2D_ && (h->Q + T - 1) / T > 32) continue;
+        if (mode == MODE_LATTICE2D_ && !forceT) T = std::min(512, std::max(64, (h->Q + 31) / 32 * 32));
         int occ = sweep_occupancy(p.storage, K, mode, T, smem);
-        while (occ == 0 && T > 64 && !forceT && !(mode == MODE_LATTICE2D_ && (h->Q + T / 2 - 1) / (T / 2) > 32)) {
+        while (occ == 0 && T > 64 && !forceT) {
             T /= 2;
             occ = sweep_occupancy(p.storage, K, mode, T, smem);
         }
@@ -439,7 +437,7 @@ static KernelArgs base_args(cosm_handle *h)
     a.wait_limit_ns = (uint64_t)env_int("COSM_WAIT_LIMIT_S", 20) * 1000000000ull;
     a.cut = h->d_cut.p;
     a.bestp = h->d_bestp.p;
-    a.wbits = h->d_wbits.p;
+    a.wnib = h->d_wnib.p;
     a.Q = h->Q;
     a.Wd = h->Wd;
     return a;

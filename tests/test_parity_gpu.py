@@ -198,21 +198,42 @@ def test_planted_optimum_reached(cosm, orc):
 
 
 def test_layouts_agree_bit_exact(cosm, orc):
-    # lattice relabel vs plain layout, and replicas per CTA, give the same trial
+    # replicas per CTA (K) never change a trial: within each kernel variant
+    # (implicit-index lattice blocks, general edge lists) results are
+    # bit-identical across K. The lattice kernel wraps a phase once per 2x2
+    # block instead of after every update, so the two variants agree to
+    # rounding per sweep (checked by the one-sweep parity tests), not bitwise.
     inst = instances.torus2d(16, 16, 6)
     col, C = orc.color_instance(inst)
-    res = []
-    for dims, K in ((True, 1), (False, 1), (True, 2), (False, 4)):
-        os.environ["COSM_K"] = str(K)
-        try:
-            s, _ = _solver(cosm, orc, inst, use_dims=dims, color=col, C=C)
-            s.run(300, 10, seed=8)
-            res.append((s.replica_cuts()[0], s.get_state()))
-        finally:
-            del os.environ["COSM_K"]
-    for cuts, x in res[1:]:
-        assert np.array_equal(cuts, res[0][0])
-        assert np.array_equal(x, res[0][1])
+    for dims, Ks, kind in ((True, (1, 2, 4), 2), (False, (1, 2, 4), 0)):
+        res = []
+        for K in Ks:
+            os.environ["COSM_K"] = str(K)
+            try:
+                s, _ = _solver(cosm, orc, inst, use_dims=dims, color=col, C=C)
+                s.run(300, 10, seed=8)
+                assert s.layout()["lattice"] == kind and s.layout()["K"] == K
+                res.append((s.replica_cuts()[0], s.get_state()))
+            finally:
+                del os.environ["COSM_K"]
+        for cuts, x in res[1:]:
+            assert np.array_equal(cuts, res[0][0])
+            assert np.array_equal(x, res[0][1])
+
+
+def test_lattice_kernel_needs_the_regular_pattern(cosm, orc):
+    inst = instances.torus2d(16, 16, 6)
+    col, C = orc.color_instance(inst)
+    s, _ = _solver(cosm, orc, inst, color=col, C=C)
+    assert s.layout()["lattice"] == 2
+    # the same partition with colours renumbered runs colours in another
+    # order, so it must take the general kernel
+    s2, _ = _solver(cosm, orc, inst, color=(col + 1) % 4, C=4)
+    assert s2.layout()["lattice"] == 1
+    # weights beyond +-1 also take the general kernel
+    w3 = instances.Instance(inst.n, inst.src, inst.dst, inst.w * 3, inst.dims)
+    s3, _ = _solver(cosm, orc, w3, color=col, C=C)
+    assert s3.layout()["lattice"] == 1
 
 
 def test_chunked_schedule_matches_single_segment(cosm, orc):
