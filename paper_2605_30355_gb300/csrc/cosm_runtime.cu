@@ -354,7 +354,7 @@ static int env_int(const char *name, int dflt)
 }
 
 // Replicas per CTA (K) and threads per CTA: maximise resident replicas per
-// SM, prefer the smaller tile on ties (more CTAs hide barrier latency).
+// SM (COSM_K / COSM_THREADS override for experiments).
 static int choose_layout(cosm_handle *h, int replicas)
 {
     const cosm_params &p = h->prm;
@@ -382,9 +382,12 @@ static int choose_layout(cosm_handle *h, int replicas)
         }
         if (occ == 0) continue;
         const long tiles = (replicas + K - 1) / K;
-        // resident replicas per SM, capped by what the run can fill
+        // resident replicas per SM, capped by what the run can fill; on a tie
+        // a larger tile amortises per-edge work when the run fills every CTA
+        // slot, a smaller one spreads a small run over more SMs
         const long resident = std::min<long>((long)occ * K, std::max<long>(1, tiles * K / h->num_sms));
-        const long score = resident * 1000 - K;
+        const bool full = tiles >= (long)occ * h->num_sms;
+        const long score = resident * 1000 + (full ? K : -K);
         if (score > bestScore) {
             bestScore = score;
             bestK = K;
