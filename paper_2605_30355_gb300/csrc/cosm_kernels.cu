@@ -387,25 +387,34 @@ __device__ __forceinline__ void general_colour(const KernelArgs &a, Store *xs, i
     }
 }
 
-// Pair update of eq. (6) without the wrap: used inside a 2x2 block, whose
-// four phases are wrapped once when the block is written back. Between
-// wraps a phase moves by at most two steps, so |g| < 1 and FP32 keeps an
-// ulp of at most 2^-24 turn.
+// Pair update inside a 2x2 block, for +-1 weights. x1, x2 are the block's
+// slots; eq. (6) takes x_i as the endpoint with the smaller original id,
+// which is x1 except at a torus wrap. With m = d - rint(d), d = x1 - x2, the
+// minimum angular difference (valid for any |d| < 2^22, so the phases may
+// stay unwrapped inside a block), the biased sign of eq. (4) gives
+//     x_i = x1:  the step on x1 is positive iff m >= 0
+//     x_i = x2:  the step on x1 is positive iff m > 0   (= -sgn_b(-m))
+// so one comparison threshold tz (0, or the least positive binary32 2^-149
+// for a wrap edge) covers both orientations. wneg: w = -1. Phases are
+// wrapped once per sweep, at the end of the odd pass: in between a phase
+// moves by at most a few steps, so |g| < 1 and binary32 keeps an ulp of at
+// most 2^-24 turn.
 template <int K>
-__device__ __forceinline__ void pair_update_nowrap(float (&xi)[K], float (&xj)[K], float aw)
+__device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float alpha, bool wneg, float tz)
 {
 #pragma unroll
     for (int r = 0; r < K; ++r) {
-        const float d = __fadd_rn(xi[r], -xj[r]);
+        const float d = __fadd_rn(x1[r], -x2[r]);
         const float m = __fadd_rn(d, -rint_fast(d));
-        const float st = (m >= 0.0f) ? aw : -aw;
-        xi[r] = __fadd_rn(xi[r], st);
-        xj[r] = __fadd_rn(xj[r], -st);
+        const bool p = (m >= tz) != wneg;
+        const float st = p ? alpha : -alpha;
+        x1[r] = __fadd_rn(x1[r], st);
+        x2[r] = __fadd_rn(x2[r], -st);
     }
 }
 
 // Binary16 storage: every phase write is a binary16 store of the wrapped
-// value, also between the two colours of a block, so each update there is
+// value, also between the colours of a block, so each update there is
 // wrapped and rounded through binary16 at once.
 template <int K>
 __device__ __forceinline__ void round_f16(float (&x)[K])
@@ -419,24 +428,18 @@ __device__ __forceinline__ void round_f16(float (&x)[K])
 }
 
 template <typename Store, int K>
-__device__ __forceinline__ void pair_block(float (&xi)[K], float (&xj)[K], float aw)
+__device__ __forceinline__ void pair_block(float (&x1)[K], float (&x2)[K], float alpha, bool wneg, float tz)
 {
-    if constexpr (sizeof(Store) == 4) {
-        pair_update_nowrap<K>(xi, xj, aw);
-    } else {
-        pair_update<K>(xi, xj, aw);
-        round_f16<K>(xi);
-        round_f16<K>(xj);
+    pair_fast<K>(x1, x2, alpha, wneg, tz);
+    if constexpr (sizeof(Store) == 2) {
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            x1[r] = wrap_c(x1[r]);
+            x2[r] = wrap_c(x2[r]);
+        }
+        round_f16<K>(x1);
+        round_f16<K>(x2);
     }
-}
-
-// Oriented update: eq. (6)'s roles follow the original vertex ids; `swp`
-// marks an edge whose second slot holds the smaller id (torus wrap).
-template <typename Store, int K>
-__device__ __forceinline__ void pair_oriented(float (&x1)[K], float (&x2)[K], float aw, bool swp)
-{
-    if (swp) pair_block<Store, K>(x2, x1, aw);
-    else pair_block<Store, K>(x1, x2, aw);
 }
 
 template <int K>
@@ -468,6 +471,8 @@ __device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, floa
 // loads a block, applies both colours in registers and stores it: every
 // vertex meets one edge of each colour inside its block. Edge indices are
 // implicit; weights are +-1 bits.
+constexpr float kTieUp = 0x1p-149f;  // least positive binary32
+
 template <typename Store, int K>
 __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, float alpha, int Q)
 {
@@ -479,11 +484,11 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
         ldk<K>(xs + (size_t)(2 * Q + f) * K, xc);
         ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
         // colour 0: A-B, C-D; colour 1: A-C, B-D (first slot = smaller id)
-        pair_block<Store, K>(xa, xb, (wb & 1u) ? -alpha : alpha);
-        pair_block<Store, K>(xc, xd, (wb & 2u) ? -alpha : alpha);
-        pair_block<Store, K>(xa, xc, (wb & 4u) ? -alpha : alpha);
-        pair_block<Store, K>(xb, xd, (wb & 8u) ? -alpha : alpha);
-        wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
+        pair_block<Store, K>(xa, xb, alpha, wb & 1u, 0.0f);
+        pair_block<Store, K>(xc, xd, alpha, wb & 2u, 0.0f);
+        pair_block<Store, K>(xa, xc, alpha, wb & 4u, 0.0f);
+        pair_block<Store, K>(xb, xd, alpha, wb & 8u, 0.0f);
+        // binary32 phases stay unwrapped until the odd pass of this sweep
         stk<K>(xs + (size_t)f * K, xa);
         stk<K>(xs + (size_t)(Q + f) * K, xb);
         stk<K>(xs + (size_t)(2 * Q + f) * K, xc);
@@ -505,6 +510,7 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
         const int gh = rw ? g + Wd - Q : g + Wd;
         m += dm;
         if (m >= Wd) m -= Wd;
+        const float tzc = cw ? kTieUp : 0.0f, tzr = rw ? kTieUp : 0.0f;
         const uint32_t wb = __ldg(wnib + Q + f);
         float xd[K], xc[K], xb[K], xa[K];
         ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
@@ -512,11 +518,11 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
         ldk<K>(xs + (size_t)(Q + h) * K, xb);
         ldk<K>(xs + (size_t)gh * K, xa);
         // colour 2: D-C, B-A (horizontal from odd columns)
-        pair_oriented<Store, K>(xd, xc, (wb & 1u) ? -alpha : alpha, cw);
-        pair_oriented<Store, K>(xb, xa, (wb & 2u) ? -alpha : alpha, cw);
+        pair_block<Store, K>(xd, xc, alpha, wb & 1u, tzc);
+        pair_block<Store, K>(xb, xa, alpha, wb & 2u, tzc);
         // colour 3: D-B, C-A (vertical from odd rows)
-        pair_oriented<Store, K>(xd, xb, (wb & 4u) ? -alpha : alpha, rw);
-        pair_oriented<Store, K>(xc, xa, (wb & 8u) ? -alpha : alpha, rw);
+        pair_block<Store, K>(xd, xb, alpha, wb & 4u, tzr);
+        pair_block<Store, K>(xc, xa, alpha, wb & 8u, tzr);
         if (dwt) {
             // the DWT follows the last colour of the sweep; every vertex is in
             // exactly one shifted block
