@@ -206,6 +206,31 @@ int cosm_validate_partition(int32_t n, int64_t m, const int32_t *src, const int3
  * memory and synchronises the device. */
 int cosm_probe_smem(int32_t iters, double *bytes_per_clk_per_sm, double *gbps);
 
+/* No-allocation run, for callers that cannot allocate device memory (code
+ * inside a host application that owns every device allocation, a plugin
+ * with no allocator, a process whose device memory is already committed).
+ * The paper has no counterpart; it is the edge-list sweep of cosm_run for
+ * one trial per replica, with the kernel's scratch -- packed edge records,
+ * weights, the step table, the work list and an error word -- held in a
+ * fixed static device array of COSM_STATIC_SCRATCH_BYTES that every GPU
+ * loading the library keeps until the process exits. It needs
+ *   5 m + 4 n + 8 sweeps + 28 ceil(replicas / tile) bytes
+ * (each part rounded up to 256 bytes); larger problems fail with
+ * COSM_ERR_TOO_LARGE before any device work. It calls no cudaMalloc or
+ * cudaFree. Inputs are host arrays as for cosm_create (the lattice hint is
+ * ignored; color may be NULL for the greedy colouring); outputs are
+ * caller-owned DEVICE buffers of `replicas` entries: each replica's best
+ * cut and best bisector index, the same values cosm_run + cosm_get_replica_cuts
+ * give for that graph without a lattice hint. Asynchronous on `stream`.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture. All calls share the array and it keeps the last call's contents:
+ * calls on one stream are ordered, but calls that may overlap on the GPU
+ * (other streams, other host threads) race and must not be issued. */
+#define COSM_STATIC_SCRATCH_BYTES (8u << 20)
+int cosm_solve_static(const cosm_graph_desc *g, const cosm_params *p, int64_t sweeps, int32_t replicas,
+                      uint64_t seed, int64_t *replica_cuts, int32_t *best_p, void *stream);
+
 /* Message for the calling thread's last failed call ("" if none). */
 const char *cosm_last_error(void);
 

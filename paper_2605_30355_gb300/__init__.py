@@ -42,7 +42,7 @@ EXPORTS = (
     "cosm_get_replica_cuts", "cosm_get_state", "cosm_set_state", "cosm_step", "cosm_readout",
     "cosm_solve", "cosm_layout", "cosm_color_greedy", "cosm_color_misra_gries",
     "cosm_color_torus2d", "cosm_color_torus3d", "cosm_validate_partition", "cosm_probe_smem",
-    "cosm_last_error",
+    "cosm_solve_static", "cosm_last_error",
 )
 
 
@@ -90,6 +90,7 @@ def _load():
         "cosm_color_torus3d": (C.c_int, [i32, i32, i32, i64, P, P, P]),
         "cosm_validate_partition": (C.c_int, [i32, i64, P, P, i32, P]),
         "cosm_probe_smem": (C.c_int, [i32, P, P]),
+        "cosm_solve_static": (C.c_int, [P, P, i64, i32, u64, P, P, P]),
         "cosm_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -250,6 +251,17 @@ def solve(n, src, dst, w, sweeps, replicas, seed, color=None, n_colors=0, dims=(
     _check(_lib.cosm_solve(C.byref(desc), C.byref(prm), int(sweeps), int(replicas), int(seed),
                            C.byref(cut), C.byref(en), _p(spins), _p(cuts)))
     return int(cut.value), int(en.value), spins, cuts
+
+
+def solve_static(n, src, dst, w, sweeps, replicas, seed, cuts_out, best_p_out, color=None,
+                 n_colors=0, params=None, stream=None, **kw):
+    """cosm_solve_static: no device allocation inside the library. cuts_out
+    (int64) and best_p_out (int32) are caller-owned device buffers of
+    `replicas` entries, e.g. torch tensors on the current device."""
+    prm = params if params is not None else default_params(**kw)
+    desc, keep = _desc(n, src, dst, w, color, n_colors, ())
+    _check(_lib.cosm_solve_static(C.byref(desc), C.byref(prm), int(sweeps), int(replicas), int(seed),
+                                  _p(cuts_out), _p(best_p_out), _stream(stream)))
 
 
 def probe_smem(iters=4096):

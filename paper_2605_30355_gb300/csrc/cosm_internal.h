@@ -101,6 +101,9 @@ struct FinalArgs {
 };
 int finalize_launch(const FinalArgs &a, void *stream);
 
+// Records the message that cosm_last_error() returns on this thread.
+void set_last_error(const std::string &msg);
+
 // Host-side graph tools (cosm_graph.cpp).
 struct Graph {
     int32_t n = 0;

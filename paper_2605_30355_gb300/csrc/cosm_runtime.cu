@@ -104,6 +104,8 @@ struct cosm_handle {
 
 extern "C" const char *cosm_last_error(void) { return g_err.c_str(); }
 
+void cosm::set_last_error(const std::string &msg) { g_err = msg; }
+
 extern "C" void cosm_default_params(cosm_params *p)
 {
     if (!p) return;
