@@ -277,7 +277,7 @@ def frustrated_loop_planted(dims, rho: float, seed: int, R: int = 0) -> Instance
         tries += 1
         if tries > 50 * max(n_loops, 1) + 1000:
             raise RuntimeError("could not place loops under the R cap")
-        rnd = st.u64(4 * n + 8)
+        rnd = st.u64(64)
         k = 0
         start = int(rnd[k] % np.uint64(n)); k += 1
         path = [start]
@@ -286,7 +286,7 @@ def frustrated_loop_planted(dims, rho: float, seed: int, R: int = 0) -> Instance
         cur = start
         while True:
             if k >= rnd.shape[0]:
-                rnd = st.u64(4 * n + 8)
+                rnd = st.u64(64)
                 k = 0
             choices = [int(x) for x in nb[cur] if int(x) != prev]
             nxt = choices[int(rnd[k] % np.uint64(len(choices)))]; k += 1
