@@ -48,6 +48,19 @@ WORKLOADS = {
     "reg4_20k": (lambda: instances.random_regular(20000, 4, 0), 2048, 10_000,
                  dict(alpha0_deg=14.0, dwt_ratio=1.0, dwt_period=3),
                  "random 4-regular N=20000, Misra-Gries colouring, 2048 replicas, 1e4 sweeps"),
+    "batch512": (None, None, 2000, dict(alpha0_deg=14.0, dwt_ratio=1.0, dwt_period=3),
+                 "ragged batch: 512 instances, N log-uniform in [800, 20000], half 2D +-1 tori, "
+                 "half G(n, m) with average degree 4-6 and weights in [-3,3]\\{0}, 64-256 replicas "
+                 "each, 2000 sweeps per trial, one graph-captured run"),
+    "serve": (None, 32, 2000, dict(alpha0_deg=25.0, dwt_ratio=1.0, dwt_period=3),
+              "serving: Poisson arrivals (50 requests/s for 10 s) of frustrated-loop planted "
+              "instances on 2D/3D periodic lattices (N in [1000, 50000], loop density 0.2-1.0), "
+              "32 replicas x 2000 sweeps per trial, up to 4 trials, target = planted optimum, "
+              "FP16 phase storage"),
+    "ablation": (lambda: g70_like(0), 512, 20_000, dict(alpha0_deg=14.0, dwt_ratio=1.0, dwt_period=6),
+                 "ablation of Table VII on a G70-like graph (G(n, m) with n = 10000, m = 9999, unit "
+                 "weights, greedy colouring): Cosm, without SCS, without DWT, neither; 512 trials x "
+                 "2e4 sweeps each"),
     "torus16": (lambda: instances.torus2d(16, 16, 0), 64, 1000,
                 dict(alpha0_deg=14.0, dwt_ratio=0.5, dwt_period=3),
                 "2D +-1 torus 16x16 (N=256), 64 replicas, 1000 sweeps"),
@@ -59,6 +72,40 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def g70_like(seed: int):
+    """Stand-in for Gset G70 (Table III: 10,000 vertices, 9,999 edges,
+    unweighted, bounded degree): a uniform G(n, m) with unit Max-Cut weights."""
+    g = instances.sparse_gnm(10000, 9999, seed, wmax=1)
+    g.w = np.ones_like(g.w)
+    g.meta["family"] = "g70_like"
+    return g
+
+
+def rank_seed(base: int, rank: int) -> int:
+    """Seed of one rank's replicas. The seed keys Philox, so ranks with
+    different seeds run disjoint, independent trials (replicas shard across
+    ranks with no exchange on the data path)."""
+    return int(base) + (int(rank) << 32)
+
+
+def max_over_ranks(x: float, device: str = "cpu") -> float:
+    """The largest x over all ranks (the slowest rank's time); x itself on
+    one process."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, t_max: float) -> float:
+    """Whole-job throughput: every rank processed units_per_rank units; the
+    job took the slowest rank's time."""
+    return units_per_rank * world / t_max
 
 
 def _colour(inst, name):
@@ -165,10 +212,10 @@ def run_ours(args):
         R = args.replicas
     if args.sweeps:
         S = args.sweeps
-    storage = cosm.F16 if args.storage == "f16" else cosm.F32
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage]
     inst = builder()
     col, C = _colour(inst, args.workload)
-    seed = 1 + rank  # every rank runs its own independent replicas
+    seed = rank_seed(1, rank)  # every rank runs its own independent replicas
     solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, **prm)
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
@@ -202,13 +249,9 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     t_step = sum(times) / len(times)
-    t_max = t_step
-    if ws > 1:
-        tt = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max = max_over_ranks(t_step, "cuda")
     updates = inst.m * S * R  # edge-replica updates per step per rank
-    value = updates * ws / t_max
+    value = whole_job_rate(updates, ws, t_max)
 
     # ---- end to end through the one-shot host-buffer call (cosm_solve)
     e2e_times = []
@@ -221,10 +264,8 @@ def run_ours(args):
                    n_colors=C, dims=inst.dims, storage=storage, replica_cuts=True, **prm)
         e2e_times.append(time.perf_counter() - t0)
     e2e_t = sum(e2e_times) / len(e2e_times) if e2e_times else None
-    if ws > 1 and e2e_t is not None:
-        tt = torch.tensor([e2e_t], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_t = float(tt.item())
+    if e2e_t is not None:
+        e2e_t = max_over_ranks(e2e_t, "cuda")
 
     if rank != 0:
         if ws > 1:
@@ -252,7 +293,7 @@ def run_ours(args):
         "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1000.0, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if storage == cosm.F32 else "f16-storage/f32-compute",
+        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point"}[storage],
         "data": "synthetic (seeded instance generator; no Gset files)",
         "config": {"workload": args.workload, "description": desc, "n": inst.n, "edges": inst.m,
                    "replicas_per_gpu": R, "sweeps_per_trial": S, "colors": layout["colors"],
@@ -260,7 +301,7 @@ def run_ours(args):
                    "ctas": layout["grid"], "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas sharded over {ws} GPU(s), no collective on the data path"},
         "e2e": None if e2e_t is None else {
-            "value": updates * ws / e2e_t, "unit": "updates/s", "h2d_bytes_per_step": h2d,
+            "value": whole_job_rate(updates, ws, e2e_t), "unit": "updates/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "api": "cosm_solve (host buffers)"},
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
@@ -296,7 +337,7 @@ def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks):
     finaliser is microseconds), so the step time is its launch duration."""
     import torch
     bpc, smem_gbps = cosm.probe_smem(4096)
-    b = 4 if storage == cosm.F32 else 2
+    b = 4 if storage == cosm.F32 else 2  # binary16 and u16 fixed point are 2 bytes
     if layout["lattice"] == 2:
         per_update = 2.0 * b
     else:
@@ -317,6 +358,231 @@ def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks):
     main = dict(main)
     main["other"] = other
     return main
+
+
+# ---------------------------------------------------------------------- batch
+
+def run_batch(args):
+    """The ragged batch: every step is one cosm_batch_run over all instances."""
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_30355_gb300 as cosm
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    _, _, S, prm, desc = WORKLOADS[args.workload]
+    if args.sweeps:
+        S = args.sweeps
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage]
+    insts, reps = instances.ragged_batch(512, seed=0)
+    seeds = np.arange(len(insts), dtype=np.uint64) + np.uint64(rank_seed(1, rank))
+    t0 = time.perf_counter()
+    batch = cosm.Batch(insts, storage=storage, **prm)
+    create_s = time.perf_counter() - t0
+    stream = torch.cuda.Stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    if not args.no_tune:
+        batch.tune(reps, probe_sweeps=20, stream=stream)
+    for _ in range(args.warmup):
+        batch.run(S, reps, seeds, stream)
+        batch.sync()
+    sampler = ClockSampler(local)
+    times = []
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    for k in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        batch.run(S, reps, seeds + 7919 * (k + 1), stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1000.0)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_step = sum(times) / len(times)
+    t_max = max_over_ranks(t_step, "cuda")
+    updates = sum(int(i.m) * S * r for i, r in zip(insts, reps))
+    info = batch.info()
+    # end to end: host instances -> create -> run -> every instance's best cut and spins
+    e2e_t = None
+    h2d = sum(i.src.nbytes + i.dst.nbytes + i.w.nbytes for i in insts)
+    d2h = sum(i.n + 24 for i in insts)
+    if args.e2e_steps:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b2 = cosm.Batch(insts, storage=storage, **prm)
+        b2.run(S, reps, seeds + 1, stream)
+        for i in range(len(insts)):
+            b2.best(i)
+        b2.close()
+        e2e_t = time.perf_counter() - t0
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = clocks.get("sm_mhz") or 2070.0
+    alu_peak = FP32_LANES_PER_SM * props.multi_processor_count * mhz * 1e6 / 1e12
+    alu_ach = ALU_OPS_PER_UPDATE * updates / t_step / 1e12
+    line = {
+        "metric": "edge-replica updates/s (ragged batch, one graph-captured run)",
+        "value": whole_job_rate(updates, ws, t_max), "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max * 1000.0, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point"}[storage],
+        "data": "synthetic (seeded instance generator; no Gset files)",
+        "config": {"workload": args.workload, "description": desc, "instances": len(insts),
+                   "replicas_total": int(sum(reps)), "sweeps_per_trial": S,
+                   "edges_total": int(sum(i.m for i in insts)), "batch": info,
+                   "create_s": create_s, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"all instances on each of {ws} GPU(s), no collective"},
+        "e2e": None if e2e_t is None else {
+            "value": whole_job_rate(updates, ws, e2e_t), "unit": "updates/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "api": "cosm_batch_create + cosm_batch_run + get_best (host buffers)"},
+        "gpu_launches": int(info["launches"]) * args.steps,
+        "clocks": clocks,
+        "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s",
+                     "frac": alu_ach / alu_peak, "traffic": None, "ops_per_update": ALU_OPS_PER_UPDATE,
+                     "peak_source": f"{FP32_LANES_PER_SM} FP32 lanes/SM x {props.multi_processor_count} "
+                                    f"SMs x {mhz:.0f} MHz (median sampled SM clock)"},
+    }
+    print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+    return line
+
+
+# ---------------------------------------------------------------------- ablation
+
+def run_ablation(args):
+    """Table VII's four variants on the same graph, replicas and seeds."""
+    import torch
+
+    import paper_2605_30355_gb300 as cosm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return None
+    builder, R, S, prm, desc = WORKLOADS[args.workload]
+    if args.sweeps:
+        S = args.sweeps
+    inst = builder()
+    rows = {}
+    t0 = time.perf_counter()
+    for name, flags in (("cosm", 0), ("without_scs", cosm.NO_SCS), ("without_dwt", cosm.NO_DWT),
+                        ("neither", cosm.NO_SCS | cosm.NO_DWT)):
+        s = cosm.Solver.from_instance(inst, flags=flags, **prm)
+        s.run(S, R, 1)
+        cuts, _ = s.replica_cuts()
+        rows[name] = {"highest_cut": int(cuts.max()), "average_cut": float(cuts.mean()),
+                      "P_highest_of_all": None}
+        rows[name]["_cuts"] = cuts
+        s.close()
+    top = max(r["highest_cut"] for r in rows.values())
+    for r in rows.values():
+        r["P_highest_of_all"] = float((r.pop("_cuts") >= top).mean())
+    line = {"metric": "ablation: highest / average cut per variant (Table VII shape)",
+            "value": rows["cosm"]["average_cut"], "unit": "cut", "n_gpus": 1, "steps": 1, "warmup": 0,
+            "ms_per_step": (time.perf_counter() - t0) * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic G70-like graph (seeded)",
+            "config": {"workload": "ablation", "description": desc, "n": inst.n, "edges": inst.m,
+                       "replicas": R, "sweeps_per_trial": S},
+            "ablation": rows,
+            "paper_context": {"G70_1.5M_sweeps": {"cosm": [9595, 9593.39], "without_scs": [9551, 9528.00],
+                                                  "without_dwt": [9544, 9501.40], "neither": [9481, 9432.81]},
+                              "source": "Table VII (highest, average cut)"}}
+    print(json.dumps(line))
+    return line
+
+
+# ---------------------------------------------------------------------- serving
+
+def serve_pool(count=10, seed=0):
+    """Planted instances spread over N in [1000, 50000] (2D and 3D, even
+    sides) and loop densities 0.2..1.0."""
+    st = instances.Stream(seed, tag=9)
+    us = (st.u64(count) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    pool = []
+    for k in range(count):
+        n = 1000 + us[k] * 49000
+        rho = [0.2, 0.4, 0.6, 0.8, 1.0][k % 5]
+        if k % 2 == 0:
+            L = max(4, 2 * int(round(np.sqrt(n) / 2)))
+            pool.append(instances.frustrated_loop_planted((L, L), rho, 1000 + k))
+        else:
+            L = max(4, 2 * int(round(n ** (1 / 3) / 2)))
+            pool.append(instances.frustrated_loop_planted((L, L, L), rho, 1000 + k))
+    return pool
+
+
+def run_serve(args):
+    import torch
+
+    import paper_2605_30355_gb300 as cosm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return None
+    _, R, S, prm, desc = WORKLOADS[args.workload]
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage]
+    pool = serve_pool()
+    rate, window, max_trials = 50.0, args.serve_seconds, 4
+    arr = instances.Stream(77, tag=10)
+    gaps = -np.log(1.0 - (arr.u64(100000) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) / rate
+    t_arr = np.cumsum(gaps)
+    t_arr = t_arr[t_arr < window]
+    picks = arr.below(len(pool), len(t_arr))
+    srv = cosm.Server(memory_budget=48 << 30, max_active=256, chunk_sweeps=500)
+    # warm-up: one request per pool instance size class
+    for inst in pool[:2]:
+        srv.wait(srv.submit(inst, S, R, 1, inst.meta["opt_cut"], max_trials=1, storage=storage, **prm), 600)
+    sampler = ClockSampler(local)
+    sampler.start()
+    ids = []
+    t0 = time.perf_counter()
+    for k, ta in enumerate(t_arr):
+        delay = t0 + ta - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        inst = pool[int(picks[k])]
+        ids.append(srv.submit(inst, S, R, 1000 + k, inst.meta["opt_cut"], max_trials=max_trials,
+                              storage=storage, **prm))
+    res = [srv.wait(r, 3600) for r in ids]
+    t_total = time.perf_counter() - t0
+    clocks = sampler.stop()
+    st = srv.stats()
+    srv.close()
+    reached = [r for r in res if r["status"] == cosm.REACHED]
+    ttt = np.array([r["ttt"] for r in reached]) if reached else np.array([])
+    updates = sum(int(r["updates"]) for r in res)
+    line = {
+        "metric": "serving: requests/s and time-to-target p50/p99 (planted instances)",
+        "value": len(res) / t_total, "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": t_total * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point"}[storage],
+        "data": "synthetic (seeded frustrated-loop planted instances)",
+        "config": {"workload": "serve", "description": desc, "pool": [(i.n, i.m, len(i.dims)) for i in pool],
+                   "requests": len(res), "arrival_rate": rate, "window_s": window,
+                   "server": {"memory_budget": 48 << 30, "max_active": 256, "chunk_sweeps": 500}},
+        "serving": {"reached": len(reached), "exhausted": len(res) - len(reached),
+                    "ttt_p50_s": float(np.percentile(ttt, 50)) if len(ttt) else None,
+                    "ttt_p99_s": float(np.percentile(ttt, 99)) if len(ttt) else None,
+                    "updates_per_s": updates / t_total, "stats": st},
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return line
 
 
 # ---------------------------------------------------------------------- oracle
@@ -348,7 +614,14 @@ def run_reference(args):
     if rank != 0:
         return None
     builder, R, S, prm, desc = WORKLOADS[args.workload]
-    inst = builder()
+    # the ragged batch is sampled through its largest torus instance, the
+    # serving workload through its first pool instance
+    if builder is not None:
+        inst = builder()
+    elif args.workload == "serve":
+        inst = serve_pool()[0]
+    else:
+        inst = max((i for i in instances.ragged_batch(512, seed=0)[0] if i.dims), key=lambda i: i.m)
     import oracle
     oracle.build()
     col, C = (None, 0)
@@ -380,16 +653,24 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="torus20k")
-    ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
+    ap.add_argument("--storage", choices=["f32", "f16", "q16"], default="f32")
     ap.add_argument("--replicas", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1, help="0 skips the end-to-end leg")
     ap.add_argument("--cpu-updates", type=float, default=6e9,
                     help="edge-replica updates in the bounded oracle sample")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
+    ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window")
     args = ap.parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch512":
+        run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
+    elif args.workload == "ablation":
+        run_ablation(args)
     else:
         run_ours(args)
 

@@ -48,9 +48,11 @@ extern "C" {
 #define COSM_ERR_STATE -7         /* call out of order (e.g. no run yet)     */
 #define COSM_ERR_NOMEM -8         /* host or device allocation failed        */
 
-/* ---- phase storage (arithmetic is FP32 in both) ------------------------ */
-#define COSM_F32 0 /* binary32 phases                                       */
-#define COSM_F16 1 /* binary16 phases: half the shared memory per replica   */
+/* ---- phase storage ----------------------------------------------------- */
+#define COSM_F32 0 /* binary32 phases, FP32 arithmetic                      */
+#define COSM_F16 1 /* binary16 phases (half the shared memory), FP32 arithmetic */
+#define COSM_Q16 2 /* fixed point: phases on the 2^-16-turn grid as u16,
+                    * steps rounded to the grid, exact integer arithmetic   */
 
 /* ---- variant flags (ablations of Table VII) ---------------------------- */
 #define COSM_NO_DWT 1 /* no dual window twist                              */
@@ -67,8 +69,10 @@ extern "C" {
  *           pattern when dims describes an even-sided torus, else greedy).
  *  dims     lattice hint {L1, L2, 0} for a 2D torus with v = r*L2 + c,
  *           {L1, L2, L3} for a 3D torus, {0, 0, 0} for a general graph.
- *           The hint only selects a faster shared-memory layout; it is
- *           checked against the edges and rejected if it does not match. */
+ *           Every edge must be an edge of that torus (a subset is fine);
+ *           the hint selects a shared-memory layout, and for the full 2D
+ *           torus with +-1 weights and the regular colouring an
+ *           implicit-index kernel. A hint that does not match is rejected. */
 typedef struct cosm_graph_desc {
     int32_t n;
     int64_t m;
@@ -86,7 +90,7 @@ typedef struct cosm_graph_desc {
  *  dwt_period   sweeps between DWT events (3 or 6); 0 disables the DWT
  *  window_deg   width of each of the two DWT windows, (0, 180] (paper: 90)
  *  n_bisectors  bisectors over a semicircle at readout, 1..256 (paper: 100)
- *  storage      COSM_F32 or COSM_F16
+ *  storage      COSM_F32, COSM_F16 or COSM_Q16
  *  flags        COSM_NO_DWT | COSM_NO_SCS                                  */
 typedef struct cosm_params {
     double alpha0_deg;
@@ -150,7 +154,8 @@ int cosm_set_state(cosm_handle *h, const double *phases, int32_t replicas, uint6
 
 /* Applies exactly one sweep with index `sweep` (1-based; the DWT fires when
  * sweep % dwt_period == 0) and step `alpha` (turns, FP32) to every replica
- * of the current state. The DWT rotation is dwt_ratio * alpha. */
+ * of the current state. The DWT rotation is dwt_ratio * alpha. With
+ * COSM_Q16 both are rounded to the nearest 2^-16-turn quantum. */
 int cosm_step(cosm_handle *h, int64_t sweep, float alpha, void *stream);
 
 /* Bisector readout of the current state without sweeping (Alg. 1 final
@@ -164,6 +169,127 @@ int cosm_readout(cosm_handle *h, void *stream);
 int cosm_solve(const cosm_graph_desc *g, const cosm_params *p, int64_t sweeps, int32_t replicas,
                uint64_t seed, int64_t *best_cut, int64_t *energy, int8_t *spins,
                int64_t *replica_cuts);
+
+/* ---- ragged batches: many instances of uneven size in one run ---------- */
+typedef struct cosm_batch cosm_batch;
+
+/* Creates `count` instances, each exactly as cosm_create would (graphs[i];
+ * params[i], or params[0] for all when shared_params != 0). Inputs are
+ * copied. Errors as cosm_create, with the failing instance in the message. */
+int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, const cosm_params *params,
+                      int32_t shared_params, cosm_batch **out);
+
+/* Runs one trial (Alg. 1) per replica of every instance i: sweeps[i] sweeps,
+ * replicas[i] replicas, seed seeds[i] (host arrays of `count`). Replica
+ * tiles of all instances are work units; units of one (storage, tile width,
+ * kernel) class share one persistent launch draining a queue ordered by
+ * decreasing cost; class launches overlap on forked streams; the run is
+ * captured into a CUDA graph once and replayed while its layout holds.
+ * Per instance, results equal those of cosm_run with the same arguments.
+ * Asynchronous: ordered after earlier work on `stream`, and later work on
+ * `stream` is ordered after it. */
+int cosm_batch_run(cosm_batch *b, const int64_t *sweeps, const int32_t *replicas, const uint64_t *seeds,
+                   void *stream);
+
+/* Waits for the batch's last run. */
+int cosm_batch_sync(cosm_batch *b);
+
+/* Results of instance i of the last run, as cosm_get_best /
+ * cosm_get_replica_cuts / cosm_get_state for that instance. */
+int cosm_batch_get_best(cosm_batch *b, int32_t i, int64_t *cut, int64_t *energy, int32_t *replica,
+                        int8_t *spins);
+int cosm_batch_get_replica_cuts(cosm_batch *b, int32_t i, int64_t *cuts, int32_t *best_p);
+int cosm_batch_get_state(cosm_batch *b, int32_t i, double *phases);
+
+/* Autotuner: times a short run (probe_sweeps sweeps per instance, the given
+ * replica counts) for each tile policy (per-instance widest tile that keeps
+ * the most replicas resident, or the narrowest tile) and thread count
+ * (rule-based, 128, 256, 512 per CTA) and keeps the fastest for later runs.
+ * With the environment variable COSM_TUNE_CACHE naming a file, a choice for
+ * the same batch shape is read from it, and new choices are appended. */
+int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t probe_sweeps, void *stream);
+
+/* out[0] instances, out[1] classes, out[2] units, out[3] kernel launches
+ * per run, out[4] graphs built, out[5] tile policy, out[6] forced threads
+ * (0 = rule), out[7] CTAs over all classes. */
+int cosm_batch_info(cosm_batch *b, int64_t out[8]);
+
+/* Releases the batch and all its instances. NULL is a no-op. */
+void cosm_batch_destroy(cosm_batch *b);
+
+/* ---- serving: continuous batching of requests ------------------------- */
+typedef struct cosm_server cosm_server;
+
+/* memory_budget: device bytes the admitted requests may hold together (a
+ * request's graph, phases of all its replicas, outputs, step table);
+ * max_active: requests on the device at once; chunk_sweeps: sweeps each
+ * active request advances per launch; threads: threads per CTA (0 = rule). */
+typedef struct cosm_server_config {
+    int64_t memory_budget;
+    int32_t max_active;
+    int32_t chunk_sweeps;
+    int32_t threads;
+    int32_t reserved;
+} cosm_server_config;
+
+/* status: 0 queued, 1 running, 2 target reached, 3 trials used up without
+ * reaching it, < 0 a COSM_ERR_* code. Times are seconds on the server's
+ * steady clock; ttt = time from submission to the end of the first trial
+ * whose best cut reached the target (< 0 if none). updates: edge-replica
+ * updates spent. best_* refer to the best trial so far. */
+typedef struct cosm_request_result {
+    int32_t status;
+    int32_t trials;
+    int64_t best_cut;
+    int64_t energy;
+    int32_t best_trial;
+    int32_t best_replica;
+    double t_submit;
+    double t_admit;
+    double t_done;
+    double ttt;
+    int64_t updates;
+} cosm_request_result;
+
+/* Defaults: 8 GiB budget, 64 active requests, 500-sweep chunks. */
+void cosm_server_default_config(cosm_server_config *c);
+
+/* Starts a server on the current device with its own worker thread. A
+ * request, once admitted (in arrival order, when a slot is free and its
+ * footprint fits the budget), keeps its phases on the device; all active
+ * requests advance together, one chunk of sweeps per launch; a request
+ * retires when a trial's best cut reaches its target or after max_trials
+ * trials, freeing its slot and memory. Trial t uses the seed
+ * seed + t * 0x9E3779B97F4A7C15, so a request's result is the same alone
+ * and in any mix. No paper counterpart (the paper runs batches of trials,
+ * Section III-B). */
+int cosm_server_create(const cosm_server_config *cfg, cosm_server **out);
+
+/* Queues a request (the graph is copied): trials of `sweeps` sweeps and
+ * `replicas` replicas each (Alg. 1 per replica), until a trial's best cut
+ * >= target_cut or max_trials trials. Returns at once with *id.
+ * COSM_ERR_TOO_LARGE if its footprint exceeds the whole budget. */
+int cosm_server_submit(cosm_server *s, const cosm_graph_desc *g, const cosm_params *p, int64_t sweeps,
+                       int32_t replicas, uint64_t seed, int64_t target_cut, int32_t max_trials,
+                       int64_t *id);
+
+/* Current state of a request (non-blocking). */
+int cosm_server_poll(cosm_server *s, int64_t id, cosm_request_result *out);
+
+/* Waits up to timeout_s seconds for a request to retire; COSM_ERR_TIMEOUT
+ * if it has not (out still receives its current state). */
+int cosm_server_wait(cosm_server *s, int64_t id, double timeout_s, cosm_request_result *out);
+
+/* Spins (+1/-1, n entries, original order) of a retired request's best trial. */
+int cosm_server_get_spins(cosm_server *s, int64_t id, int8_t *spins);
+
+/* out[0] queued, out[1] active, out[2] retired, out[3] chunks run, out[4]
+ * kernel launches, out[5] most requests active at once, out[6] peak
+ * admitted footprint (bytes), out[7] current footprint. */
+int cosm_server_stats(cosm_server *s, int64_t out[8]);
+
+/* Stops the worker after its current chunk and releases everything. */
+void cosm_server_destroy(cosm_server *s);
 
 /* Kernel layout chosen by cosm_create / cosm_run, for inspection:
  * out[0] replicas per CTA, out[1] threads per CTA, out[2] dynamic shared

@@ -30,6 +30,7 @@ NO_DWT = 1
 NO_SCS = 2
 STORE_F64 = 0
 STORE_F16 = 1
+STORE_Q16 = 2
 
 
 def build(force: bool = False) -> str:
@@ -105,6 +106,12 @@ def init_phases(n: int, seed: int, replica: int) -> np.ndarray:
     x = np.zeros(n, dtype=np.float64)
     lib().orc_init_phases(n, seed, replica, _p(x))
     return x
+
+
+def q16_grid(x):
+    """Phases on the 2^-16-turn grid (the fixed-point initial state: top 16
+    bits of the 24-bit draw)."""
+    return np.floor(np.asarray(x, dtype=np.float64) * 65536.0) / 65536.0
 
 
 def theta(seed: int, replica: int, sweep: int) -> float:

@@ -140,8 +140,15 @@ double orc_round_binary16(double y)
     return nearbyint(y / q) * q; /* default rounding mode: to nearest, ties to even */
 }
 
+/* Fixed-point phases (storage 2): phases live on the grid of 2^-16 turn
+ * and every step is rounded to that grid, a step a becoming
+ * floor(a 2^16 + 1/2) 2^-16; sums and differences of grid values are then
+ * exact in FP64, so the dynamics are exact integer arithmetic mod 2^16. */
+static double orc_q16_step(double a) { return floor(a * 65536.0 + 0.5) / 65536.0; }
+
 /* Storage rounding: 0 = none (FP64), 1 = binary16 of the phase's
- * representative in [-1/2, 1/2). The result is returned in [0,1). */
+ * representative in [-1/2, 1/2), 2 = fixed point (values already on the
+ * grid). The result is returned in [0,1). */
 static double orc_store(double x, int32_t storage)
 {
     if (storage != 1) return x;
@@ -190,6 +197,8 @@ int orc_in_window_q(double x, double theta, double W) { return orc_in_window(x, 
  *   over all edges (eq. (8)), the ablation "without SCS" of Table VII.
  *   Then, when sweep % dwt_period == 0 and DWT is on, every phase inside the
  *   dual windows moves by +dwt_ratio * alpha (Section II-D; one direction).
+ * storage: 0 FP64, 1 binary16 storage rounding, 2 fixed point on the
+ * 2^-16-turn grid (alpha and the twist rounded to the grid).
  * Near-ties: an edge whose angular difference is within tie_eps of 0 or 1/2
  * when processed, and a phase within tie_eps of a window edge, are recorded
  * in ties[] (edge e as e, vertex v as m + v). force[], when given, has m + n
@@ -205,6 +214,11 @@ int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
 {
     int64_t m = off[C];
     int64_t nt = 0;
+    double step = dwt_ratio * alpha;
+    if (storage == 2) {
+        step = orc_q16_step(step);
+        alpha = orc_q16_step(alpha);
+    }
     if (!(flags & ORC_NO_SCS)) {
         for (int32_t c = 0; c < C; ++c) {
             for (int64_t e = off[c]; e < off[c + 1]; ++e) {
@@ -242,7 +256,6 @@ int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
     }
     if (!(flags & ORC_NO_DWT) && dwt_period > 0 && (sweep % dwt_period) == 0) {
         double theta = orc_theta(seed, replica, sweep);
-        double step = dwt_ratio * alpha;
         for (int32_t v = 0; v < n; ++v) {
             double dist = 1.0;
             int in = orc_in_window(x[v], theta, window, &dist);
@@ -318,7 +331,10 @@ int64_t orc_trial(int32_t n, int32_t C, const int64_t *off, const int32_t *src, 
                   int32_t storage, double *x, int8_t *spins, int32_t *best_p)
 {
     orc_init_phases(n, seed, replica, x);
-    for (int32_t v = 0; v < n; ++v) x[v] = orc_store(x[v], storage);
+    for (int32_t v = 0; v < n; ++v) {
+        x[v] = orc_store(x[v], storage);
+        if (storage == 2) x[v] = floor(x[v] * 65536.0) / 65536.0; /* top 16 bits */
+    }
     for (int64_t s = 1; s <= S; ++s) {
         double a = orc_alpha(s, S, alpha0);
         orc_sweep(n, C, off, src, dst, w, x, a, s, dwt_period, dwt_ratio, window, seed, replica,

@@ -33,6 +33,7 @@ ERR_NOMEM = -8
 
 F32 = 0
 F16 = 1
+Q16 = 2
 NO_DWT = 1
 NO_SCS = 2
 
@@ -42,7 +43,11 @@ EXPORTS = (
     "cosm_get_replica_cuts", "cosm_get_state", "cosm_set_state", "cosm_step", "cosm_readout",
     "cosm_solve", "cosm_layout", "cosm_color_greedy", "cosm_color_misra_gries",
     "cosm_color_torus2d", "cosm_color_torus3d", "cosm_validate_partition", "cosm_probe_smem",
-    "cosm_solve_static", "cosm_last_error",
+    "cosm_solve_static", "cosm_batch_create", "cosm_batch_run", "cosm_batch_sync",
+    "cosm_batch_get_best", "cosm_batch_get_replica_cuts", "cosm_batch_get_state", "cosm_batch_tune",
+    "cosm_batch_info", "cosm_batch_destroy", "cosm_server_default_config", "cosm_server_create",
+    "cosm_server_submit", "cosm_server_poll", "cosm_server_wait", "cosm_server_get_spins",
+    "cosm_server_stats", "cosm_server_destroy", "cosm_last_error",
 )
 
 
@@ -56,6 +61,21 @@ class GraphDesc(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int64), ("src", C.c_void_p), ("dst", C.c_void_p),
                 ("w", C.c_void_p), ("n_colors", C.c_int32), ("color", C.c_void_p),
                 ("dims", C.c_int32 * 3)]
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("memory_budget", C.c_int64), ("max_active", C.c_int32), ("chunk_sweeps", C.c_int32),
+                ("threads", C.c_int32), ("reserved", C.c_int32)]
+
+
+class RequestResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("trials", C.c_int32), ("best_cut", C.c_int64),
+                ("energy", C.c_int64), ("best_trial", C.c_int32), ("best_replica", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("ttt", C.c_double), ("updates", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Params(C.Structure):
@@ -91,6 +111,23 @@ def _load():
         "cosm_validate_partition": (C.c_int, [i32, i64, P, P, i32, P]),
         "cosm_probe_smem": (C.c_int, [i32, P, P]),
         "cosm_solve_static": (C.c_int, [P, P, i64, i32, u64, P, P, P]),
+        "cosm_batch_create": (C.c_int, [i32, P, P, i32, P]),
+        "cosm_batch_run": (C.c_int, [P, P, P, P, P]),
+        "cosm_batch_sync": (C.c_int, [P]),
+        "cosm_batch_get_best": (C.c_int, [P, i32, P, P, P, P]),
+        "cosm_batch_get_replica_cuts": (C.c_int, [P, i32, P, P]),
+        "cosm_batch_get_state": (C.c_int, [P, i32, P]),
+        "cosm_batch_tune": (C.c_int, [P, P, i64, P]),
+        "cosm_batch_info": (C.c_int, [P, P]),
+        "cosm_batch_destroy": (None, [P]),
+        "cosm_server_default_config": (None, [P]),
+        "cosm_server_create": (C.c_int, [P, P]),
+        "cosm_server_submit": (C.c_int, [P, P, P, i64, i32, u64, i64, i32, P]),
+        "cosm_server_poll": (C.c_int, [P, i64, P]),
+        "cosm_server_wait": (C.c_int, [P, i64, C.c_double, P]),
+        "cosm_server_get_spins": (C.c_int, [P, i64, P]),
+        "cosm_server_stats": (C.c_int, [P, P]),
+        "cosm_server_destroy": (None, [P]),
         "cosm_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -240,6 +277,140 @@ class Solver:
         return dict(zip(keys, list(out)))
 
 
+class Batch:
+    """Many instances in one run (cosm_batch_*). `instances` is a list of
+    objects with n, src, dst, w and dims (and optional colour arrays)."""
+
+    def __init__(self, instances, params=None, colors=None, use_dims=True, **kw):
+        self.params = params if params is not None else default_params(**kw)
+        self.n = [int(i.n) for i in instances]
+        self._keep = []
+        descs = (GraphDesc * len(instances))()
+        for k, inst in enumerate(instances):
+            col, C_ = (colors[k] if colors is not None else (None, 0))
+            d, keep = _desc(inst.n, inst.src, inst.dst, inst.w, col, C_,
+                            inst.dims if use_dims else ())
+            descs[k] = d
+            self._keep.append(keep)
+        h = C.c_void_p()
+        _check(_lib.cosm_batch_create(len(instances), descs, C.byref(self.params), 1, C.byref(h)))
+        self._h = h
+        self.replicas = [0] * len(instances)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cosm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, sweeps, replicas, seeds, stream=None):
+        k = len(self.n)
+        sw = np.ascontiguousarray(np.broadcast_to(sweeps, (k,)), dtype=np.int64)
+        rp = np.ascontiguousarray(np.broadcast_to(replicas, (k,)), dtype=np.int32)
+        sd = np.ascontiguousarray(np.broadcast_to(seeds, (k,)), dtype=np.uint64)
+        self.replicas = [int(x) for x in rp]
+        _check(_lib.cosm_batch_run(self._h, _p(sw), _p(rp), _p(sd), _stream(stream)))
+
+    def sync(self):
+        _check(_lib.cosm_batch_sync(self._h))
+
+    def tune(self, replicas, probe_sweeps=20, stream=None):
+        rp = np.ascontiguousarray(np.broadcast_to(replicas, (len(self.n),)), dtype=np.int32)
+        _check(_lib.cosm_batch_tune(self._h, _p(rp), int(probe_sweeps), _stream(stream)))
+
+    def best(self, i):
+        cut, en, rep = C.c_int64(), C.c_int64(), C.c_int32()
+        spins = np.zeros(self.n[i], dtype=np.int8)
+        _check(_lib.cosm_batch_get_best(self._h, int(i), C.byref(cut), C.byref(en), C.byref(rep), _p(spins)))
+        return int(cut.value), int(en.value), int(rep.value), spins
+
+    def replica_cuts(self, i):
+        cuts = np.zeros(self.replicas[i], dtype=np.int64)
+        bps = np.zeros(self.replicas[i], dtype=np.int32)
+        _check(_lib.cosm_batch_get_replica_cuts(self._h, int(i), _p(cuts), _p(bps)))
+        return cuts, bps
+
+    def get_state(self, i):
+        x = np.zeros((self.replicas[i], self.n[i]), dtype=np.float64)
+        _check(_lib.cosm_batch_get_state(self._h, int(i), _p(x)))
+        return x
+
+    def info(self):
+        out = (C.c_int64 * 8)()
+        _check(_lib.cosm_batch_info(self._h, out))
+        keys = ("instances", "classes", "units", "launches", "graphs_built", "policy", "threads", "ctas")
+        return dict(zip(keys, list(out)))
+
+
+QUEUED, RUNNING, REACHED, EXHAUSTED = 0, 1, 2, 3
+
+
+class Server:
+    """Continuous-batching request server (cosm_server_*)."""
+
+    def __init__(self, memory_budget=None, max_active=None, chunk_sweeps=None, threads=None):
+        cfg = ServerConfig()
+        _lib.cosm_server_default_config(C.byref(cfg))
+        for k, v in (("memory_budget", memory_budget), ("max_active", max_active),
+                     ("chunk_sweeps", chunk_sweeps), ("threads", threads)):
+            if v is not None:
+                setattr(cfg, k, int(v))
+        self.cfg = cfg
+        h = C.c_void_p()
+        _check(_lib.cosm_server_create(C.byref(cfg), C.byref(h)))
+        self._h = h
+        self._n = {}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.cosm_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, inst, sweeps, replicas, seed, target_cut, max_trials=1, params=None, color=None,
+               n_colors=0, use_dims=True, **kw):
+        prm = params if params is not None else default_params(**kw)
+        desc, keep = _desc(inst.n, inst.src, inst.dst, inst.w, color, n_colors,
+                           inst.dims if use_dims else ())
+        rid = C.c_int64()
+        _check(_lib.cosm_server_submit(self._h, C.byref(desc), C.byref(prm), int(sweeps), int(replicas),
+                                       int(seed), int(target_cut), int(max_trials), C.byref(rid)))
+        self._n[rid.value] = int(inst.n)
+        return int(rid.value)
+
+    def poll(self, rid):
+        out = RequestResult()
+        _check(_lib.cosm_server_poll(self._h, int(rid), C.byref(out)))
+        return out.as_dict()
+
+    def wait(self, rid, timeout=60.0):
+        out = RequestResult()
+        _check(_lib.cosm_server_wait(self._h, int(rid), float(timeout), C.byref(out)))
+        return out.as_dict()
+
+    def spins(self, rid):
+        sp = np.zeros(self._n[rid], dtype=np.int8)
+        _check(_lib.cosm_server_get_spins(self._h, int(rid), _p(sp)))
+        return sp
+
+    def stats(self):
+        out = (C.c_int64 * 8)()
+        _check(_lib.cosm_server_stats(self._h, out))
+        keys = ("queued", "active", "retired", "chunks", "launches", "max_concurrent",
+                "peak_footprint", "footprint")
+        return dict(zip(keys, list(out)))
+
+
 def solve(n, src, dst, w, sweeps, replicas, seed, color=None, n_colors=0, dims=(), params=None,
           replica_cuts=False, **kw):
     """One-shot host-buffer call (cosm_solve): returns (cut, energy, spins, cuts|None)."""
@@ -307,5 +478,5 @@ def validate_partition(n, src, dst, n_colors, color) -> int:
                                             _p(color)))
 
 
-__all__ = ["Solver", "solve", "default_params", "color_greedy", "color_misra_gries",
+__all__ = ["Solver", "Batch", "Server", "solve", "default_params", "color_greedy", "color_misra_gries",
            "color_torus2d", "color_torus3d", "validate_partition", "CosmError", "EXPORTS"]

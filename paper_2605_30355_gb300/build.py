@@ -18,7 +18,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libcosm.so")
 BUILD = os.path.join(HERE, "_build")
 GENCODE = "arch=compute_103a,code=sm_103a"
-SOURCES = ["cosm_kernels.cu", "cosm_runtime.cu", "cosm_static.cu", "cosm_graph.cpp"]
+SOURCES = ["cosm_kernels.cu", "cosm_runtime.cu", "cosm_server.cu", "cosm_static.cu", "cosm_graph.cpp"]
 
 
 def nvcc() -> str:

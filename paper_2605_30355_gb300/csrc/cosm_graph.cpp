@@ -263,7 +263,8 @@ bool lattice_relabel(const Graph &g, std::vector<int32_t> &slot_of, std::string 
     slot_of.assign((size_t)g.n, 0);
     if (d[0] > 0 && d[1] > 0 && d[2] == 0) {
         const int32_t L1 = d[0], L2 = d[1];
-        if ((int64_t)L1 * L2 != g.n || g.m != 2 * (int64_t)g.n ||
+        // any subset of the torus edges (e.g. couplings that cancelled to 0)
+        if ((int64_t)L1 * L2 != g.n || g.m > 2 * (int64_t)g.n ||
             color_torus2d(L1, L2, g.m, g.src.data(), g.dst.data(), col.data()) != COSM_OK) {
             why = "dims does not describe this graph as an even-sided 2D torus";
             return false;
@@ -277,7 +278,7 @@ bool lattice_relabel(const Graph &g, std::vector<int32_t> &slot_of, std::string 
     }
     if (d[0] > 0 && d[1] > 0 && d[2] > 0) {
         const int32_t L1 = d[0], L2 = d[1], L3 = d[2];
-        if ((int64_t)L1 * L2 * L3 != g.n || g.m != 3 * (int64_t)g.n ||
+        if ((int64_t)L1 * L2 * L3 != g.n || g.m > 3 * (int64_t)g.n ||
             color_torus3d(L1, L2, L3, g.m, g.src.data(), g.dst.data(), col.data()) != COSM_OK) {
             why = "dims does not describe this graph as an even-sided 3D torus";
             return false;

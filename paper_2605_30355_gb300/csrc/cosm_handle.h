@@ -1,0 +1,116 @@
+// Host-side state of one instance and the runtime helpers shared by the
+// single-instance, batch and serving code.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/cosm.h"
+#include "cosm_internal.h"
+
+namespace cosm {
+
+// Records msg for cosm_last_error() and returns code.
+int fail(int code, const std::string &msg);
+
+}  // namespace cosm
+
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(COSM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+namespace cosm {
+
+template <typename T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t cap = 0;  // elements
+    int ensure(size_t count)
+    {
+        if (count <= cap && p) return COSM_OK;
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMalloc((void **)&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(COSM_ERR_NOMEM, "cudaMalloc failed");
+        }
+        cap = std::max<size_t>(count, 1);
+        return COSM_OK;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
+}  // namespace cosm
+
+struct cosm_handle {
+    using Graph = cosm::Graph;
+    template <typename T> using DevBuf = cosm::DevBuf<T>;
+    Graph g;                        // host copy, original vertex ids
+    cosm_params prm;
+    int device = 0;
+    int num_sms = 0;
+    bool lattice = false;
+    int64_t W = 0;                  // total weight
+    std::vector<int32_t> slot_of;   // original id -> slot
+    std::vector<int32_t> orig_of;   // slot -> original id
+    int32_t off[cosm::kMaxColors + 1] = {0};
+    int32_t C = 0;
+    DevBuf<uint32_t> d_ij;
+    DevBuf<int8_t> d_w;
+    DevBuf<int32_t> d_orig;
+    DevBuf<int32_t> d_off;          // colour offsets
+    int mode = cosm::MODE_GENERAL_;       // kernel variant
+    int32_t Q = 0, Wd = 0;          // 2D lattice geometry
+    DevBuf<uint8_t> d_wnib;         // 2D lattice block weight bits
+    // per run
+    DevBuf<unsigned char> d_state;
+    DevBuf<int64_t> d_cut;
+    DevBuf<int32_t> d_bestp;
+    DevBuf<float2> d_alpha;
+    DevBuf<cosm::Segment> d_segs;
+    DevBuf<int32_t> d_segoff;
+    DevBuf<int32_t> d_ready;
+    DevBuf<int32_t> d_err;
+    DevBuf<int64_t> d_best;
+    DevBuf<int8_t> d_spins;
+    // cached host tables
+    int64_t alpha_S = -1;
+    double alpha_a0 = -1, alpha_ratio = -1;
+    std::vector<cosm::Segment> h_segs;
+    std::vector<int32_t> h_segoff;
+    int64_t sched_tiles = -1, sched_S = -1, sched_G = -1;
+    bool segs_uploaded = false;
+    // state of the last launch
+    int replicas = 0;
+    int K = 0, threads = 0, occupancy = 0, grid = 0;
+    size_t smem = 0;
+    int64_t tile_stride = 0;  // storage elements per tile
+    uint64_t seed = 0;
+    bool have_state = false, have_result = false;
+    cudaStream_t stream = nullptr;
+    int launches = 0;
+};
+
+namespace cosm {
+
+int env_int(const char *name, int dflt);
+int choose_layout(cosm_handle *h, int replicas);
+int ensure_run_buffers(cosm_handle *h, int replicas);
+InstView inst_view(cosm_handle *h);
+int upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st);
+int launch_finalize(cosm_handle *h, cudaStream_t st);
+
+}  // namespace cosm

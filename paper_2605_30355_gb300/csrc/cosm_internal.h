@@ -31,15 +31,20 @@ struct Segment {
     int64_t s_end;
 };
 
-struct KernelArgs {
+// Everything a work segment of one instance touches.
+struct InstView {
     int32_t n;            // vertices (slots)
     int32_t C;            // colours
-    int32_t off[kMaxColors + 1];  // colour offsets into ij / w
+    const int32_t *off;   // device: colour offsets into ij / w (C + 1)
     const uint32_t *ij;   // edge records: slot(src) | slot(dst) << 16, colour-major
     const int8_t *w;      // Max-Cut weights, colour-major
     const int32_t *orig_of;  // slot -> original vertex id (Philox init key)
-    void *state;          // [tiles][n_pad][K] phases in the storage type
-    int64_t state_tile_stride;  // elements of the storage type per tile
+    // 2D lattice mode: Q = n/4 slots per sublattice, Wd = L2/2 columns;
+    // wnib[pass * Q + f] holds the weight bits of the four edges of 2x2
+    // block f in that pass (bit set: w = -1)
+    const uint8_t *wnib;
+    int32_t Q;
+    int32_t Wd;
     const float2 *alpha_tab;    // (alpha_s, dwt_step_s) for s = alpha_base ..
     int64_t alpha_base;
     int64_t S;            // sweeps of the trial (readout after sweep S)
@@ -49,19 +54,40 @@ struct KernelArgs {
     float window;         // DWT window width in turns
     int32_t flags;        // COSM_NO_DWT | COSM_NO_SCS
     int32_t P;            // bisectors
-    const Segment *segs;  // all segments
-    const int32_t *seg_off;  // CTA b runs segs[seg_off[b] .. seg_off[b+1])
-    int32_t *ready;       // per tile: last sweep whose state is published
-    int32_t *err;         // device error word (1 = wait timeout)
-    uint64_t wait_limit_ns;
+    int32_t mode;         // KernelMode of this instance
+    int32_t K;            // replicas per tile
+    uint32_t qwin;        // DWT window width in 2^-32 turns (fixed point)
+    void *state;          // [tiles][n_pad][K] phases in the storage type
+    int64_t state_tile_stride;  // elements of the storage type per tile
     int64_t *cut;         // [replicas] best cut
     int32_t *bestp;       // [replicas] best bisector
-    // 2D lattice mode: Q = n/4 slots per sublattice, Wd = L2/2 columns;
-    // wnib[pass * Q + f] holds the weight bits of the four edges of 2x2
-    // block f in that pass (bit set: w = -1)
-    const uint8_t *wnib;
-    int32_t Q;
-    int32_t Wd;
+};
+
+// Single-instance launch: the instance plus the CTAs' segment lists.
+struct KernelArgs {
+    InstView v;
+    const Segment *segs;     // all segments
+    const int32_t *seg_off;  // CTA b runs segs[seg_off[b] .. seg_off[b+1])
+    int32_t *ready;          // per tile: last sweep whose state is published
+    int32_t *err;            // device error word (1 = wait timeout)
+    uint64_t wait_limit_ns;
+};
+
+// Queue launch: CTAs take units (instance, tile, sweep range, SegFlags)
+// from a queue; a whole trial is (1, S, INIT | READOUT | STORE).
+struct BatchUnit {
+    int32_t inst;
+    int32_t tile;
+    int32_t flags;
+    int32_t pad_;
+    int64_t s_begin;
+    int64_t s_end;
+};
+struct BatchArgs {
+    const InstView *insts;
+    const BatchUnit *units;  // in decreasing cost order
+    int32_t n_units;
+    int32_t *counter;        // next unit (zeroed before the launch)
 };
 
 enum KernelMode { MODE_GENERAL_ = 0, MODE_ACCUM_ = 1, MODE_LATTICE2D_ = 2 };
@@ -82,6 +108,20 @@ struct LaunchCfg {
 size_t sweep_smem_bytes(int storage, int K, int n, int P, int mode);
 int sweep_occupancy(int storage, int K, int mode, int threads, size_t smem);
 int sweep_launch(const LaunchCfg &cfg, const KernelArgs &a, void *stream);
+
+// Batch kernels, one per (storage, K, mode) class.
+int batch_occupancy(int storage, int K, int mode, int threads, size_t smem);
+int batch_launch(int storage, int K, int mode, int grid, int threads, size_t smem, const BatchArgs &b,
+                 void *stream);
+// Per-instance finalisation of a batch: CTA i handles instance i.
+struct BatchFinal {
+    int64_t W;
+    int8_t *spins;        // n, original vertex order
+    int64_t *best;        // [0] cut, [1] energy, [2] replica
+    int32_t storage;      // 0 f32, 1 f16
+    int32_t pad_;
+};
+int batch_finalize_launch(int count, const InstView *insts, const BatchFinal *fin, void *stream);
 
 // Finalisation: best replica (max cut, ties -> lowest index), energy, spins.
 struct FinalArgs {

@@ -18,6 +18,8 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <type_traits>
+
 #include "../../include/cosm.h"
 #include "cosm_internal.h"
 
@@ -141,6 +143,58 @@ __device__ __forceinline__ void stk(__half *p, const float (&x)[K])
     }
 }
 
+// COSM_Q16 phases: integers on the 2^-16-turn grid stored as u16. In
+// registers a phase is the 32-bit integer q << 16, so 32-bit wrap-around is
+// the modular arithmetic of the circle and needs no wrap step; steps are
+// integers on the same grid, so every update is exact.
+template <int K>
+__device__ __forceinline__ void ldq(const uint16_t *p, uint32_t (&x)[K])
+{
+    if constexpr (K == 2) {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(p);
+        x[0] = w << 16; x[1] = w & 0xFFFF0000u;
+    } else if constexpr (K == 4) {
+        const uint2 w = *reinterpret_cast<const uint2 *>(p);
+        x[0] = w.x << 16; x[1] = w.x & 0xFFFF0000u;
+        x[2] = w.y << 16; x[3] = w.y & 0xFFFF0000u;
+    } else {
+        static_assert(K == 8, "K");
+        const uint4 w = *reinterpret_cast<const uint4 *>(p);
+        x[0] = w.x << 16; x[1] = w.x & 0xFFFF0000u;
+        x[2] = w.y << 16; x[3] = w.y & 0xFFFF0000u;
+        x[4] = w.z << 16; x[5] = w.z & 0xFFFF0000u;
+        x[6] = w.w << 16; x[7] = w.w & 0xFFFF0000u;
+    }
+}
+// low half-word from a's top half, high half-word from b's top half
+__device__ __forceinline__ uint32_t pack_q(uint32_t a, uint32_t b) { return __byte_perm(a, b, 0x7632); }
+template <int K>
+__device__ __forceinline__ void stq(uint16_t *p, const uint32_t (&x)[K])
+{
+    if constexpr (K == 2) {
+        *reinterpret_cast<uint32_t *>(p) = pack_q(x[0], x[1]);
+    } else if constexpr (K == 4) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(pack_q(x[0], x[1]), pack_q(x[2], x[3]));
+    } else {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(pack_q(x[0], x[1]), pack_q(x[2], x[3]),
+                                                   pack_q(x[4], x[5]), pack_q(x[6], x[7]));
+    }
+}
+
+// q = floor(x 2^32) mod 2^32 of each of K phases, for any storage type.
+template <typename Store, int K>
+__device__ __forceinline__ void ld_q32(const Store *p, uint32_t (&q)[K])
+{
+    if constexpr (sizeof(Store) == 2 && !std::is_same<Store, __half>::value) {
+        ldq<K>(p, q);
+    } else {
+        float x[K];
+        ldk<K>(p, x);
+#pragma unroll
+        for (int r = 0; r < K; ++r) q[r] = phase_q(x[r]);
+    }
+}
+
 __host__ __device__ constexpr size_t round16(size_t b) { return (b + 15) & ~size_t(15); }
 
 template <typename Store, int K>
@@ -220,7 +274,8 @@ __device__ __forceinline__ Tile<Store, K> carve(unsigned char *smem, int n, int 
 
 // Returns false when the bounded wait gave up (the error word is set).
 template <typename Store, int K>
-__device__ bool seg_begin(const KernelArgs &a, const Segment &sg, const Tile<Store, K> &t, int *s_skip)
+__device__ bool seg_begin(const InstView &v, const Segment &sg, const Tile<Store, K> &t, int *s_skip,
+                          int32_t *ready, int32_t *err, uint64_t wait_limit_ns)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (tid == 0) {
@@ -229,10 +284,10 @@ __device__ bool seg_begin(const KernelArgs &a, const Segment &sg, const Tile<Sto
             const int need = (int)(sg.s_begin - 1);
             unsigned long long t0, t1;
             asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-            while (atomicAdd(&a.ready[sg.tile], 0) < need) {
+            while (atomicAdd(&ready[sg.tile], 0) < need) {
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-                if (t1 - t0 > a.wait_limit_ns) {
-                    atomicExch(a.err, 1);
+                if (t1 - t0 > wait_limit_ns) {
+                    atomicExch(err, 1);
                     *s_skip = 1;
                     break;
                 }
@@ -243,20 +298,21 @@ __device__ bool seg_begin(const KernelArgs &a, const Segment &sg, const Tile<Sto
     }
     __syncthreads();
     if (*s_skip) return false;
-    const Store *gst = reinterpret_cast<const Store *>(a.state) + (size_t)sg.tile * a.state_tile_stride;
+    const Store *gst = reinterpret_cast<const Store *>(v.state) + (size_t)sg.tile * v.state_tile_stride;
     if (sg.flags & SEG_INIT) {
         // Alg. 1 "Set x_i random": Philox keyed by seed, counter (v/4, r, 0, 0)
         const uint32_t rep0 = (uint32_t)sg.tile * K;
-        const uint32_t k0 = (uint32_t)a.seed, k1 = (uint32_t)(a.seed >> 32);
-        for (int k = tid; k < a.n * K; k += nt) {
-            const int v = k / K, r = k % K;
-            const uint32_t ov = (uint32_t)a.orig_of[v];
+        const uint32_t k0 = (uint32_t)v.seed, k1 = (uint32_t)(v.seed >> 32);
+        for (int k = tid; k < v.n * K; k += nt) {
+            const int slot = k / K, r = k % K;
+            const uint32_t ov = (uint32_t)v.orig_of[slot];
             uint32_t c[4] = {ov >> 2, rep0 + (uint32_t)r, 0u, 0u};
             philox4x32_10(c, k0, k1);
             const uint32_t lo = (ov & 1) ? c[1] : c[0], hi = (ov & 1) ? c[3] : c[2];
-            const float g = u24_centered((ov & 2) ? hi : lo);
-            if constexpr (sizeof(Store) == 4) t.xs[k] = g;
-            else t.xs[k] = __float2half_rn(g);
+            const uint32_t word = (ov & 2) ? hi : lo;
+            if constexpr (std::is_same<Store, uint16_t>::value) t.xs[k] = (uint16_t)(word >> 16);
+            else if constexpr (sizeof(Store) == 4) t.xs[k] = u24_centered(word);
+            else t.xs[k] = __float2half_rn(u24_centered(word));
         }
     } else if (sg.flags & SEG_LOAD) {
         const uint4 *src = reinterpret_cast<const uint4 *>(gst);
@@ -273,7 +329,7 @@ __device__ bool seg_begin(const KernelArgs &a, const Segment &sg, const Tile<Sto
 // an edge is therefore cut on one interval of p or on its complement, which
 // a difference array over p accumulates exactly.
 template <typename Store, int K>
-__device__ void seg_readout(const KernelArgs &a, const Segment &sg, const Tile<Store, K> &t)
+__device__ void seg_readout(const InstView &a, const Segment &sg, const Tile<Store, K> &t)
 {
     const int tid = threadIdx.x, nt = blockDim.x, P = a.P;
     const uint32_t rep0 = (uint32_t)sg.tile * K;
@@ -282,17 +338,17 @@ __device__ void seg_readout(const KernelArgs &a, const Segment &sg, const Tile<S
     int base[K];
 #pragma unroll
     for (int r = 0; r < K; ++r) base[r] = 0;
-    const int m = a.off[a.C];
+    const int m = __ldg(a.off + a.C);
     for (int e = tid; e < m; e += nt) {
         const uint32_t rec = __ldg(a.ij + e);
         const int wv = (int)__ldg(a.w + e);
         const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
-        float xi[K], xj[K];
-        ldk<K>(t.xs + (size_t)i * K, xi);
-        ldk<K>(t.xs + (size_t)j * K, xj);
+        uint32_t qis[K], qjs[K];
+        ld_q32<Store, K>(t.xs + (size_t)i * K, qis);
+        ld_q32<Store, K>(t.xs + (size_t)j * K, qjs);
 #pragma unroll
         for (int r = 0; r < K; ++r) {
-            const uint32_t qi = phase_q(xi[r]), qj = phase_q(xj[r]);
+            const uint32_t qi = qis[r], qj = qjs[r];
             const int fi = (int)(((uint64_t)((qi & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
             const int fj = (int)(((uint64_t)((qj & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
             const int lo = min(fi, fj), hi = max(fi, fj);
@@ -331,7 +387,7 @@ __device__ void seg_readout(const KernelArgs &a, const Segment &sg, const Tile<S
 }
 
 template <typename Store, int K>
-__device__ void seg_end(const KernelArgs &a, const Segment &sg, const Tile<Store, K> &t)
+__device__ void seg_end(const InstView &a, const Segment &sg, const Tile<Store, K> &t, int32_t *ready)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     if (sg.flags & SEG_READOUT) seg_readout<Store, K>(a, sg, t);
@@ -343,7 +399,7 @@ __device__ void seg_end(const KernelArgs &a, const Segment &sg, const Tile<Store
         __threadfence();
     }
     __syncthreads();
-    if ((sg.flags & SEG_SIGNAL) && tid == 0) atomicExch(&a.ready[sg.tile], (int)sg.s_end);
+    if ((sg.flags & SEG_SIGNAL) && tid == 0) atomicExch(&ready[sg.tile], (int)sg.s_end);
 }
 
 // ---------------------------------------------------------------- sub-sweeps
@@ -354,11 +410,11 @@ __device__ void seg_end(const KernelArgs &a, const Segment &sg, const Tile<Store
 constexpr int kBatch = 4;
 
 template <typename Store, int K>
-__device__ __forceinline__ void general_colour(const KernelArgs &a, Store *xs, int c, float alpha)
+__device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int c, float alpha)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int e1 = a.off[c + 1];
-    for (int e0 = a.off[c] + tid; e0 < e1; e0 += kBatch * nt) {
+    const int e1 = __ldg(a.off + c + 1);
+    for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += kBatch * nt) {
         uint32_t rec[kBatch];
         float aw[kBatch];
 #pragma unroll
@@ -387,27 +443,27 @@ __device__ __forceinline__ void general_colour(const KernelArgs &a, Store *xs, i
     }
 }
 
-// Pair update inside a 2x2 block, for +-1 weights. x1, x2 are the block's
-// slots; eq. (6) takes x_i as the endpoint with the smaller original id,
-// which is x1 except at a torus wrap. With m = d - rint(d), d = x1 - x2, the
-// minimum angular difference (valid for any |d| < 2^22, so the phases may
-// stay unwrapped inside a block), the biased sign of eq. (4) gives
+// Pair update inside a 2x2 block. x1, x2 are the block's slots; eq. (6)
+// takes x_i as the endpoint with the smaller original id, which is x1
+// except at a torus wrap. With d = x1 - x2 and m = d - rint(d) its minimum
+// angular difference (valid for any |d| < 2^22, so phases may stay
+// unwrapped inside a sweep), the biased sign of eq. (4) gives
 //     x_i = x1:  the step on x1 is positive iff m >= 0
 //     x_i = x2:  the step on x1 is positive iff m > 0   (= -sgn_b(-m))
 // so one comparison threshold tz (0, or the least positive binary32 2^-149
-// for a wrap edge) covers both orientations. wneg: w = -1. Phases are
-// wrapped once per sweep, at the end of the odd pass: in between a phase
-// moves by at most a few steps, so |g| < 1 and binary32 keeps an ulp of at
+// for a wrap edge) covers both orientations; they agree with the oracle
+// except at the measure-zero tie m = +1/2. aw = alpha w (w = +-1). Phases
+// are wrapped once per sweep, at the end of the odd pass: in between a
+// phase moves by a few steps, so |g| < 1 and binary32 keeps an ulp of at
 // most 2^-24 turn.
 template <int K>
-__device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float alpha, bool wneg, float tz)
+__device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float aw, float tz)
 {
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         const float d = __fadd_rn(x1[r], -x2[r]);
-        const float m = __fadd_rn(d, -rint_fast(d));
-        const bool p = (m >= tz) != wneg;
-        const float st = p ? alpha : -alpha;
+        const bool p = __fadd_rn(d, -rint_fast(d)) >= tz;
+        const float st = p ? aw : -aw;
         x1[r] = __fadd_rn(x1[r], st);
         x2[r] = __fadd_rn(x2[r], -st);
     }
@@ -428,9 +484,9 @@ __device__ __forceinline__ void round_f16(float (&x)[K])
 }
 
 template <typename Store, int K>
-__device__ __forceinline__ void pair_block(float (&x1)[K], float (&x2)[K], float alpha, bool wneg, float tz)
+__device__ __forceinline__ void pair_block(float (&x1)[K], float (&x2)[K], float aw, float tz)
 {
-    pair_fast<K>(x1, x2, alpha, wneg, tz);
+    pair_fast<K>(x1, x2, aw, tz);
     if constexpr (sizeof(Store) == 2) {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
@@ -473,9 +529,15 @@ __device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, floa
 // implicit; weights are +-1 bits.
 constexpr float kTieUp = 0x1p-149f;  // least positive binary32
 
+__device__ __forceinline__ float signed_alpha(uint32_t wb, uint32_t bit, float alpha)
+{
+    return (wb & bit) ? -alpha : alpha;
+}
+
 template <typename Store, int K>
 __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, float alpha, int Q)
 {
+#pragma unroll 2
     for (int f = threadIdx.x; f < Q; f += blockDim.x) {
         const uint32_t wb = __ldg(wnib + f);
         float xa[K], xb[K], xc[K], xd[K];
@@ -484,10 +546,10 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
         ldk<K>(xs + (size_t)(2 * Q + f) * K, xc);
         ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
         // colour 0: A-B, C-D; colour 1: A-C, B-D (first slot = smaller id)
-        pair_block<Store, K>(xa, xb, alpha, wb & 1u, 0.0f);
-        pair_block<Store, K>(xc, xd, alpha, wb & 2u, 0.0f);
-        pair_block<Store, K>(xa, xc, alpha, wb & 4u, 0.0f);
-        pair_block<Store, K>(xb, xd, alpha, wb & 8u, 0.0f);
+        pair_block<Store, K>(xa, xb, signed_alpha(wb, 1u, alpha), 0.0f);
+        pair_block<Store, K>(xc, xd, signed_alpha(wb, 2u, alpha), 0.0f);
+        pair_block<Store, K>(xa, xc, signed_alpha(wb, 4u, alpha), 0.0f);
+        pair_block<Store, K>(xb, xd, signed_alpha(wb, 8u, alpha), 0.0f);
         // binary32 phases stay unwrapped until the odd pass of this sweep
         stk<K>(xs + (size_t)f * K, xa);
         stk<K>(xs + (size_t)(Q + f) * K, xb);
@@ -496,21 +558,32 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
     }
 }
 
-template <typename Store, int K>
+// kFixedColumn: the thread count is a multiple of Wd, so every block a
+// thread visits sits in the same column and the column wrap is fixed.
+template <typename Store, int K, bool kFixedColumn>
 __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
                                                int m0, int dm, bool dwt, const float *thc, float W2,
                                                float step)
 {
     int m = m0;  // column of block f within its row
+    const bool cw0 = (m0 == Wd - 1);
+    const int goff0 = cw0 ? 1 - Wd : 1;
+    const float tzc0 = cw0 ? kTieUp : 0.0f;
+#pragma unroll 2
     for (int f = threadIdx.x; f < Q; f += blockDim.x) {
-        const bool cw = (m == Wd - 1);      // next column wraps to column 0
+        int goff = goff0;
+        float tzc = tzc0;
+        if (!kFixedColumn) {
+            const bool cw = (m == Wd - 1);  // next column wraps to column 0
+            goff = cw ? 1 - Wd : 1;
+            tzc = cw ? kTieUp : 0.0f;
+            m += dm;
+            if (m >= Wd) m -= Wd;
+        }
         const bool rw = (f >= Q - Wd);      // next row wraps to row 0
-        const int g = cw ? f + 1 - Wd : f + 1;
-        const int h = rw ? f + Wd - Q : f + Wd;
-        const int gh = rw ? g + Wd - Q : g + Wd;
-        m += dm;
-        if (m >= Wd) m -= Wd;
-        const float tzc = cw ? kTieUp : 0.0f, tzr = rw ? kTieUp : 0.0f;
+        const int hoff = rw ? Wd - Q : Wd;
+        const int g = f + goff, h = f + hoff, gh = g + hoff;
+        const float tzr = rw ? kTieUp : 0.0f;
         const uint32_t wb = __ldg(wnib + Q + f);
         float xd[K], xc[K], xb[K], xa[K];
         ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
@@ -518,11 +591,11 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
         ldk<K>(xs + (size_t)(Q + h) * K, xb);
         ldk<K>(xs + (size_t)gh * K, xa);
         // colour 2: D-C, B-A (horizontal from odd columns)
-        pair_block<Store, K>(xd, xc, alpha, wb & 1u, tzc);
-        pair_block<Store, K>(xb, xa, alpha, wb & 2u, tzc);
+        pair_block<Store, K>(xd, xc, signed_alpha(wb, 1u, alpha), tzc);
+        pair_block<Store, K>(xb, xa, signed_alpha(wb, 2u, alpha), tzc);
         // colour 3: D-B, C-A (vertical from odd rows)
-        pair_block<Store, K>(xd, xb, alpha, wb & 4u, tzr);
-        pair_block<Store, K>(xc, xa, alpha, wb & 8u, tzr);
+        pair_block<Store, K>(xd, xb, signed_alpha(wb, 4u, alpha), tzr);
+        pair_block<Store, K>(xc, xa, signed_alpha(wb, 8u, alpha), tzr);
         if (dwt) {
             // the DWT follows the last colour of the sweep; every vertex is in
             // exactly one shifted block
@@ -546,113 +619,384 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
     }
 }
 
-// ---------------------------------------------------------------- sweep kernel
+// ---------------------------------------------------------------- fixed point sweep
+// Eq. (6) on the 2^-16-turn grid: with phases held as q << 16, d = x_i - x_j
+// read as int32 is the minimum angular difference (times 2^32) and the
+// biased sign of eq. (4) is d >= 0 (d = -2^31, exactly opposite, gives -1).
+// ap = (alpha quanta x w) << 16; every operation is exact.
+template <int K>
+__device__ __forceinline__ void pair_q(uint32_t (&xi)[K], uint32_t (&xj)[K], uint32_t ap)
+{
+#pragma unroll
+    for (int r = 0; r < K; ++r) {
+        const uint32_t st = ((int32_t)(xi[r] - xj[r]) >= 0) ? ap : 0u - ap;
+        xi[r] += st;
+        xj[r] -= st;
+    }
+}
+
+// Dual window twist on the grid: inside iff ((q - q_theta + QW/2) mod 2^31)
+// < QW; c = QW/2 - q_theta per replica.
+template <int K>
+__device__ __forceinline__ void dwt_q(uint32_t (&x)[K], const uint32_t *c, uint32_t qw, uint32_t stepq)
+{
+#pragma unroll
+    for (int r = 0; r < K; ++r)
+        if (((x[r] + c[r]) & 0x7FFFFFFFu) < qw) x[r] += stepq;
+}
+
+template <int K>
+__device__ __forceinline__ void general_colour_q(const InstView &a, uint16_t *xs, int c, uint32_t aq)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int e1 = __ldg(a.off + c + 1);
+    for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += kBatch * nt) {
+        uint32_t rec[kBatch], ap[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int e = e0 + u * nt;
+            rec[u] = e < e1 ? __ldg(a.ij + e) : 0u;
+            ap[u] = e < e1 ? (uint32_t)((int32_t)aq * (int32_t)__ldg(a.w + e)) << 16 : 0u;
+        }
+        uint32_t xi[kBatch][K], xj[kBatch][K];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (e0 + u * nt < e1) {
+                ldq<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
+                ldq<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) pair_q<K>(xi[u], xj[u], ap[u]);
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            if (e0 + u * nt < e1) {
+                stq<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
+                stq<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t signed_q(uint32_t wb, uint32_t bit, uint32_t ap)
+{
+    return (wb & bit) ? 0u - ap : ap;
+}
+
+template <int K>
+__device__ __forceinline__ void block_pass_even_q(uint16_t *xs, const uint8_t *wnib, uint32_t ap, int Q)
+{
+    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+        const uint32_t wb = __ldg(wnib + f);
+        uint32_t xa[K], xb[K], xc[K], xd[K];
+        ldq<K>(xs + (size_t)f * K, xa);
+        ldq<K>(xs + (size_t)(Q + f) * K, xb);
+        ldq<K>(xs + (size_t)(2 * Q + f) * K, xc);
+        ldq<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        pair_q<K>(xa, xb, signed_q(wb, 1u, ap));
+        pair_q<K>(xc, xd, signed_q(wb, 2u, ap));
+        pair_q<K>(xa, xc, signed_q(wb, 4u, ap));
+        pair_q<K>(xb, xd, signed_q(wb, 8u, ap));
+        stq<K>(xs + (size_t)f * K, xa);
+        stq<K>(xs + (size_t)(Q + f) * K, xb);
+        stq<K>(xs + (size_t)(2 * Q + f) * K, xc);
+        stq<K>(xs + (size_t)(3 * Q + f) * K, xd);
+    }
+}
+
+// In the shifted blocks the second slot holds the smaller original id at a
+// torus wrap; the roles of eq. (6) then swap exactly (the exactly-opposite
+// tie is an integer value on the grid, so no shortcut is taken).
+template <int K>
+__device__ __forceinline__ void pair_q_oriented(uint32_t (&x1)[K], uint32_t (&x2)[K], uint32_t ap, bool swp)
+{
+    if (swp) pair_q<K>(x2, x1, ap);
+    else pair_q<K>(x1, x2, ap);
+}
+
+template <int K>
+__device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wnib, uint32_t ap, int Q, int Wd,
+                                                 int m0, int dm, bool dwt, const uint32_t *c, uint32_t qw,
+                                                 uint32_t stepq)
+{
+    int m = m0;
+    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+        const bool cw = (m == Wd - 1);
+        m += dm;
+        if (m >= Wd) m -= Wd;
+        const bool rw = (f >= Q - Wd);
+        const int hoff = rw ? Wd - Q : Wd;
+        const int g = f + (cw ? 1 - Wd : 1), h = f + hoff, gh = g + hoff;
+        const uint32_t wb = __ldg(wnib + Q + f);
+        uint32_t xd[K], xc[K], xb[K], xa[K];
+        ldq<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        ldq<K>(xs + (size_t)(2 * Q + g) * K, xc);
+        ldq<K>(xs + (size_t)(Q + h) * K, xb);
+        ldq<K>(xs + (size_t)gh * K, xa);
+        pair_q_oriented<K>(xd, xc, signed_q(wb, 1u, ap), cw);
+        pair_q_oriented<K>(xb, xa, signed_q(wb, 2u, ap), cw);
+        pair_q_oriented<K>(xd, xb, signed_q(wb, 4u, ap), rw);
+        pair_q_oriented<K>(xc, xa, signed_q(wb, 8u, ap), rw);
+        if (dwt) {
+            dwt_q<K>(xd, c, qw, stepq);
+            dwt_q<K>(xc, c, qw, stepq);
+            dwt_q<K>(xb, c, qw, stepq);
+            dwt_q<K>(xa, c, qw, stepq);
+        }
+        stq<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        stq<K>(xs + (size_t)(2 * Q + g) * K, xc);
+        stq<K>(xs + (size_t)(Q + h) * K, xb);
+        stq<K>(xs + (size_t)gh * K, xa);
+    }
+}
+
+// ---------------------------------------------------------------- segment body
 enum { MODE_GENERAL = 0, MODE_ACCUM = 1, MODE_LATTICE2D = 2 };
 
+// Fixed-point (COSM_Q16) segment: as run_segment below, on the grid.
+template <int K, int kMode>
+__device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment &sg, unsigned char *smem,
+                                                int *s_skip, int32_t *ready, int32_t *err,
+                                                uint64_t wait_limit_ns)
+{
+    const Tile<uint16_t, K> t = carve<uint16_t, K>(smem, v.n, v.P, kMode == MODE_ACCUM);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = v.n;
+    const bool dwt_on = !(v.flags & 1) && v.dwt_period > 0;
+    uint32_t *cq = reinterpret_cast<uint32_t *>(t.thc);
+    int m0 = 0, dm = 0;
+    if (kMode == MODE_LATTICE2D) {
+        m0 = tid % v.Wd;
+        dm = nt % v.Wd;
+    }
+    if (!seg_begin<uint16_t, K>(v, sg, t, s_skip, ready, err, wait_limit_ns)) return;
+    const uint32_t rep0 = (uint32_t)sg.tile * K;
+    int phase = dwt_on ? (int)(sg.s_begin % v.dwt_period) : 1;
+    for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
+        const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));  // grid quanta
+        const uint32_t aq = (uint32_t)__float2int_rn(at.x), stepq = (uint32_t)__float2int_rn(at.y) << 16;
+        const bool dwt = dwt_on && phase == 0;
+        if (dwt && tid < K) {
+            const uint32_t qth = (uint32_t)__float2uint_rn(dwt_theta(v.seed, rep0 + tid, s) * 16777216.0f) << 8;
+            cq[tid] = (v.qwin >> 1) - qth;
+        }
+        if (kMode == MODE_LATTICE2D) {
+            block_pass_even_q<K>(t.xs, v.wnib, aq << 16, v.Q);
+            __syncthreads();
+            block_pass_odd_q<K>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, stepq);
+            __syncthreads();
+        } else {
+            if (kMode == MODE_GENERAL) {
+                for (int c = 0; c < v.C; ++c) {
+                    general_colour_q<K>(v, t.xs, c, aq);
+                    __syncthreads();
+                }
+            } else {
+                // simultaneous step (eq. (8)): integer sums of the pair steps
+                uint32_t *acc = reinterpret_cast<uint32_t *>(t.acc);
+                for (int k = tid; k < n * K; k += nt) acc[k] = 0u;
+                __syncthreads();
+                for (int c = 0; c < v.C; ++c) {
+                    const int e1 = __ldg(v.off + c + 1);
+                    for (int e = __ldg(v.off + c) + tid; e < e1; e += nt) {
+                        const uint32_t rec = __ldg(v.ij + e);
+                        const uint32_t ap = (uint32_t)((int32_t)aq * (int32_t)__ldg(v.w + e)) << 16;
+                        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+                        uint32_t xi[K], xj[K];
+                        ldq<K>(t.xs + (size_t)i * K, xi);
+                        ldq<K>(t.xs + (size_t)j * K, xj);
+#pragma unroll
+                        for (int r = 0; r < K; ++r) {
+                            const uint32_t st = ((int32_t)(xi[r] - xj[r]) >= 0) ? ap : 0u - ap;
+                            acc[(size_t)i * K + r] += st;
+                            acc[(size_t)j * K + r] -= st;
+                        }
+                    }
+                    __syncthreads();
+                }
+                for (int u = tid; u < n; u += nt) {
+                    uint32_t x[K];
+                    ldq<K>(t.xs + (size_t)u * K, x);
+#pragma unroll
+                    for (int r = 0; r < K; ++r) x[r] += acc[(size_t)u * K + r];
+                    stq<K>(t.xs + (size_t)u * K, x);
+                }
+                __syncthreads();
+            }
+            if (dwt) {
+                if (v.C == 0) __syncthreads();
+                for (int u = tid; u < n; u += nt) {
+                    uint32_t x[K];
+                    ldq<K>(t.xs + (size_t)u * K, x);
+                    dwt_q<K>(x, cq, v.qwin, stepq);
+                    stq<K>(t.xs + (size_t)u * K, x);
+                }
+                __syncthreads();
+            }
+        }
+        if (dwt_on && ++phase == v.dwt_period) phase = 0;
+    }
+    seg_end<uint16_t, K>(v, sg, t, ready);
+}
+
+// One work segment of one replica tile: wait / init / load, sweeps
+// s_begin..s_end, readout, store / publish. Every thread of the CTA calls it.
+template <typename Store, int K, int kMode>
+__device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment &sg, unsigned char *smem,
+                                               int *s_skip, int32_t *ready, int32_t *err,
+                                               uint64_t wait_limit_ns)
+{
+    const Tile<Store, K> t = carve<Store, K>(smem, v.n, v.P, kMode == MODE_ACCUM);
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int n = v.n;
+    const bool dwt_on = !(v.flags & 1) && v.dwt_period > 0;
+    const float W2 = 2.0f * v.window, hw = 0.5f * v.window;
+    constexpr bool kLattice = (kMode == MODE_LATTICE2D);
+    int m0 = 0, dm = 0;
+    if (kLattice) {
+        m0 = tid % v.Wd;
+        dm = nt % v.Wd;
+    }
+    if (!seg_begin<Store, K>(v, sg, t, s_skip, ready, err, wait_limit_ns)) return;
+    const uint32_t rep0 = (uint32_t)sg.tile * K;
+    int phase = dwt_on ? (int)(sg.s_begin % v.dwt_period) : 1;
+    for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
+        const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));
+        const bool dwt = dwt_on && phase == 0;
+        if (dwt && tid < K)
+            t.thc[tid] = 2.0f * (hw - dwt_theta(v.seed, rep0 + tid, s));
+        if (kLattice) {
+            // colours 0, 1 in the 2x2 blocks; colours 2, 3 (+ DWT) in the
+            // shifted blocks
+            block_pass_even<Store, K>(t.xs, v.wnib, at.x, v.Q);
+            __syncthreads();
+            if (dm == 0)
+                block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, at.y);
+            else
+                block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, at.y);
+            __syncthreads();
+        } else {
+            if (kMode == MODE_GENERAL) {
+                // sequential conflict-free search: colours in order (eq. (11))
+                for (int c = 0; c < v.C; ++c) {
+                    general_colour<Store, K>(v, t.xs, c, at.x);
+                    __syncthreads();
+                }
+            } else {
+                // simultaneous generalized-gradient step over all edges (eq. (8))
+                for (int k = tid; k < n * K; k += nt) t.acc[k] = 0.0f;
+                __syncthreads();
+                for (int c = 0; c < v.C; ++c) {
+                    const int e1 = __ldg(v.off + c + 1);
+                    for (int e = __ldg(v.off + c) + tid; e < e1; e += nt) {
+                        const uint32_t rec = __ldg(v.ij + e);
+                        const float aw = at.x * (float)__ldg(v.w + e);
+                        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+                        float xi[K], xj[K];
+                        ldk<K>(t.xs + (size_t)i * K, xi);
+                        ldk<K>(t.xs + (size_t)j * K, xj);
+#pragma unroll
+                        for (int r = 0; r < K; ++r) {
+                            const float d = __fadd_rn(xi[r], -xj[r]);
+                            const float mm = __fadd_rn(d, -rint_fast(d));
+                            const float st = (mm >= 0.0f) ? aw : -aw;
+                            t.acc[(size_t)i * K + r] += st;
+                            t.acc[(size_t)j * K + r] -= st;
+                        }
+                    }
+                    __syncthreads();  // one colour is a matching: no shared vertex
+                }
+                for (int u = tid; u < n; u += nt) {
+                    float x[K];
+                    ldk<K>(t.xs + (size_t)u * K, x);
+#pragma unroll
+                    for (int r = 0; r < K; ++r) x[r] = wrap_c(__fadd_rn(x[r], t.acc[(size_t)u * K + r]));
+                    stk<K>(t.xs + (size_t)u * K, x);
+                }
+                __syncthreads();
+            }
+            if (dwt) {
+                if (v.C == 0) __syncthreads();
+                for (int u = tid; u < n; u += nt) {
+                    float x[K];
+                    ldk<K>(t.xs + (size_t)u * K, x);
+                    dwt_apply<K>(x, t.thc, W2, at.y);
+                    stk<K>(t.xs + (size_t)u * K, x);
+                }
+                __syncthreads();
+            }
+        }
+        if (dwt_on && ++phase == v.dwt_period) phase = 0;
+    }
+    seg_end<Store, K>(v, sg, t, ready);
+}
+
+template <typename Store, int K, int kMode>
+__device__ __forceinline__ void run_segment(const InstView &v, const Segment &sg, unsigned char *smem,
+                                            int *s_skip, int32_t *ready, int32_t *err,
+                                            uint64_t wait_limit_ns)
+{
+    if constexpr (std::is_same<Store, uint16_t>::value)
+        run_segment_q16<K, kMode>(v, sg, smem, s_skip, ready, err, wait_limit_ns);
+    else
+        run_segment_fp<Store, K, kMode>(v, sg, smem, s_skip, ready, err, wait_limit_ns);
+}
+
+// ---------------------------------------------------------------- sweep kernel
+// One instance: CTA b runs its segment list (one whole trial per tile, or
+// the head / tail pieces of the wrap-around schedule).
 template <typename Store, int K, int kMode>
 __global__ void __launch_bounds__(512) sweep_kernel(const KernelArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_skip;
-    const Tile<Store, K> t = carve<Store, K>(smem, a.n, a.P, kMode == MODE_ACCUM);
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int n = a.n;
-    const bool dwt_on = !(a.flags & 1) && a.dwt_period > 0;
-    const float W2 = 2.0f * a.window, hw = 0.5f * a.window;
-
-    int m0 = 0, dm = 0;
-    if (kMode == MODE_LATTICE2D) {
-        m0 = tid % a.Wd;
-        dm = nt % a.Wd;
-    }
-
     for (int si = a.seg_off[blockIdx.x]; si < a.seg_off[blockIdx.x + 1]; ++si) {
         const Segment sg = a.segs[si];
-        if (!seg_begin<Store, K>(a, sg, t, &s_skip)) continue;
-        const uint32_t rep0 = (uint32_t)sg.tile * K;
-        int phase = dwt_on ? (int)(sg.s_begin % a.dwt_period) : 1;
-        for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
-            const float2 at = __ldg(a.alpha_tab + (s - a.alpha_base));
-            const bool dwt = dwt_on && phase == 0;
-            if (dwt && tid < K)
-                t.thc[tid] = 2.0f * (hw - dwt_theta(a.seed, rep0 + tid, s));
-            if (kMode == MODE_LATTICE2D) {
-                // colours 0, 1 in the 2x2 blocks; colours 2, 3 (+ DWT) in the
-                // shifted blocks
-                block_pass_even<Store, K>(t.xs, a.wnib, at.x, a.Q);
-                __syncthreads();
-                block_pass_odd<Store, K>(t.xs, a.wnib, at.x, a.Q, a.Wd, m0, dm, dwt, t.thc, W2, at.y);
-                __syncthreads();
-            } else {
-                if (kMode == MODE_GENERAL) {
-                    // sequential conflict-free search: colours in order (eq. (11))
-                    for (int c = 0; c < a.C; ++c) {
-                        general_colour<Store, K>(a, t.xs, c, at.x);
-                        __syncthreads();
-                    }
-                } else {
-                    // simultaneous generalized-gradient step over all edges (eq. (8))
-                    for (int k = tid; k < n * K; k += nt) t.acc[k] = 0.0f;
-                    __syncthreads();
-                    for (int c = 0; c < a.C; ++c) {
-                        const int e1 = a.off[c + 1];
-                        for (int e = a.off[c] + tid; e < e1; e += nt) {
-                            const uint32_t rec = __ldg(a.ij + e);
-                            const float aw = at.x * (float)__ldg(a.w + e);
-                            const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
-                            float xi[K], xj[K];
-                            ldk<K>(t.xs + (size_t)i * K, xi);
-                            ldk<K>(t.xs + (size_t)j * K, xj);
-#pragma unroll
-                            for (int r = 0; r < K; ++r) {
-                                const float d = __fadd_rn(xi[r], -xj[r]);
-                                const float mm = __fadd_rn(d, -rint_fast(d));
-                                const float st = (mm >= 0.0f) ? aw : -aw;
-                                t.acc[(size_t)i * K + r] += st;
-                                t.acc[(size_t)j * K + r] -= st;
-                            }
-                        }
-                        __syncthreads();  // one colour is a matching: no shared vertex
-                    }
-                    for (int v = tid; v < n; v += nt) {
-                        float x[K];
-                        ldk<K>(t.xs + (size_t)v * K, x);
-#pragma unroll
-                        for (int r = 0; r < K; ++r) x[r] = wrap_c(__fadd_rn(x[r], t.acc[(size_t)v * K + r]));
-                        stk<K>(t.xs + (size_t)v * K, x);
-                    }
-                    __syncthreads();
-                }
-                if (dwt) {
-                    if (a.C == 0) __syncthreads();
-                    for (int v = tid; v < n; v += nt) {
-                        float x[K];
-                        ldk<K>(t.xs + (size_t)v * K, x);
-                        dwt_apply<K>(x, t.thc, W2, at.y);
-                        stk<K>(t.xs + (size_t)v * K, x);
-                    }
-                    __syncthreads();
-                }
-            }
-            if (dwt_on && ++phase == a.dwt_period) phase = 0;
-        }
-        seg_end<Store, K>(a, sg, t);
+        run_segment<Store, K, kMode>(a.v, sg, smem, &s_skip, a.ready, a.err, a.wait_limit_ns);
+    }
+}
+
+// ---------------------------------------------------------------- batch kernel
+// Many instances of uneven size: the instances of one (storage, K, mode)
+// class share a persistent launch whose CTAs take the next unit (instance,
+// tile, sweep range, flags) from a queue ordered by decreasing cost and run
+// it (a whole trial, or a chunk with the state kept in global memory);
+// shared memory is sized for the class's largest tile.
+template <typename Store, int K, int kMode>
+__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs b)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_skip, s_unit;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(b.counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();  // all threads read s_unit before it is overwritten
+        if (u >= b.n_units) break;
+        const BatchUnit bu = b.units[u];
+        const InstView &v = b.insts[bu.inst];
+        const Segment sg{bu.tile, bu.flags, bu.s_begin, bu.s_end};
+        run_segment<Store, K, kMode>(v, sg, smem, &s_skip, nullptr, nullptr, 0);
     }
 }
 
 // ---------------------------------------------------------------- finalize
-__global__ void __launch_bounds__(1024) finalize_kernel(const FinalArgs a)
+// Best replica (max cut, ties -> lowest index), energy H = W - 2 cut, and
+// the spins of that replica at its best bisector, in original vertex order.
+__device__ void finalize_body(int replicas, int K, int storage, int P, int n, int64_t W,
+                              const void *state, int64_t stride, const int32_t *orig_of,
+                              const int64_t *cut, const int32_t *bestp, int64_t *best, int8_t *spins)
 {
     __shared__ long long s_cut[1024];
     __shared__ int s_rep[1024];
     const int tid = threadIdx.x, nt = blockDim.x;
-    long long best = LLONG_MIN;
+    long long bc = LLONG_MIN;
     int br = 0x7FFFFFFF;
-    for (int r = tid; r < a.replicas; r += nt) {
-        const long long c = a.cut[r];
-        if (c > best || (c == best && r < br)) { best = c; br = r; }
+    for (int r = tid; r < replicas; r += nt) {
+        const long long c = cut[r];
+        if (c > bc || (c == bc && r < br)) { bc = c; br = r; }
     }
-    s_cut[tid] = best;
+    s_cut[tid] = bc;
     s_rep[tid] = br;
     __syncthreads();
     for (int o = nt / 2; o > 0; o >>= 1) {
@@ -669,20 +1013,34 @@ __global__ void __launch_bounds__(1024) finalize_kernel(const FinalArgs a)
     const int rb = s_rep[0];
     const long long cb = s_cut[0];
     if (tid == 0) {
-        a.best[0] = cb;
-        a.best[1] = a.W - 2 * cb;
-        a.best[2] = rb;
+        best[0] = cb;
+        best[1] = W - 2 * cb;
+        best[2] = rb;
     }
-    const int tile = rb / a.K, lane = rb % a.K;
-    const uint32_t B = (uint32_t)(((uint64_t)a.bestp[rb] << 31) / (uint64_t)a.P);
-    for (int v = tid; v < a.n; v += nt) {
-        const size_t idx = (size_t)tile * a.state_tile_stride + (size_t)v * a.K + lane;
-        float g;
-        if (a.storage == 0) g = reinterpret_cast<const float *>(a.state)[idx];
-        else g = __half2float(reinterpret_cast<const __half *>(a.state)[idx]);
-        const uint32_t q = phase_q(g);
-        a.spins[a.orig_of[v]] = ((uint32_t)(q - B) < 0x80000000u) ? 1 : -1;
+    const int tile = rb / K, lane = rb % K;
+    const uint32_t B = (uint32_t)(((uint64_t)bestp[rb] << 31) / (uint64_t)P);
+    for (int v = tid; v < n; v += nt) {
+        const size_t idx = (size_t)tile * stride + (size_t)v * K + lane;
+        uint32_t q;
+        if (storage == 0) q = phase_q(reinterpret_cast<const float *>(state)[idx]);
+        else if (storage == 1) q = phase_q(__half2float(reinterpret_cast<const __half *>(state)[idx]));
+        else q = (uint32_t)reinterpret_cast<const uint16_t *>(state)[idx] << 16;
+        spins[orig_of[v]] = ((uint32_t)(q - B) < 0x80000000u) ? 1 : -1;
     }
+}
+
+__global__ void __launch_bounds__(1024) finalize_kernel(const FinalArgs a)
+{
+    finalize_body(a.replicas, a.K, a.storage, a.P, a.n, a.W, a.state, a.state_tile_stride, a.orig_of,
+                  a.cut, a.bestp, a.best, a.spins);
+}
+
+__global__ void __launch_bounds__(1024) batch_finalize_kernel(const InstView *insts, const BatchFinal *fin)
+{
+    const InstView &v = insts[blockIdx.x];
+    const BatchFinal &f = fin[blockIdx.x];
+    finalize_body(v.replicas, v.K, f.storage, v.P, v.n, f.W, v.state, v.state_tile_stride, v.orig_of,
+                  v.cut, v.bestp, f.best, f.spins);
 }
 
 // ---------------------------------------------------------------- host side
@@ -734,10 +1092,14 @@ static int occ_one(int threads, size_t smem)
             if ((K) == 1) COSM_DISPATCH_M(float, 1, MODE, CALL);    \
             if ((K) == 2) COSM_DISPATCH_M(float, 2, MODE, CALL);    \
             if ((K) == 4) COSM_DISPATCH_M(float, 4, MODE, CALL);    \
-        } else {                                                    \
+        } else if ((STORAGE) == 1) {                                \
             if ((K) == 2) COSM_DISPATCH_M(__half, 2, MODE, CALL);   \
             if ((K) == 4) COSM_DISPATCH_M(__half, 4, MODE, CALL);   \
             if ((K) == 8) COSM_DISPATCH_M(__half, 8, MODE, CALL);   \
+        } else {                                                    \
+            if ((K) == 2) COSM_DISPATCH_M(uint16_t, 2, MODE, CALL); \
+            if ((K) == 4) COSM_DISPATCH_M(uint16_t, 4, MODE, CALL); \
+            if ((K) == 8) COSM_DISPATCH_M(uint16_t, 8, MODE, CALL); \
         }                                                           \
     } while (0)
 
@@ -768,6 +1130,63 @@ int sweep_launch(const LaunchCfg &cfg, const KernelArgs &a, void *stream)
 int finalize_launch(const FinalArgs &a, void *stream)
 {
     finalize_kernel<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+// Raises a batch kernel's dynamic shared-memory limit once per size (not
+// again while a launch is being captured into a graph).
+template <typename Store, int K, int M>
+static int batch_set_smem(size_t smem)
+{
+    static size_t set_bytes = 0;
+    if (smem > 48 * 1024 && smem > set_bytes) {
+        if (cudaFuncSetAttribute(batch_kernel<Store, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem) != cudaSuccess)
+            return -1;
+        set_bytes = smem;
+    }
+    return 0;
+}
+
+template <typename Store, int K, int M>
+static int batch_occ_one(int threads, size_t smem)
+{
+    auto fn = batch_kernel<Store, K, M>;
+    if (batch_set_smem<Store, K, M>(smem)) return 0;
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess) return 0;
+    return blocks;
+}
+
+template <typename Store, int K, int M>
+static int batch_launch_one(int grid, int threads, size_t smem, const BatchArgs &b, void *stream)
+{
+    auto fn = batch_kernel<Store, K, M>;
+    if (batch_set_smem<Store, K, M>(smem)) return -1;
+    fn<<<grid, threads, smem, reinterpret_cast<cudaStream_t>(stream)>>>(b);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int batch_occupancy(int storage, int K, int mode, int threads, size_t smem)
+{
+#define BOCC_CALL(T, KK, M) batch_occ_one<T, KK, M>(threads, smem)
+    COSM_DISPATCH(storage, K, mode, BOCC_CALL);
+#undef BOCC_CALL
+    return 0;
+}
+
+int batch_launch(int storage, int K, int mode, int grid, int threads, size_t smem, const BatchArgs &b,
+                 void *stream)
+{
+#define BLAUNCH_CALL(T, KK, M) batch_launch_one<T, KK, M>(grid, threads, smem, b, stream)
+    COSM_DISPATCH(storage, K, mode, BLAUNCH_CALL);
+#undef BLAUNCH_CALL
+    return -1;
+}
+
+int batch_finalize_launch(int count, const InstView *insts, const BatchFinal *fin, void *stream)
+{
+    batch_finalize_kernel<<<count, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(insts, fin);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

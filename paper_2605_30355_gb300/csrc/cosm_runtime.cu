@@ -12,95 +12,18 @@
 #include <vector>
 
 #include "../../include/cosm.h"
+#include "cosm_handle.h"
 #include "cosm_internal.h"
 
 using namespace cosm;
 
 static thread_local std::string g_err;
 
-static int fail(int code, const std::string &msg)
+int cosm::fail(int code, const std::string &msg)
 {
     g_err = msg;
     return code;
 }
-
-#define CK(call)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess)                                                            \
-            return fail(COSM_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
-    } while (0)
-
-template <typename T>
-struct DevBuf {
-    T *p = nullptr;
-    size_t cap = 0;  // elements
-    int ensure(size_t count)
-    {
-        if (count <= cap && p) return COSM_OK;
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-        if (cudaMalloc((void **)&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(COSM_ERR_NOMEM, "cudaMalloc failed");
-        }
-        cap = std::max<size_t>(count, 1);
-        return COSM_OK;
-    }
-    void release()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-};
-
-struct cosm_handle {
-    Graph g;                        // host copy, original vertex ids
-    cosm_params prm;
-    int device = 0;
-    int num_sms = 0;
-    bool lattice = false;
-    int64_t W = 0;                  // total weight
-    std::vector<int32_t> slot_of;   // original id -> slot
-    std::vector<int32_t> orig_of;   // slot -> original id
-    int32_t off[kMaxColors + 1] = {0};
-    int32_t C = 0;
-    DevBuf<uint32_t> d_ij;
-    DevBuf<int8_t> d_w;
-    DevBuf<int32_t> d_orig;
-    int mode = MODE_GENERAL_;       // kernel variant
-    int32_t Q = 0, Wd = 0;          // 2D lattice geometry
-    DevBuf<uint8_t> d_wnib;         // 2D lattice block weight bits
-    // per run
-    DevBuf<unsigned char> d_state;
-    DevBuf<int64_t> d_cut;
-    DevBuf<int32_t> d_bestp;
-    DevBuf<float2> d_alpha;
-    DevBuf<Segment> d_segs;
-    DevBuf<int32_t> d_segoff;
-    DevBuf<int32_t> d_ready;
-    DevBuf<int32_t> d_err;
-    DevBuf<int64_t> d_best;
-    DevBuf<int8_t> d_spins;
-    // cached host tables
-    int64_t alpha_S = -1;
-    double alpha_a0 = -1, alpha_ratio = -1;
-    std::vector<Segment> h_segs;
-    std::vector<int32_t> h_segoff;
-    int64_t sched_tiles = -1, sched_S = -1, sched_G = -1;
-    bool segs_uploaded = false;
-    // state of the last launch
-    int replicas = 0;
-    int K = 0, threads = 0, occupancy = 0, grid = 0;
-    size_t smem = 0;
-    int64_t tile_stride = 0;  // storage elements per tile
-    uint64_t seed = 0;
-    bool have_state = false, have_result = false;
-    cudaStream_t stream = nullptr;
-    int launches = 0;
-};
 
 extern "C" const char *cosm_last_error(void) { return g_err.c_str(); }
 
@@ -131,8 +54,8 @@ static int check_params(const cosm_params *p)
         return fail(COSM_ERR_INVALID_ARG, "window_deg must be in (0, 180]");
     if (p->n_bisectors < 1 || p->n_bisectors > kMaxBisectors)
         return fail(COSM_ERR_INVALID_ARG, "n_bisectors must be in [1, 256]");
-    if (p->storage != COSM_F32 && p->storage != COSM_F16)
-        return fail(COSM_ERR_INVALID_ARG, "storage must be COSM_F32 or COSM_F16");
+    if (p->storage != COSM_F32 && p->storage != COSM_F16 && p->storage != COSM_Q16)
+        return fail(COSM_ERR_INVALID_ARG, "storage must be COSM_F32, COSM_F16 or COSM_Q16");
     if (p->flags & ~(COSM_NO_DWT | COSM_NO_SCS)) return fail(COSM_ERR_INVALID_ARG, "unknown flags");
     return COSM_OK;
 }
@@ -195,7 +118,7 @@ extern "C" void cosm_destroy(cosm_handle *h)
 {
     if (!h) return;
     if (h->stream || h->have_state) cudaStreamSynchronize(h->stream);
-    h->d_ij.release(); h->d_w.release(); h->d_orig.release(); h->d_state.release();
+    h->d_ij.release(); h->d_w.release(); h->d_orig.release(); h->d_off.release(); h->d_state.release();
     h->d_cut.release(); h->d_bestp.release(); h->d_alpha.release(); h->d_segs.release();
     h->d_segoff.release(); h->d_ready.release(); h->d_err.release(); h->d_best.release();
     h->d_spins.release();
@@ -214,7 +137,9 @@ static int setup_lattice2d(cosm_handle *h)
     const Graph &g = h->g;
     h->mode = (h->prm.flags & COSM_NO_SCS) ? MODE_ACCUM_ : MODE_GENERAL_;
     if (std::getenv("COSM_NO_LATTICE")) return COSM_OK;
-    if (!h->lattice || g.dims[2] != 0 || h->mode != MODE_GENERAL_ || h->C != 4) return COSM_OK;
+    // the full torus only (every block needs its four edges)
+    if (!h->lattice || g.dims[2] != 0 || h->mode != MODE_GENERAL_ || h->C != 4 || g.m != 2 * (int64_t)g.n)
+        return COSM_OK;
     for (int64_t e = 0; e < g.m; ++e)
         if (g.w[(size_t)e] != 1 && g.w[(size_t)e] != -1) return COSM_OK;
     std::vector<int32_t> pat((size_t)g.m);
@@ -327,7 +252,8 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if ((rc = h->d_ij.ensure((size_t)g.m)) || (rc = h->d_w.ensure((size_t)g.m)) ||
-        (rc = h->d_orig.ensure((size_t)g.n)) || (rc = h->d_err.ensure(1)) ||
+        (rc = h->d_orig.ensure((size_t)g.n)) || (rc = h->d_off.ensure((size_t)h->C + 1)) ||
+        (rc = h->d_err.ensure(1)) ||
         (rc = h->d_best.ensure(4)) || (rc = h->d_spins.ensure((size_t)g.n))) {
         cosm_destroy(h);
         return rc;
@@ -335,7 +261,9 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
     if (cudaMemcpy(h->d_ij.p, ij.data(), ij.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_w.p, wv.data(), wv.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(h->d_orig.p, h->orig_of.data(), (size_t)g.n * 4, cudaMemcpyHostToDevice) !=
-            cudaSuccess) {
+            cudaSuccess ||
+        cudaMemcpy(h->d_off.p, h->off, ((size_t)h->C + 1) * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(h->d_err.p, 0, 4) != cudaSuccess) {
         cosm_destroy(h);
         return fail(COSM_ERR_CUDA, "copying the graph to the device failed");
     }
@@ -349,7 +277,7 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
 
 // ------------------------------------------------------------------ layout
 
-static int env_int(const char *name, int dflt)
+int cosm::env_int(const char *name, int dflt)
 {
     const char *s = std::getenv(name);
     return (s && *s) ? std::atoi(s) : dflt;
@@ -357,7 +285,7 @@ static int env_int(const char *name, int dflt)
 
 // Replicas per CTA (K) and threads per CTA: maximise resident replicas per
 // SM (COSM_K / COSM_THREADS override for experiments).
-static int choose_layout(cosm_handle *h, int replicas)
+int cosm::choose_layout(cosm_handle *h, int replicas)
 {
     const cosm_params &p = h->prm;
     const int mode = h->mode;
@@ -376,7 +304,11 @@ static int choose_layout(cosm_handle *h, int replicas)
         if (smem > 227 * 1024) continue;
         int T = forceT ? forceT : std::min(1024, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
         if (!forceT && T > 512) T = 512;
-        if (mode == MODE_LATTICE2D_ && !forceT) T = std::min(512, std::max(64, (h->Q + 31) / 32 * 32));
+        if (mode == MODE_LATTICE2D_ && !forceT) {
+            T = std::min(512, std::max(64, (h->Q + 31) / 32 * 32));
+            // a multiple of the block-row width fixes each thread's column
+            if (h->Wd <= T && (T / h->Wd) * h->Wd >= T / 2) T = (T / h->Wd) * h->Wd;
+        }
         int occ = sweep_occupancy(p.storage, K, mode, T, smem);
         while (occ == 0 && T > 64 && !forceT) {
             T /= 2;
@@ -407,7 +339,7 @@ static int choose_layout(cosm_handle *h, int replicas)
     return COSM_OK;
 }
 
-static int ensure_run_buffers(cosm_handle *h, int replicas)
+int cosm::ensure_run_buffers(cosm_handle *h, int replicas)
 {
     const size_t esz = h->prm.storage == COSM_F32 ? 4 : 2;
     const int64_t tiles = (replicas + h->K - 1) / h->K;
@@ -419,32 +351,43 @@ static int ensure_run_buffers(cosm_handle *h, int replicas)
     return COSM_OK;
 }
 
+InstView cosm::inst_view(cosm_handle *h)
+{
+    InstView v;
+    std::memset(&v, 0, sizeof(v));
+    v.n = h->g.n;
+    v.C = h->C;
+    v.off = h->d_off.p;
+    v.ij = h->d_ij.p;
+    v.w = h->d_w.p;
+    v.orig_of = h->d_orig.p;
+    v.wnib = h->d_wnib.p;
+    v.Q = h->Q;
+    v.Wd = h->Wd;
+    v.seed = h->seed;
+    v.replicas = h->replicas;
+    v.dwt_period = (h->prm.flags & COSM_NO_DWT) ? 0 : h->prm.dwt_period;
+    v.window = (float)(h->prm.window_deg / 360.0);
+    v.flags = h->prm.flags;
+    v.P = h->prm.n_bisectors;
+    v.mode = h->mode;
+    v.K = h->K;
+    v.qwin = (uint32_t)std::min(2147483648.0, std::floor(h->prm.window_deg / 360.0 * 4294967296.0 + 0.5));
+    v.state = h->d_state.p;
+    v.state_tile_stride = h->tile_stride;
+    v.cut = h->d_cut.p;
+    v.bestp = h->d_bestp.p;
+    return v;
+}
+
 static KernelArgs base_args(cosm_handle *h)
 {
     KernelArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.n = h->g.n;
-    a.C = h->C;
-    std::memcpy(a.off, h->off, sizeof(a.off));
-    a.ij = h->d_ij.p;
-    a.w = h->d_w.p;
-    a.orig_of = h->d_orig.p;
-    a.state = h->d_state.p;
-    a.state_tile_stride = h->tile_stride;
-    a.seed = h->seed;
-    a.replicas = h->replicas;
-    a.dwt_period = (h->prm.flags & COSM_NO_DWT) ? 0 : h->prm.dwt_period;
-    a.window = (float)(h->prm.window_deg / 360.0);
-    a.flags = h->prm.flags;
-    a.P = h->prm.n_bisectors;
+    a.v = inst_view(h);
     a.ready = h->d_ready.p;
     a.err = h->d_err.p;
     a.wait_limit_ns = (uint64_t)env_int("COSM_WAIT_LIMIT_S", 20) * 1000000000ull;
-    a.cut = h->d_cut.p;
-    a.bestp = h->d_bestp.p;
-    a.wnib = h->d_wnib.p;
-    a.Q = h->Q;
-    a.Wd = h->Wd;
     return a;
 }
 
@@ -518,15 +461,19 @@ static void build_schedule(cosm_handle *h, int64_t tiles, int64_t S, int64_t G)
     h->sched_G = G;
 }
 
-static int upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st)
+int cosm::upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st)
 {
     const double a0 = h->prm.alpha0_deg / 360.0, ratio = h->prm.dwt_ratio;
     if (h->alpha_S == S && h->alpha_a0 == a0 && h->alpha_ratio == ratio) return COSM_OK;
     std::vector<float2> tab((size_t)S);
+    const bool q16 = h->prm.storage == COSM_Q16;
     for (int64_t s = 1; s <= S; ++s) {
-        // linear ramp alpha_0 -> 0 (Table IX), FP64 rounded once to FP32
+        // linear ramp alpha_0 -> 0 (Table IX), FP64 rounded once to FP32, or
+        // for fixed-point phases rounded to the nearest 2^-16-turn quantum
         const double a = (S <= 1) ? a0 : a0 * (double)(S - s) / (double)(S - 1);
-        tab[(size_t)(s - 1)] = make_float2((float)a, (float)(ratio * a));
+        tab[(size_t)(s - 1)] = q16 ? make_float2((float)std::floor(a * 65536.0 + 0.5),
+                                                 (float)std::floor(ratio * a * 65536.0 + 0.5))
+                                   : make_float2((float)a, (float)(ratio * a));
     }
     int rc = h->d_alpha.ensure((size_t)S);
     if (rc) return rc;
@@ -538,7 +485,7 @@ static int upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st)
     return COSM_OK;
 }
 
-static int launch_finalize(cosm_handle *h, cudaStream_t st)
+int cosm::launch_finalize(cosm_handle *h, cudaStream_t st)
 {
     FinalArgs f;
     f.n = h->g.n;
@@ -583,9 +530,9 @@ extern "C" int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64
     if (waits) CK(cudaMemsetAsync(h->d_ready.p, 0, (size_t)tiles * 4, st));
     CK(cudaMemsetAsync(h->d_err.p, 0, 4, st));
     KernelArgs a = base_args(h);
-    a.alpha_tab = h->d_alpha.p;
-    a.alpha_base = 1;
-    a.S = sweeps;
+    a.v.alpha_tab = h->d_alpha.p;
+    a.v.alpha_base = 1;
+    a.v.S = sweeps;
     a.segs = h->d_segs.p;
     a.seg_off = h->d_segoff.p;
     LaunchCfg cfg{h->mode, h->prm.storage, h->K, h->threads, (int)(h->h_segoff.size() - 1), h->smem, waits};
@@ -663,10 +610,14 @@ extern "C" int cosm_get_state(cosm_handle *h, double *phases)
                 float f;
                 std::memcpy(&f, raw.data() + idx * 4, 4);
                 g = f;
-            } else {
+            } else if (h->prm.storage == COSM_F16) {
                 __half hv;
                 std::memcpy(&hv, raw.data() + idx * 2, 2);
                 g = (double)__half2float(hv);
+            } else {
+                uint16_t q;
+                std::memcpy(&q, raw.data() + idx * 2, 2);
+                g = (double)q / 65536.0;  // fixed point: already a turn in [0, 1)
             }
             out[(size_t)r * h->g.n + v] = to_turn(g);
         }
@@ -702,9 +653,12 @@ extern "C" int cosm_set_state(cosm_handle *h, const double *phases, int32_t repl
             if (esz == 4) {
                 const float f = (float)g;
                 std::memcpy(raw.data() + idx * 4, &f, 4);
-            } else {
+            } else if (h->prm.storage == COSM_F16) {
                 const __half hv = __float2half_rn((float)g);
                 std::memcpy(raw.data() + idx * 2, &hv, 2);
+            } else {
+                const uint16_t q = (uint16_t)((uint32_t)std::floor(x * 65536.0 + 0.5) & 0xFFFFu);
+                std::memcpy(raw.data() + idx * 2, &q, 2);
             }
         }
     }
@@ -732,9 +686,9 @@ static int launch_on_state(cosm_handle *h, int32_t flags, int64_t s0, int64_t s1
     if (rc) return rc;
     CK(cudaMemsetAsync(h->d_err.p, 0, 4, st));
     KernelArgs a = base_args(h);
-    a.alpha_tab = tab;
-    a.alpha_base = base;
-    a.S = s1;
+    a.v.alpha_tab = tab;
+    a.v.alpha_base = base;
+    a.v.S = s1;
     a.segs = h->d_segs.p;
     a.seg_off = h->d_segoff.p;
     LaunchCfg cfg{h->mode, h->prm.storage, h->K, h->threads, (int)tiles, h->smem, false};
@@ -754,7 +708,10 @@ extern "C" int cosm_step(cosm_handle *h, int64_t sweep, float alpha, void *strea
     int rc;
     DevBuf<float2> tab;  // one-entry step table for this sweep
     if ((rc = tab.ensure(1))) return rc;
-    const float2 v = make_float2(alpha, (float)(h->prm.dwt_ratio * (double)alpha));
+    const float2 v = h->prm.storage == COSM_Q16
+                         ? make_float2((float)std::floor((double)alpha * 65536.0 + 0.5),
+                                       (float)std::floor(h->prm.dwt_ratio * (double)alpha * 65536.0 + 0.5))
+                         : make_float2(alpha, (float)(h->prm.dwt_ratio * (double)alpha));
     if (h->stream) CK(cudaStreamSynchronize(h->stream));
     if (cudaMemcpy(tab.p, &v, sizeof(v), cudaMemcpyHostToDevice) != cudaSuccess) {
         tab.release();
@@ -807,4 +764,385 @@ extern "C" int cosm_solve(const cosm_graph_desc *g, const cosm_params *p, int64_
     if (!rc && replica_cuts) rc = cosm_get_replica_cuts(h, replica_cuts, nullptr);
     cosm_destroy(h);
     return rc;
+}
+
+// ====================================================================== batch
+// Many instances of uneven size run together. Each instance is a handle as
+// above; its replica tiles form units (instance, tile) = one whole trial of
+// K replicas. Units of one (storage, K, kernel mode) class share a
+// persistent launch whose CTAs drain a queue ordered by decreasing cost
+// (longest processing time first); class launches are forked on separate
+// streams so a class's tail overlaps the next class's start, and the whole
+// run -- counter resets, class kernels, per-instance finalisation -- is
+// captured once into a CUDA graph and replayed while the layout is unchanged.
+
+struct BatchClass {
+    int storage, K, mode;
+    int threads;        // threads per CTA
+    size_t smem;        // largest tile of the class
+    int grid;           // CTAs (resident capacity, capped by units)
+    int32_t unit0, units;
+};
+
+struct cosm_batch {
+    std::vector<cosm_handle *> hs;
+    std::vector<BatchClass> classes;
+    std::vector<BatchUnit> h_units;
+    DevBuf<BatchUnit> d_units;
+    DevBuf<InstView> d_insts;
+    DevBuf<BatchFinal> d_fin;
+    DevBuf<int32_t> d_counters;
+    std::vector<cudaStream_t> side;  // one per class (created on demand)
+    std::vector<cudaEvent_t> ev;     // fork + one per class
+    cudaStream_t own = nullptr;      // capture stream (the legacy stream cannot capture)
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> sig;        // layout signature of the captured graph
+    int policy = 0;                  // 0: per-instance layout rule, 1: smallest tile
+    int threads = 0;                 // 0: per-class rule, else forced
+    cudaStream_t last = nullptr;
+    bool have_result = false;
+    int64_t launches = 0;
+    int64_t graph_builds = 0;
+};
+
+extern "C" void cosm_batch_destroy(cosm_batch *b)
+{
+    if (!b) return;
+    if (b->own) cudaStreamSynchronize(b->own);
+    // instances first: their handles still name the batch's stream
+    for (cosm_handle *h : b->hs) {
+        h->stream = nullptr;
+        h->have_state = false;
+        cosm_destroy(h);
+    }
+    b->hs.clear();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    if (b->own) cudaStreamDestroy(b->own);
+    b->d_units.release(); b->d_insts.release(); b->d_fin.release(); b->d_counters.release();
+    delete b;
+}
+
+extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, const cosm_params *params,
+                                 int32_t shared_params, cosm_batch **out)
+{
+    if (!graphs || !params || !out || count < 1 || count > (1 << 20))
+        return fail(COSM_ERR_INVALID_ARG, "bad batch arguments");
+    *out = nullptr;
+    cosm_batch *b = new (std::nothrow) cosm_batch();
+    if (!b) return fail(COSM_ERR_NOMEM, "host allocation failed");
+    for (int32_t i = 0; i < count; ++i) {
+        cosm_handle *h = nullptr;
+        int rc = cosm_create(&graphs[i], shared_params ? &params[0] : &params[i], &h);
+        if (rc) {
+            std::string msg = "instance " + std::to_string(i) + ": " + g_err;
+            cosm_batch_destroy(b);
+            return fail(rc, msg);
+        }
+        b->hs.push_back(h);
+    }
+    if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess) {
+        cosm_batch_destroy(b);
+        return fail(COSM_ERR_CUDA, "stream creation failed");
+    }
+    *out = b;
+    return COSM_OK;
+}
+
+static int batch_layout(cosm_batch *b, const int64_t *sweeps, const int32_t *replicas, const uint64_t *seeds,
+                        cudaStream_t st)
+{
+    const int n = (int)b->hs.size();
+    std::vector<InstView> views((size_t)n);
+    std::vector<BatchFinal> fins((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        cosm_handle *h = b->hs[(size_t)i];
+        if (sweeps[i] < 1 || sweeps[i] >= ((int64_t)1 << 31) || replicas[i] < 1 || replicas[i] >= (1 << 24))
+            return fail(COSM_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": bad sweeps or replicas");
+        int rc;
+        if ((rc = choose_layout(h, replicas[i]))) return rc;
+        if (b->policy == 1 && h->K != (h->prm.storage == COSM_F32 ? 1 : 2)) {
+            // smallest tile of the storage type
+            const int Kmin = h->prm.storage == COSM_F32 ? 1 : 2;
+            const size_t esz = h->prm.storage == COSM_F32 ? 4 : 2;
+            h->K = Kmin;
+            h->smem = sweep_smem_bytes(h->prm.storage, Kmin, h->g.n, h->prm.n_bisectors, h->mode);
+            h->tile_stride = (int64_t)(((size_t)h->g.n * Kmin * esz + 15) / 16 * 16 / esz);
+        }
+        h->replicas = replicas[i];
+        h->seed = seeds[i];
+        if ((rc = ensure_run_buffers(h, replicas[i]))) return rc;
+        if ((rc = upload_alpha(h, sweeps[i], st))) return rc;
+        InstView v = inst_view(h);
+        v.alpha_tab = h->d_alpha.p;
+        v.alpha_base = 1;
+        v.S = sweeps[i];
+        views[(size_t)i] = v;
+        fins[(size_t)i] = BatchFinal{h->W, h->d_spins.p, h->d_best.p, h->prm.storage, 0};
+    }
+    // classes and their unit queues, longest trials first
+    b->classes.clear();
+    b->h_units.clear();
+    struct Key { int storage, K, mode; };
+    std::vector<Key> keys;
+    std::vector<int> cls((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        const cosm_handle *h = b->hs[(size_t)i];
+        int c = -1;
+        for (size_t k = 0; k < keys.size(); ++k)
+            if (keys[k].storage == h->prm.storage && keys[k].K == h->K && keys[k].mode == h->mode) c = (int)k;
+        if (c < 0) {
+            keys.push_back(Key{h->prm.storage, h->K, h->mode});
+            c = (int)keys.size() - 1;
+        }
+        cls[(size_t)i] = c;
+    }
+    int dev_sms = b->hs[0]->num_sms;
+    for (size_t c = 0; c < keys.size(); ++c) {
+        BatchClass bc{keys[c].storage, keys[c].K, keys[c].mode, 0, 0, 0, (int32_t)b->h_units.size(), 0};
+        std::vector<std::pair<double, BatchUnit>> us;
+        int max_ec = 0;
+        for (int i = 0; i < n; ++i) {
+            if (cls[(size_t)i] != (int)c) continue;
+            const cosm_handle *h = b->hs[(size_t)i];
+            bc.smem = std::max(bc.smem, h->smem);
+            for (int cc = 0; cc < h->C; ++cc) max_ec = std::max(max_ec, h->off[cc + 1] - h->off[cc]);
+            const int64_t tiles = (replicas[i] + h->K - 1) / h->K;
+            const double cost = (double)h->g.m * (double)h->K * (double)sweeps[i];
+            for (int64_t t = 0; t < tiles; ++t)
+                us.push_back({cost, BatchUnit{i, (int32_t)t, SEG_INIT | SEG_READOUT | SEG_STORE, 0, 1, sweeps[i]}});
+        }
+        std::stable_sort(us.begin(), us.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+        for (auto &u : us) b->h_units.push_back(u.second);
+        bc.units = (int32_t)us.size();
+        int T = b->threads;
+        if (!T) T = std::min(512, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
+        int occ = batch_occupancy(bc.storage, bc.K, bc.mode, T, bc.smem);
+        while (occ == 0 && T > 64) {
+            T /= 2;
+            occ = batch_occupancy(bc.storage, bc.K, bc.mode, T, bc.smem);
+        }
+        if (occ == 0) return fail(COSM_ERR_TOO_LARGE, "a batch tile does not fit on an SM");
+        bc.threads = T;
+        bc.grid = (int)std::min<int64_t>((int64_t)occ * dev_sms, bc.units);
+        b->classes.push_back(bc);
+    }
+    int rc;
+    if ((rc = b->d_insts.ensure((size_t)n)) || (rc = b->d_fin.ensure((size_t)n)) ||
+        (rc = b->d_units.ensure(b->h_units.size())) || (rc = b->d_counters.ensure(b->classes.size())))
+        return rc;
+    CK(cudaMemcpyAsync(b->d_insts.p, views.data(), views.size() * sizeof(InstView), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->d_fin.p, fins.data(), fins.size() * sizeof(BatchFinal), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(b->d_units.p, b->h_units.data(), b->h_units.size() * sizeof(BatchUnit),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // host tables are released on return
+    return COSM_OK;
+}
+
+// Records the class launches and the finaliser on `st` (captured or not).
+static int batch_enqueue(cosm_batch *b, cudaStream_t st)
+{
+    const size_t nc = b->classes.size();
+    while (b->side.size() < nc) {
+        cudaStream_t s;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        b->side.push_back(s);
+    }
+    while (b->ev.size() < nc + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->ev.push_back(e);
+    }
+    CK(cudaMemsetAsync(b->d_counters.p, 0, nc * 4, st));
+    CK(cudaEventRecord(b->ev[0], st));
+    for (size_t c = 0; c < nc; ++c) {
+        const BatchClass &bc = b->classes[c];
+        CK(cudaStreamWaitEvent(b->side[c], b->ev[0], 0));
+        BatchArgs a{b->d_insts.p, b->d_units.p + bc.unit0, bc.units, b->d_counters.p + c};
+        if (bc.units > 0 && batch_launch(bc.storage, bc.K, bc.mode, bc.grid, bc.threads, bc.smem, a, b->side[c]))
+            return fail(COSM_ERR_CUDA, std::string("batch launch: ") + cudaGetErrorString(cudaGetLastError()));
+        CK(cudaEventRecord(b->ev[c + 1], b->side[c]));
+    }
+    for (size_t c = 0; c < nc; ++c) CK(cudaStreamWaitEvent(st, b->ev[c + 1], 0));
+    if (batch_finalize_launch((int)b->hs.size(), b->d_insts.p, b->d_fin.p, st))
+        return fail(COSM_ERR_CUDA, std::string("batch finalize: ") + cudaGetErrorString(cudaGetLastError()));
+    return COSM_OK;
+}
+
+extern "C" int cosm_batch_run(cosm_batch *b, const int64_t *sweeps, const int32_t *replicas,
+                              const uint64_t *seeds, void *stream)
+{
+    if (!b || !sweeps || !replicas || !seeds) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
+    cudaStream_t st = b->own;
+    // order the batch after earlier work on the caller's stream
+    cudaEvent_t e0;
+    CK(cudaEventCreateWithFlags(&e0, cudaEventDisableTiming));
+    CK(cudaEventRecord(e0, user));
+    CK(cudaStreamWaitEvent(st, e0, 0));
+    cudaEventDestroy(e0);
+    int rc = batch_layout(b, sweeps, replicas, seeds, st);
+    if (rc) return rc;
+    std::vector<int64_t> sig;
+    sig.push_back((int64_t)(uintptr_t)b->d_insts.p);
+    sig.push_back((int64_t)(uintptr_t)b->d_units.p);
+    sig.push_back((int64_t)(uintptr_t)b->d_counters.p);
+    for (const BatchClass &bc : b->classes) {
+        sig.push_back(bc.storage); sig.push_back(bc.K); sig.push_back(bc.mode); sig.push_back(bc.threads);
+        sig.push_back((int64_t)bc.smem); sig.push_back(bc.grid); sig.push_back(bc.unit0); sig.push_back(bc.units);
+    }
+    if (!b->exec || sig != b->sig) {
+        if (b->exec) {
+            cudaGraphExecDestroy(b->exec);
+            b->exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        rc = batch_enqueue(b, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (ce != cudaSuccess) return fail(COSM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&b->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) return fail(COSM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        b->sig = sig;
+        b->graph_builds++;
+    }
+    CK(cudaGraphLaunch(b->exec, st));
+    cudaEvent_t e1;
+    CK(cudaEventCreateWithFlags(&e1, cudaEventDisableTiming));
+    CK(cudaEventRecord(e1, st));
+    CK(cudaStreamWaitEvent(user, e1, 0));
+    cudaEventDestroy(e1);
+    for (cosm_handle *h : b->hs) {
+        h->stream = st;
+        h->have_state = true;
+        h->have_result = true;
+    }
+    b->last = st;
+    b->have_result = true;
+    b->launches = (int64_t)b->classes.size() + 1;
+    return COSM_OK;
+}
+
+extern "C" int cosm_batch_sync(cosm_batch *b)
+{
+    if (!b) return fail(COSM_ERR_INVALID_ARG, "NULL batch");
+    CK(cudaStreamSynchronize(b->own));
+    return COSM_OK;
+}
+
+extern "C" int cosm_batch_get_best(cosm_batch *b, int32_t i, int64_t *cut, int64_t *energy, int32_t *replica,
+                                   int8_t *spins)
+{
+    if (!b || i < 0 || i >= (int32_t)b->hs.size()) return fail(COSM_ERR_INVALID_ARG, "bad instance index");
+    if (!b->have_result) return fail(COSM_ERR_STATE, "no batch run yet");
+    return cosm_get_best(b->hs[(size_t)i], cut, energy, replica, spins);
+}
+
+extern "C" int cosm_batch_get_replica_cuts(cosm_batch *b, int32_t i, int64_t *cuts, int32_t *best_p)
+{
+    if (!b || i < 0 || i >= (int32_t)b->hs.size()) return fail(COSM_ERR_INVALID_ARG, "bad instance index");
+    if (!b->have_result) return fail(COSM_ERR_STATE, "no batch run yet");
+    return cosm_get_replica_cuts(b->hs[(size_t)i], cuts, best_p);
+}
+
+extern "C" int cosm_batch_get_state(cosm_batch *b, int32_t i, double *phases)
+{
+    if (!b || i < 0 || i >= (int32_t)b->hs.size()) return fail(COSM_ERR_INVALID_ARG, "bad instance index");
+    return cosm_get_state(b->hs[(size_t)i], phases);
+}
+
+// Autotuner: times short runs of the whole batch (probe_sweeps sweeps per
+// instance, the caller's replica counts) for each tile policy and thread
+// count and keeps the fastest. With COSM_TUNE_CACHE set, choices are read
+// from / appended to that text file, keyed by the batch's shape.
+extern "C" int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t probe_sweeps, void *stream)
+{
+    if (!b || !replicas || probe_sweeps < 1) return fail(COSM_ERR_INVALID_ARG, "bad tuning arguments");
+    const size_t n = b->hs.size();
+    uint64_t key = 1469598103934665603ull;  // FNV-1a over the batch's shape
+    auto mix = [&](uint64_t x) {
+        for (int k = 0; k < 8; ++k) { key ^= (x >> (8 * k)) & 0xFF; key *= 1099511628211ull; }
+    };
+    for (size_t i = 0; i < n; ++i) {
+        const cosm_handle *h = b->hs[i];
+        mix((uint64_t)h->g.n); mix((uint64_t)h->g.m); mix((uint64_t)h->C); mix((uint64_t)h->mode);
+        mix((uint64_t)h->prm.storage); mix((uint64_t)replicas[i]);
+    }
+    const char *cache = std::getenv("COSM_TUNE_CACHE");
+    if (cache) {
+        FILE *f = std::fopen(cache, "r");
+        if (f) {
+            unsigned long long k;
+            int pol, thr;
+            while (std::fscanf(f, "%llx %d %d", &k, &pol, &thr) == 3)
+                if (k == key) {
+                    b->policy = pol;
+                    b->threads = thr;
+                    std::fclose(f);
+                    return COSM_OK;
+                }
+            std::fclose(f);
+        }
+    }
+    std::vector<int64_t> sw(n, probe_sweeps);
+    std::vector<uint64_t> seeds(n, 12345);
+    float best_ms = 1e30f;
+    int best_pol = 0, best_thr = 0;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int pols[2] = {0, 1}, thrs[4] = {0, 128, 256, 512};
+    for (int pol : pols)
+        for (int thr : thrs) {
+            b->policy = pol;
+            b->threads = thr;
+            int rc = cosm_batch_run(b, sw.data(), replicas, seeds.data(), stream);  // warm-up + graph build
+            if (rc) continue;
+            CK(cudaEventRecord(e0, b->own));
+            rc = cosm_batch_run(b, sw.data(), replicas, seeds.data(), stream);
+            CK(cudaEventRecord(e1, b->own));
+            CK(cudaEventSynchronize(e1));
+            if (rc) continue;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_pol = pol;
+                best_thr = thr;
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->policy = best_pol;
+    b->threads = best_thr;
+    if (cache) {
+        FILE *f = std::fopen(cache, "a");
+        if (f) {
+            std::fprintf(f, "%llx %d %d\n", (unsigned long long)key, best_pol, best_thr);
+            std::fclose(f);
+        }
+    }
+    return COSM_OK;
+}
+
+extern "C" int cosm_batch_info(cosm_batch *b, int64_t out[8])
+{
+    if (!b || !out) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    out[0] = (int64_t)b->hs.size();
+    out[1] = (int64_t)b->classes.size();
+    out[2] = (int64_t)b->h_units.size();
+    out[3] = b->launches;
+    out[4] = b->graph_builds;
+    out[5] = b->policy;
+    out[6] = b->threads;
+    int64_t ctas = 0;
+    for (const BatchClass &bc : b->classes) ctas += bc.grid;
+    out[7] = ctas;
+    return COSM_OK;
 }

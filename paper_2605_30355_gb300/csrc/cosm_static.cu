@@ -115,12 +115,13 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
     const size_t o_segs = align256(o_alpha + (size_t)sweeps * sizeof(float2));
     const size_t o_segoff = align256(o_segs + (size_t)tiles * sizeof(Segment));
     const size_t o_err = align256(o_segoff + (size_t)(tiles + 1) * 4);
-    const size_t total = align256(o_err + 4);
+    const size_t o_off = align256(o_err + 4);
+    const size_t total = align256(o_off + (size_t)(g.C + 1) * 4);
     if (total > kScratchBytes)
         return fail(COSM_ERR_TOO_LARGE,
                     "graph, step table and work list need " + std::to_string(total) +
                         " bytes of scratch; the static scratch holds " + std::to_string(kScratchBytes) +
-                        " (5 m + 4 n + 8 sweeps + 28 ceil(replicas / tile) bytes, 256-aligned parts)");
+                        " (5 m + 4 n + 8 sweeps + 28 ceil(replicas / tile) + 4 colours bytes, 256-aligned parts)");
     unsigned char *base = nullptr;
     if ((rc = scratch_address(&base))) return rc;
 
@@ -161,8 +162,14 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
                             {o_orig, orig.data(), orig.size() * 4}, {o_alpha, tab.data(), tab.size() * sizeof(float2)},
                             {o_segs, segs.data(), segs.size() * sizeof(Segment)},
                             {o_segoff, segoff.data(), segoff.size() * 4}};
+    std::vector<int32_t> offs((size_t)g.C + 1);
+    for (int c = 0; c <= g.C; ++c) offs[(size_t)c] = (int32_t)count[(size_t)c];
     for (const Piece &pc : pieces) {
         cudaError_t e = cudaMemcpyAsync(base + pc.off, pc.src, pc.bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return fail(COSM_ERR_CUDA, std::string("copy to scratch: ") + cudaGetErrorString(e));
+    }
+    {
+        cudaError_t e = cudaMemcpyAsync(base + o_off, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) return fail(COSM_ERR_CUDA, std::string("copy to scratch: ") + cudaGetErrorString(e));
     }
     cudaError_t e = cudaMemsetAsync(base + o_err, 0, 4, st);  // the error word starts at zero
@@ -170,30 +177,33 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
 
     KernelArgs a;
     std::memset(&a, 0, sizeof(a));
-    a.n = g.n;
-    a.C = g.C;
-    for (int c = 0; c <= g.C; ++c) a.off[c] = (int32_t)count[(size_t)c];
-    a.ij = reinterpret_cast<const uint32_t *>(base + o_ij);
-    a.w = reinterpret_cast<const int8_t *>(base + o_w);
-    a.orig_of = reinterpret_cast<const int32_t *>(base + o_orig);
-    a.state = base;  // no segment loads or stores the state
-    a.state_tile_stride = 0;
-    a.alpha_tab = reinterpret_cast<const float2 *>(base + o_alpha);
-    a.alpha_base = 1;
-    a.S = sweeps;
-    a.seed = seed;
-    a.replicas = replicas;
-    a.dwt_period = (p->flags & COSM_NO_DWT) ? 0 : p->dwt_period;
-    a.window = (float)(p->window_deg / 360.0);
-    a.flags = p->flags;
-    a.P = p->n_bisectors;
+    InstView &v = a.v;
+    v.n = g.n;
+    v.C = g.C;
+    v.off = reinterpret_cast<const int32_t *>(base + o_off);
+    v.ij = reinterpret_cast<const uint32_t *>(base + o_ij);
+    v.w = reinterpret_cast<const int8_t *>(base + o_w);
+    v.orig_of = reinterpret_cast<const int32_t *>(base + o_orig);
+    v.state = base;  // no segment loads or stores the state
+    v.state_tile_stride = 0;
+    v.alpha_tab = reinterpret_cast<const float2 *>(base + o_alpha);
+    v.alpha_base = 1;
+    v.S = sweeps;
+    v.seed = seed;
+    v.replicas = replicas;
+    v.dwt_period = (p->flags & COSM_NO_DWT) ? 0 : p->dwt_period;
+    v.window = (float)(p->window_deg / 360.0);
+    v.flags = p->flags;
+    v.P = p->n_bisectors;
+    v.mode = mode;
+    v.K = K;
+    v.cut = replica_cuts;
+    v.bestp = best_p;
     a.segs = reinterpret_cast<const Segment *>(base + o_segs);
     a.seg_off = reinterpret_cast<const int32_t *>(base + o_segoff);
     a.ready = reinterpret_cast<int32_t *>(base + o_err);  // no segment waits or signals
     a.err = reinterpret_cast<int32_t *>(base + o_err);
     a.wait_limit_ns = 0;
-    a.cut = replica_cuts;
-    a.bestp = best_p;
     LaunchCfg cfg{mode, p->storage, K, threads, (int)tiles, smem, false};
     if (sweep_launch(cfg, a, st))
         return fail(COSM_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(cudaGetLastError()));

@@ -382,3 +382,36 @@ def test_metrics_match_paper_tables(orc):
         if tt != "-":
             assert orc.ttt(float(tt), ps) == pytest.approx(ttt_, rel=tol)
     assert orc.r99(1.0) == 1.0
+
+
+# ------------------------------------------------------------------ fixed point
+
+def test_q16_mode_equals_fp64_on_grid_inputs(orc):
+    # with grid phases and a grid step every FP64 operation is exact, so the
+    # fixed-point mode must reproduce the FP64 sweep bit for bit
+    inst = instances.random_regular(300, 3, 6)
+    g = orc.coloured(inst)
+    x0 = orc.q16_grid(orc.init_phases(inst.n, 4, 1))
+    a = 417 / 65536
+    for s in (1, 2, 3):
+        xq, _ = orc.sweep(g, x0, a, s, seed=4, replica=1, dwt_ratio=0.5 * 2, storage=orc.STORE_Q16)
+        xf, _ = orc.sweep(g, x0, a, s, seed=4, replica=1, dwt_ratio=1.0)
+        assert np.array_equal(xq, xf)
+        assert np.array_equal(np.floor(xq * 65536), xq * 65536)
+        x0 = xq
+
+
+def test_q16_step_rounds_to_nearest_grid_point(orc):
+    fm = _graph(orc, 2, [(0, 1, -1)], [0])
+    x0 = [0.5, 0.25]
+    for frac, expect in ((0.49, 100), (0.51, 101), (0.0, 100)):
+        a = (100 + frac) / 65536
+        x, _ = orc.sweep(fm, x0, a, 1, flags=orc.NO_DWT, storage=orc.STORE_Q16)
+        np.testing.assert_array_equal(x, [0.5 - expect / 65536, 0.25 + expect / 65536])
+
+
+def test_q16_trials_reach_planted_optimum(orc):
+    inst = instances.gauge_planted(instances.torus2d(16, 16, 3), 4)
+    g = orc.coloured(inst)
+    cuts, *_ = orc.trials(g, 1000, 16, seed=5, storage=orc.STORE_Q16)
+    assert cuts.max() == inst.meta["opt_cut"]

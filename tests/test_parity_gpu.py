@@ -94,6 +94,26 @@ def test_one_sweep_f32(cosm, orc, name, make, dims, sweep):
     assert total_ties <= 0.001 * g.m * R
 
 
+@pytest.mark.parametrize("alpha0_deg", [25.0, 40.0])
+@pytest.mark.parametrize("sweep", [1, 3])
+def test_one_sweep_lattice_large_steps(cosm, orc, alpha0_deg, sweep):
+    # larger steps (alpha0 of the planted runs, and beyond) keep phases
+    # further from their wrapped range inside a sweep
+    inst = instances.torus2d(12, 20, 9)
+    s, g = _solver(cosm, orc, inst, alpha0_deg=alpha0_deg, dwt_ratio=1.5)
+    assert s.layout()["lattice"] == 2
+    R = 9
+    x0 = np.stack([orc.init_phases(inst.n, 6, r) for r in range(R)])
+    s.set_state(x0, seed=6)
+    alpha = float(np.float32(alpha0_deg / 360.0))
+    s.step(sweep, alpha)
+    x1 = s.get_state()
+    for r in range(R):
+        err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=6, replica=r,
+                                 **_params_kw(s))
+        assert err <= TOL_F32, (r, err)
+
+
 @pytest.mark.parametrize("flags", [1, 2, 3])
 def test_one_sweep_ablation_flags(cosm, orc, flags):
     inst = instances.random_regular(600, 4, 8)
