@@ -197,6 +197,51 @@ def _peaks():
 
 # ---------------------------------------------------------------------- ours
 
+def success_stats(cuts, target, t_step, R):
+    """P_s, R99 and TTT = t_trial R99 (Appendix A) at the target cut and two
+    slightly lower ones, with t_trial the step time over the replicas."""
+    allc = np.concatenate(cuts) if isinstance(cuts, list) else np.asarray(cuts)
+    out = {"trials": int(allc.size), "best_cut": int(allc.max()), "mean_cut": float(allc.mean()),
+           "t_trial_s": t_step / R, "levels": []}
+    for tgt in (target, target - 2, target - 4):
+        ps = float((allc >= tgt).mean())
+        r = _r99(ps)
+        out["levels"].append({"cut": int(tgt), "P_s": ps, "R99": r if math.isfinite(r) else None,
+                              "TTT_s": t_step / R * r if math.isfinite(r) else None})
+    return out
+
+
+def measure_single(cosm, inst, col, C, prm, storage, R, S, steps, warmup, seed, local, stream, flush):
+    """Times `steps` full trials of R replicas (one cosm_run each) with CUDA
+    events on the launching stream, L2 flushed between steps."""
+    import torch
+    solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, **prm)
+    for _ in range(warmup):
+        solver.run(S, R, seed, stream)
+        solver.sync()
+    sampler = ClockSampler(local)
+    times, cuts = [], []
+    torch.cuda.synchronize()
+    sampler.start()
+    for k in range(steps):
+        flush.zero_()  # L2 flush between timed steps (not timed)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        solver.run(S, R, seed + 1000 * (k + 1), stream)
+        e1.record(stream)
+        e1.synchronize()
+        solver.sync()
+        times.append(e0.elapsed_time(e1) / 1000.0)
+        cuts.append(solver.replica_cuts()[0])
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    layout = solver.layout()
+    solver.close()
+    return {"t_step": sum(times) / len(times), "cuts": cuts, "clocks": clocks, "layout": layout}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -216,39 +261,15 @@ def run_ours(args):
     inst = builder()
     col, C = _colour(inst, args.workload)
     seed = rank_seed(1, rank)  # every rank runs its own independent replicas
-    solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, **prm)
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    for _ in range(args.warmup):
-        solver.run(S, R, seed, stream)
-        solver.sync()
-    layout = solver.layout()
-
-    sampler = ClockSampler(local)
-    times = []
-    step_cuts = []
     if ws > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    sampler.start()
-    for k in range(args.steps):
-        flush.zero_()  # L2 flush between timed steps (not timed)
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        solver.run(S, R, seed + 1000 * (k + 1), stream)
-        e1.record(stream)
-        e1.synchronize()
-        solver.sync()
-        times.append(e0.elapsed_time(e1) / 1000.0)
-        step_cuts.append(solver.replica_cuts()[0])
-    torch.cuda.synchronize()
-    clocks = sampler.stop()
+    m = measure_single(cosm, inst, col, C, prm, storage, R, S, args.steps, args.warmup, seed, local,
+                       stream, flush)
     if ws > 1:
         dist.barrier()
-    t_step = sum(times) / len(times)
+    t_step, layout, clocks = m["t_step"], m["layout"], m["clocks"]
     t_max = max_over_ranks(t_step, "cuda")
     updates = inst.m * S * R  # edge-replica updates per step per rank
     value = whole_job_rate(updates, ws, t_max)
@@ -267,6 +288,28 @@ def run_ours(args):
     if e2e_t is not None:
         e2e_t = max_over_ranks(e2e_t, "cuda")
 
+    # ---- the other phase-storage forms and the ragged batch ("batched")
+    forms = {}
+    if args.forms and args.workload == "torus20k" and not args.replicas and not args.sweeps:
+        for name, st in (("f16", cosm.F16), ("q16", cosm.Q16)):
+            if st == storage:
+                continue
+            f = measure_single(cosm, inst, col, C, prm, st, R, S, max(2, args.steps // 2), 1, seed,
+                               local, stream, flush)
+            forms[name] = {"value": whole_job_rate(updates, ws, max_over_ranks(f["t_step"], "cuda")),
+                           "unit": "updates/s", "ms_per_step": f["t_step"] * 1000.0,
+                           "replicas_per_cta": f["layout"]["K"],
+                           "roofline": roofline(cosm, inst, prm, st, f["layout"], updates, f["t_step"],
+                                                f["clocks"]),
+                           "clocks": f["clocks"]}
+            tgt = _targets().get(args.workload)
+            if tgt is not None:
+                forms[name]["success"] = success_stats(f["cuts"], tgt["cut"], f["t_step"], R)
+    batched = None
+    if args.forms and args.workload == "torus20k" and not args.replicas and not args.sweeps:
+        batched = measure_batch(cosm, args, rank, ws, local, stream, flush, steps=2, warmup=1,
+                                e2e=False)
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -276,14 +319,12 @@ def run_ours(args):
     tgt = _targets().get(args.workload)
     ttt = None
     if tgt is not None:
-        allc = np.concatenate(step_cuts)
-        ps = float((allc >= tgt["cut"]).mean())
-        t_trial = t_step / R
-        r = _r99(ps)
-        ttt = {"target_cut": tgt["cut"], "target_source": tgt["source"], "P_s": ps,
-               "trials": int(allc.size), "R99": r if math.isfinite(r) else None,
-               "t_trial_s": t_trial, "TTT_s": t_trial * r if math.isfinite(r) else None,
-               "best_cut": int(allc.max())}
+        st_ = success_stats(m["cuts"], tgt["cut"], t_step, R)
+        top = st_["levels"][0]
+        ttt = {"target_cut": tgt["cut"], "target_source": tgt["source"], "P_s": top["P_s"],
+               "trials": st_["trials"], "R99": top["R99"], "t_trial_s": st_["t_trial_s"],
+               "TTT_s": top["TTT_s"], "best_cut": st_["best_cut"], "mean_cut": st_["mean_cut"],
+               "levels": st_["levels"]}
 
     # ---- roofline of the sweep kernel: shared memory and FP32 issue
     roof = roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks)
@@ -307,6 +348,8 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "time_to_target": ttt,
+        "forms": forms or None,
+        "batched": batched,
         "paper_context": {"updates_per_s": 1.41e10, "hardware": "2x Xeon Gold 6544Y, 64 threads, FP32",
                           "source": "derived from Section III-A and Table II (G72/G77/G81)"},
     }
@@ -362,46 +405,35 @@ def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks):
 
 # ---------------------------------------------------------------------- batch
 
-def run_batch(args):
+def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e=True):
     """The ragged batch: every step is one cosm_batch_run over all instances."""
     import torch
-    import torch.distributed as dist
-
-    import paper_2605_30355_gb300 as cosm
-
-    ws, rank, local = _dist()
-    if ws > 1:
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
-    _, _, S, prm, desc = WORKLOADS[args.workload]
-    if args.sweeps:
+    _, _, S, prm, desc = WORKLOADS["batch512"]
+    if args.workload == "batch512" and args.sweeps:
         S = args.sweeps
-    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage]
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage] \
+        if args.workload == "batch512" else cosm.F32
     insts, reps = instances.ragged_batch(512, seed=0)
     seeds = np.arange(len(insts), dtype=np.uint64) + np.uint64(rank_seed(1, rank))
     t0 = time.perf_counter()
     batch = cosm.Batch(insts, storage=storage, **prm)
     create_s = time.perf_counter() - t0
-    stream = torch.cuda.Stream()
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     if not args.no_tune:
         batch.tune(reps, probe_sweeps=20, stream=stream)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.run(S, reps, seeds, stream)
         batch.sync()
     sampler = ClockSampler(local)
     times = []
-    if ws > 1:
-        dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        batch.run(S, reps, seeds + 7919 * (k + 1), stream)
+        batch.run(S, reps, seeds + np.uint64(7919 * (k + 1)), stream)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1000.0)
@@ -411,48 +443,71 @@ def run_batch(args):
     t_max = max_over_ranks(t_step, "cuda")
     updates = sum(int(i.m) * S * r for i, r in zip(insts, reps))
     info = batch.info()
-    # end to end: host instances -> create -> run -> every instance's best cut and spins
+    batch.close()
     e2e_t = None
     h2d = sum(i.src.nbytes + i.dst.nbytes + i.w.nbytes for i in insts)
     d2h = sum(i.n + 24 for i in insts)
-    if args.e2e_steps:
+    if e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         b2 = cosm.Batch(insts, storage=storage, **prm)
-        b2.run(S, reps, seeds + 1, stream)
+        b2.run(S, reps, seeds + np.uint64(1), stream)
         for i in range(len(insts)):
             b2.best(i)
         b2.close()
-        e2e_t = time.perf_counter() - t0
-    if rank != 0:
-        if ws > 1:
-            dist.destroy_process_group()
-        return None
+        e2e_t = max_over_ranks(time.perf_counter() - t0, "cuda")
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     mhz = clocks.get("sm_mhz") or 2070.0
     alu_peak = FP32_LANES_PER_SM * props.multi_processor_count * mhz * 1e6 / 1e12
     alu_ach = ALU_OPS_PER_UPDATE * updates / t_step / 1e12
-    line = {
-        "metric": "edge-replica updates/s (ragged batch, one graph-captured run)",
-        "value": whole_job_rate(updates, ws, t_max), "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max * 1000.0, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point"}[storage],
-        "data": "synthetic (seeded instance generator; no Gset files)",
-        "config": {"workload": args.workload, "description": desc, "instances": len(insts),
-                   "replicas_total": int(sum(reps)), "sweeps_per_trial": S,
-                   "edges_total": int(sum(i.m for i in insts)), "batch": info,
-                   "create_s": create_s, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"all instances on each of {ws} GPU(s), no collective"},
+    return {
+        "value": whole_job_rate(updates, ws, t_max), "unit": "updates/s", "ms_per_step": t_max * 1000.0,
+        "storage": args.storage if args.workload == "batch512" else "f32",
+        "description": desc, "instances": len(insts), "replicas_total": int(sum(reps)),
+        "sweeps_per_trial": S, "edges_total": int(sum(i.m for i in insts)), "batch": info,
+        "create_s": create_s, "steps": steps, "warmup": warmup, "clocks": clocks,
         "e2e": None if e2e_t is None else {
             "value": whole_job_rate(updates, ws, e2e_t), "unit": "updates/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "api": "cosm_batch_create + cosm_batch_run + get_best (host buffers)"},
-        "gpu_launches": int(info["launches"]) * args.steps,
-        "clocks": clocks,
         "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s",
                      "frac": alu_ach / alu_peak, "traffic": None, "ops_per_update": ALU_OPS_PER_UPDATE,
                      "peak_source": f"{FP32_LANES_PER_SM} FP32 lanes/SM x {props.multi_processor_count} "
                                     f"SMs x {mhz:.0f} MHz (median sampled SM clock)"},
+    }
+
+
+def run_batch(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2605_30355_gb300 as cosm
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    b = measure_batch(cosm, args, rank, ws, local, stream, flush, args.steps, args.warmup,
+                      e2e=bool(args.e2e_steps))
+    if rank != 0:
+        if ws > 1:
+            dist.destroy_process_group()
+        return None
+    line = {
+        "metric": "edge-replica updates/s (ragged batch, one graph-captured run)",
+        "value": b["value"], "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"f32": "f32", "f16": "f16-storage/f32-compute", "q16": "u16-fixed-point"}[b["storage"]],
+        "data": "synthetic (seeded instance generator; no Gset files)",
+        "config": {"workload": "batch512", "description": b["description"], "instances": b["instances"],
+                   "replicas_total": b["replicas_total"], "sweeps_per_trial": b["sweeps_per_trial"],
+                   "edges_total": b["edges_total"], "batch": b["batch"], "create_s": b["create_s"],
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"all instances on each of {ws} GPU(s), no collective"},
+        "e2e": b["e2e"], "gpu_launches": int(b["batch"]["launches"]) * args.steps,
+        "clocks": b["clocks"], "roofline": b["roofline"],
     }
     print(json.dumps(line))
     if ws > 1:
@@ -661,6 +716,8 @@ def main(argv=None):
                     help="edge-replica updates in the bounded oracle sample")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-tune", action="store_true", help="batch: skip the autotuner")
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="default workload: skip the FP16 / fixed-point forms and the ragged batch")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window")
     args = ap.parse_args(argv)
     if args.impl == "reference":
