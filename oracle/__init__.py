@@ -28,6 +28,8 @@ _lib = None
 
 NO_DWT = 1
 NO_SCS = 2
+DWT_RANDDIR = 4
+OPT_BISECTOR = 8
 STORE_F64 = 0
 STORE_F16 = 1
 STORE_Q16 = 2
@@ -75,6 +77,17 @@ def lib():
                 "orc_color_torus3d": (i32, [i32, i32, i32, i64, P, P, P]),
                 "orc_validate_partition": (i32, [i32, i64, P, P, i32, P]),
                 "orc_bruteforce_maxcut": (i64, [i32, i64, P, P, P, P]),
+                "orc_twist_dir": (C.c_int, [u64, i64, i64]),
+                "orc_sweep_h": (i64, [i32, i32, P, P, P, P, P, P, f64, i64, i32, f64, f64, u64, i64,
+                                      i32, i32, P, f64, P, i64]),
+                "orc_energy_h": (i64, [i32, i64, P, P, P, P, P]),
+                "orc_readout_fields": (i64, [i32, i64, P, P, P, P, P, P, P]),
+                "orc_binarize_opt": (i64, [i32, i64, P, P, P, P, P, P]),
+                "orc_binarize_opt_brute": (i64, [i32, i64, P, P, P, P, P, P]),
+                "orc_trial_ex": (i64, [i32, i32, P, P, P, P, P, i64, f64, i32, f64, f64, i32, u64,
+                                       i64, i32, i32, i32, P, P, P, P]),
+                "orc_trials_ex": (i32, [i32, i32, P, P, P, P, P, i64, f64, i32, f64, f64, i32, u64,
+                                        i64, i32, i32, i32, i32, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -209,15 +222,22 @@ def coloured(inst, color=None, C_=None):
 
 # ---------------------------------------------------------------- dynamics
 
+def _h(h):
+    return None if h is None else _i32(h)
+
+
 def sweep(g: ColouredGraph, x, alpha_, sweep_idx, *, dwt_period=3, dwt_ratio=0.5, window=0.25,
-          seed=0, replica=0, flags=0, storage=STORE_F64, force=None, tie_eps=0.0, max_ties=4096):
-    """One sweep in place on a copy; returns (x_new, near_ties)."""
+          seed=0, replica=0, flags=0, storage=STORE_F64, force=None, tie_eps=0.0, max_ties=4096,
+          h=None):
+    """One sweep in place on a copy; returns (x_new, near_ties). h: local
+    fields per vertex (None = none)."""
     x = np.array(x, dtype=np.float64, copy=True)
     ties = np.zeros(max_ties, dtype=np.int64)
     f = None if force is None else np.ascontiguousarray(force, dtype=np.int8)
-    nt = lib().orc_sweep(g.n, g.C, _p(g.off), _p(g.src), _p(g.dst), _p(g.w), _p(x), alpha_,
-                         sweep_idx, dwt_period, dwt_ratio, window, seed, replica, flags, storage,
-                         _p(f), tie_eps, _p(ties), max_ties)
+    hh = _h(h)
+    nt = lib().orc_sweep_h(g.n, g.C, _p(g.off), _p(g.src), _p(g.dst), _p(g.w), _p(hh), _p(x), alpha_,
+                           sweep_idx, dwt_period, dwt_ratio, window, seed, replica, flags, storage,
+                           _p(f), tie_eps, _p(ties), max_ties)
     if nt < 0:
         raise MemoryError
     return x, ties[:min(nt, max_ties)].copy()
@@ -266,6 +286,80 @@ def trials(g, S, replicas, *, alpha0=14 / 360, dwt_period=3, dwt_ratio=0.5, wind
                             dwt_period, dwt_ratio, window, P, seed, replicas, flags, storage,
                             threads, _p(cuts), _p(bps), _p(xs))
     return cuts, bps, xs, int(used)
+
+
+def twist_dir(seed: int, replica: int, sweep_idx: int) -> int:
+    return int(lib().orc_twist_dir(seed, replica, sweep_idx))
+
+
+def energy_h(n, src, dst, w, h, spins) -> int:
+    """Eq. (1) with local fields: sum w s_i s_j - sum h s."""
+    src, dst, w = _i32(src), _i32(dst), _i32(w)
+    s = np.ascontiguousarray(spins, dtype=np.int8)
+    hh = _h(h)
+    return int(lib().orc_energy_h(n, src.shape[0], _p(src), _p(dst), _p(w), _p(hh), _p(s)))
+
+
+def readout_fields(g, h, x):
+    """Fixed-semicircle readout: (energy, cut, spins)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    hh = _h(h)
+    c = np.zeros(1, dtype=np.int64)
+    spins = np.zeros(g.n, dtype=np.int8)
+    H = lib().orc_readout_fields(g.n, g.m, _p(g.src), _p(g.dst), _p(g.w), _p(hh), _p(x), _p(c),
+                                 _p(spins))
+    return int(H), int(c[0]), spins
+
+
+def binarize_opt(g, x, brute=False):
+    """Optimal bisector: (best cut, position B in 2^-32 turns, spins)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    c = np.zeros(1, dtype=np.int64)
+    spins = np.zeros(g.n, dtype=np.int8)
+    fn = lib().orc_binarize_opt_brute if brute else lib().orc_binarize_opt
+    B = fn(g.n, g.m, _p(g.src), _p(g.dst), _p(g.w), _p(x), _p(c), _p(spins))
+    if B < 0:
+        raise MemoryError
+    return int(c[0]), int(B), spins
+
+
+def n_readouts(S, track):
+    return (S + track - 1) // track if track > 0 else 0
+
+
+def trial_ex(g, S, *, alpha0=14 / 360, dwt_period=3, dwt_ratio=0.5, window=0.25, P=100, seed=0,
+             replica=0, flags=0, storage=STORE_F64, track=0, h=None):
+    """One trial with fields / tracking / optimal bisector. Returns a dict:
+    cut, energy, B, p, sweep (of the kept readout), x (final phases), spins
+    (of the kept readout), trace (energies of the readouts)."""
+    x = np.zeros(g.n, dtype=np.float64)
+    spins = np.zeros(g.n, dtype=np.int8)
+    out = np.zeros(5, dtype=np.int64)
+    tr = np.zeros(max(1, n_readouts(S, track)), dtype=np.int64)
+    hh = _h(h)
+    lib().orc_trial_ex(g.n, g.C, _p(g.off), _p(g.src), _p(g.dst), _p(g.w), _p(hh), S, alpha0,
+                       dwt_period, dwt_ratio, window, P, seed, replica, flags, storage, track,
+                       _p(x), _p(spins), _p(out), _p(tr))
+    return {"cut": int(out[0]), "energy": int(out[1]), "B": int(out[2]), "p": int(out[3]),
+            "sweep": int(out[4]), "x": x, "spins": spins, "trace": tr[:n_readouts(S, track)]}
+
+
+def trials_ex(g, S, replicas, *, alpha0=14 / 360, dwt_period=3, dwt_ratio=0.5, window=0.25, P=100,
+              seed=0, flags=0, storage=STORE_F64, track=0, h=None, threads=None, keep_x=False,
+              keep_spins=False):
+    """Many replicas of trial_ex: out [replicas][5] (cut, energy, B, p, sweep),
+    trace [replicas][readouts], x, spins (or None)."""
+    threads = threads or os.cpu_count() or 1
+    out = np.zeros((replicas, 5), dtype=np.int64)
+    nr = n_readouts(S, track)
+    tr = np.zeros((replicas, max(1, nr)), dtype=np.int64)
+    xs = np.zeros((replicas, g.n), dtype=np.float64) if keep_x else None
+    sp = np.zeros((replicas, g.n), dtype=np.int8) if keep_spins else None
+    hh = _h(h)
+    lib().orc_trials_ex(g.n, g.C, _p(g.off), _p(g.src), _p(g.dst), _p(g.w), _p(hh), S, alpha0,
+                        dwt_period, dwt_ratio, window, P, seed, replicas, flags, storage, track,
+                        threads, _p(out), _p(tr if nr else None), _p(xs), _p(sp))
+    return out, tr[:, :nr], xs, sp
 
 
 def bruteforce_maxcut(n, src, dst, w):

@@ -19,6 +19,10 @@
  *   - Binarization with equally spaced bisectors over a semicircle and the
  *     best cut (Alg. 1, Appendix B: 100 bisectors spaced 1.8 degrees).
  *   - Greedy edge colouring (Section II-B) and the regular lattice pattern.
+ *   - Local fields h of eq. (1), the fixed-semicircle readout and a random
+ *     twist direction (Sections II-A, II-B, II-D); the optimal bisector
+ *     (Section II-B, after Burer, Monteiro and Zhang 2002); mid-anneal
+ *     readouts with best tracking and an energy trace (Fig. 10).
  * Readings taken where the paper is silent are listed with each function.
  *
  * Random numbers: Philox4x32-10 written from Salmon, Moraes, Dror and Shaw,
@@ -184,6 +188,21 @@ int orc_in_window_q(double x, double theta, double W) { return orc_in_window(x, 
 
 #define ORC_NO_DWT 1
 #define ORC_NO_SCS 2
+#define ORC_DWT_RANDDIR 4
+#define ORC_OPT_BISECTOR 8
+
+/* Twist direction of the DWT event of sweep s of a replica when it is
+ * randomised (Section II-D allows either direction): word 1 of the Philox
+ * draw that gives theta_ref (counter (s, replica, 0, 1)); +1 when its top
+ * bit is clear, -1 when set. */
+int orc_twist_dir(uint64_t seed, int64_t replica, int64_t sweep)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)sweep, (uint32_t)replica, 0u, 1u};
+    uint32_t o[4];
+    orc_philox4x32_10(ctr, key, o);
+    return (o[1] >> 31) ? -1 : 1;
+}
 
 /*
  * One sweep of Alg. 1 on one replica, in place.
@@ -197,20 +216,29 @@ int orc_in_window_q(double x, double theta, double W) { return orc_in_window(x, 
  *   over all edges (eq. (8)), the ablation "without SCS" of Table VII.
  *   Then, when sweep % dwt_period == 0 and DWT is on, every phase inside the
  *   dual windows moves by +dwt_ratio * alpha (Section II-D; one direction).
+ * Local fields h (eq. (1); NULL = none). Reading: a field is a coupling
+ * J = h_v to a reference variable frozen at 0, so it acts through the same
+ * pair rule, eq. (6), on x_v alone. Its updates touch each vertex once and
+ * the reference never moves, so together they form one more conflict-free
+ * sub-sweep, taken after the C colours and before the DWT (with NO_SCS the
+ * field forces join the simultaneous step).
+ * With flag DWT_RANDDIR the twist direction of each DWT event is drawn
+ * (orc_twist_dir) instead of always +1 (Section II-D).
  * storage: 0 FP64, 1 binary16 storage rounding, 2 fixed point on the
  * 2^-16-turn grid (alpha and the twist rounded to the grid).
  * Near-ties: an edge whose angular difference is within tie_eps of 0 or 1/2
- * when processed, and a phase within tie_eps of a window edge, are recorded
- * in ties[] (edge e as e, vertex v as m + v). force[], when given, has m + n
- * entries: 0 = natural branch, +1/-1 = forced sign (edges) or forced
- * inside/outside (vertices).
+ * when processed, a phase within tie_eps of a window edge, and a phase with
+ * a field within tie_eps of 0 or 1/2, are recorded in ties[] (edge e as e,
+ * DWT vertex v as m + v, field vertex v as m + n + v). force[], when given,
+ * has m + n entries (m + 2n with fields): 0 = natural branch, +1/-1 = forced
+ * sign (edges, fields) or forced inside/outside (DWT vertices).
  * Returns the number of near-ties found (ties[] holds at most max_ties).
  */
-int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
-                  const int32_t *dst, const int32_t *w, double *x, double alpha,
-                  int64_t sweep, int32_t dwt_period, double dwt_ratio, double window,
-                  uint64_t seed, int64_t replica, int32_t flags, int32_t storage,
-                  const int8_t *force, double tie_eps, int64_t *ties, int64_t max_ties)
+int64_t orc_sweep_h(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
+                    const int32_t *dst, const int32_t *w, const int32_t *h, double *x, double alpha,
+                    int64_t sweep, int32_t dwt_period, double dwt_ratio, double window,
+                    uint64_t seed, int64_t replica, int32_t flags, int32_t storage,
+                    const int8_t *force, double tie_eps, int64_t *ties, int64_t max_ties)
 {
     int64_t m = off[C];
     int64_t nt = 0;
@@ -236,6 +264,19 @@ int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
                 x[j] = orc_store(orc_wrap(xj), storage);
             }
         }
+        if (h) {
+            for (int32_t v = 0; v < n; ++v) {
+                if (h[v] == 0) continue;
+                double J = (double)h[v];
+                int s = orc_sgn_b(x[v], 0.0);
+                if (tie_eps > 0.0 && orc_tie_distance(x[v], 0.0) < tie_eps) {
+                    if (nt < max_ties && ties) ties[nt] = m + n + v;
+                    ++nt;
+                }
+                if (force && force[m + n + v]) s = force[m + n + v];
+                x[v] = orc_store(orc_wrap(x[v] - alpha * J * (double)s), storage);
+            }
+        }
     } else {
         double *dx = (double *)calloc((size_t)n, sizeof(double));
         if (!dx) return -1;
@@ -251,11 +292,25 @@ int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
             dx[i] -= alpha * J * (double)s;
             dx[j] += alpha * J * (double)s;
         }
+        if (h) {
+            for (int32_t v = 0; v < n; ++v) {
+                if (h[v] == 0) continue;
+                int s = orc_sgn_b(x[v], 0.0);
+                if (tie_eps > 0.0 && orc_tie_distance(x[v], 0.0) < tie_eps) {
+                    if (nt < max_ties && ties) ties[nt] = m + n + v;
+                    ++nt;
+                }
+                if (force && force[m + n + v]) s = force[m + n + v];
+                dx[v] -= alpha * (double)h[v] * (double)s;
+            }
+        }
         for (int32_t v = 0; v < n; ++v) x[v] = orc_store(orc_wrap(x[v] + dx[v]), storage);
         free(dx);
     }
     if (!(flags & ORC_NO_DWT) && dwt_period > 0 && (sweep % dwt_period) == 0) {
         double theta = orc_theta(seed, replica, sweep);
+        double twist = step;
+        if (flags & ORC_DWT_RANDDIR) twist = (double)orc_twist_dir(seed, replica, sweep) * step;
         for (int32_t v = 0; v < n; ++v) {
             double dist = 1.0;
             int in = orc_in_window(x[v], theta, window, &dist);
@@ -264,10 +319,21 @@ int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
                 ++nt;
             }
             if (force && force[m + v]) in = force[m + v] > 0;
-            if (in) x[v] = orc_store(orc_wrap(x[v] + step), storage);
+            if (in) x[v] = orc_store(orc_wrap(x[v] + twist), storage);
         }
     }
     return nt;
+}
+
+/* The sweep of Alg. 1 without local fields. */
+int64_t orc_sweep(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
+                  const int32_t *dst, const int32_t *w, double *x, double alpha,
+                  int64_t sweep, int32_t dwt_period, double dwt_ratio, double window,
+                  uint64_t seed, int64_t replica, int32_t flags, int32_t storage,
+                  const int8_t *force, double tie_eps, int64_t *ties, int64_t max_ties)
+{
+    return orc_sweep_h(n, C, off, src, dst, w, 0, x, alpha, sweep, dwt_period, dwt_ratio, window,
+                       seed, replica, flags, storage, force, tie_eps, ties, max_ties);
 }
 
 /* Bisector binarization and exact cut (Alg. 1 final loop; Appendix B: P
@@ -320,6 +386,221 @@ int64_t orc_energy(int64_t m, const int32_t *src, const int32_t *dst, const int3
     int64_t H = 0;
     for (int64_t e = 0; e < m; ++e) H += (int64_t)w[e] * (int64_t)s[src[e]] * (int64_t)s[dst[e]];
     return H;
+}
+
+/* Ising energy eq. (1) with local fields, Max-Cut weights w = -J:
+ * H = sum_e w_e s_i s_j - sum_v h_v s_v (h NULL = no fields). */
+int64_t orc_energy_h(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *w,
+                     const int32_t *h, const int8_t *s)
+{
+    int64_t H = orc_energy(m, src, dst, w, s);
+    if (h)
+        for (int32_t v = 0; v < n; ++v) H -= (int64_t)h[v] * (int64_t)s[v];
+    return H;
+}
+
+static int64_t orc_total_weight(int64_t m, const int32_t *w)
+{
+    int64_t W = 0;
+    for (int64_t e = 0; e < m; ++e) W += (int64_t)w[e];
+    return W;
+}
+
+static uint32_t orc_q32(double x) { return (uint32_t)(uint64_t)floor(x * 4294967296.0); }
+
+/* Spins of a bisector at position B (2^-32 turns) on the circle:
+ * s_v = +1 iff ((q_v - B) mod 2^32) < 2^31, the half circle that starts at B. */
+static void orc_spins_at(int32_t n, const double *x, uint32_t B, int8_t *s)
+{
+    for (int32_t v = 0; v < n; ++v) s[v] = ((uint32_t)(orc_q32(x[v]) - B) < 0x80000000u) ? 1 : -1;
+}
+
+/* Readout of a problem with local fields (Section II-B: the fields fix the
+ * semicircles, so no bisector search is needed). Reading: the reference
+ * variable sits at 0 and s_v = +1 iff x_v lies in the half circle centred on
+ * it, [-1/4, 1/4) turns: the bisector at B = 3/4 turn (3 2^30). Returns H
+ * (eq. (1)); writes the cut and the spins when asked. */
+int64_t orc_readout_fields(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                           const int32_t *w, const int32_t *h, const double *x, int64_t *cut,
+                           int8_t *spins)
+{
+    int8_t *s = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!s) return INT64_MIN;
+    orc_spins_at(n, x, 0xC0000000u, s);
+    if (cut) *cut = orc_cut(m, src, dst, w, s);
+    int64_t H = orc_energy_h(n, m, src, dst, w, h, s);
+    if (spins) memcpy(spins, s, (size_t)n);
+    free(s);
+    return H;
+}
+
+/* Optimal bisector, brute force (the definition): the largest cut over
+ * every bisector position B in [0, 2^31) (the half circle from B and its
+ * complement give the same cut, so half a turn of positions covers all
+ * bisectors). The spins at B change only where B passes a point of some
+ * phase, so the cut is constant on [0, phi_1] and on every [phi_k + 1,
+ * phi_{k+1}] (phi_v = q_v mod 2^31, sorted), and the candidates are
+ * B = 0 and B = phi_v + 1 < 2^31; each is evaluated from scratch.
+ * Returns the best B (ties -> smallest B), writes the cut and spins. */
+int64_t orc_binarize_opt_brute(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                               const int32_t *w, const double *x, int64_t *best_cut, int8_t *spins)
+{
+    int8_t *s = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!s) return -1;
+    int64_t best = INT64_MIN;
+    uint32_t bestB = 0;
+    for (int32_t k = -1; k < n; ++k) {
+        uint32_t B = 0;
+        if (k >= 0) {
+            uint32_t phi = orc_q32(x[k]) & 0x7FFFFFFFu;
+            if (phi + 1u >= 0x80000000u) continue;
+            B = phi + 1u;
+        }
+        orc_spins_at(n, x, B, s);
+        int64_t c = orc_cut(m, src, dst, w, s);
+        if (c > best || (c == best && B < bestB)) { best = c; bestB = B; }
+    }
+    if (spins) orc_spins_at(n, x, bestB, spins);
+    if (best_cut) *best_cut = best;
+    free(s);
+    return (int64_t)bestB;
+}
+
+typedef struct { uint32_t pos; int64_t delta; } orc_event;
+
+static int orc_event_cmp(const void *a, const void *b)
+{
+    uint32_t pa = ((const orc_event *)a)->pos, pb = ((const orc_event *)b)->pos;
+    return (pa > pb) - (pa < pb);
+}
+
+/* Optimal bisector by one sorted sweep over the bisector positions, the
+ * procedure of Burer, Monteiro and Zhang (2002) (Section II-B cites it as
+ * the exact alternative to equally spaced bisectors). With phi_v = q_v mod
+ * 2^31 and t_v = q_v's top bit, s_v(B) = +1 iff [B <= phi_v] xor t_v, so edge
+ * (i, j) is cut at B iff (t_i xor t_j) xor [lo < B <= hi] (lo, hi = the
+ * smaller and larger of phi_i, phi_j). Starting from the cut at B = 0, every
+ * edge contributes d_e = w_e (1 - 2 (t_i xor t_j)) on the interval
+ * (lo, hi]: +d_e at position lo + 1, -d_e at hi + 1. Sorting these 2m
+ * events (the library sort) and summing them in order gives the cut at
+ * every position where it can change. Same result and tie rule as the brute
+ * force above. */
+int64_t orc_binarize_opt(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                         const int32_t *w, const double *x, int64_t *best_cut, int8_t *spins)
+{
+    orc_event *ev = (orc_event *)malloc(sizeof(orc_event) * (size_t)(2 * m > 0 ? 2 * m : 1));
+    if (!ev) return -1;
+    int64_t c0 = 0, k = 0;
+    for (int64_t e = 0; e < m; ++e) {
+        uint32_t qi = orc_q32(x[src[e]]), qj = orc_q32(x[dst[e]]);
+        int cross = (int)((qi >> 31) ^ (qj >> 31));
+        if (cross) c0 += (int64_t)w[e];
+        uint32_t pi = qi & 0x7FFFFFFFu, pj = qj & 0x7FFFFFFFu;
+        uint32_t lo = pi < pj ? pi : pj, hi = pi < pj ? pj : pi;
+        if (lo == hi) continue;
+        int64_t d = (int64_t)w[e] * (cross ? -1 : 1);
+        ev[k].pos = lo + 1u; ev[k].delta = d; ++k;
+        ev[k].pos = hi + 1u; ev[k].delta = -d; ++k;
+    }
+    qsort(ev, (size_t)k, sizeof(orc_event), orc_event_cmp);
+    int64_t best = c0, cur = c0;
+    uint32_t bestB = 0;
+    for (int64_t a = 0; a < k;) {
+        uint32_t pos = ev[a].pos;
+        while (a < k && ev[a].pos == pos) cur += ev[a++].delta;
+        if (pos < 0x80000000u && cur > best) { best = cur; bestB = pos; }
+    }
+    free(ev);
+    if (spins) orc_spins_at(n, x, bestB, spins);
+    if (best_cut) *best_cut = best;
+    return (int64_t)bestB;
+}
+
+/* One readout of the current phases: with fields the fixed semicircle,
+ * with opt the optimal bisector, else the P bisectors. out: [0] cut,
+ * [1] energy H, [2] bisector position B, [3] bisector index p (-1 unless
+ * the P bisectors chose). */
+static void orc_readout(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
+                        const int32_t *w, const int32_t *h, int64_t W, const double *x, int32_t P,
+                        int opt, int64_t out[4], int8_t *spins)
+{
+    if (h) {
+        int64_t c = 0;
+        out[1] = orc_readout_fields(n, m, src, dst, w, h, x, &c, spins);
+        out[0] = c;
+        out[2] = 0xC0000000u;
+        out[3] = -1;
+    } else if (opt) {
+        int64_t c = 0;
+        out[2] = orc_binarize_opt(n, m, src, dst, w, x, &c, spins);
+        out[0] = c;
+        out[1] = W - 2 * c;
+        out[3] = -1;
+    } else {
+        int64_t c = 0;
+        int32_t p = orc_binarize(n, m, src, dst, w, x, P, 0, &c, spins);
+        out[0] = c;
+        out[1] = W - 2 * c;
+        out[2] = (int64_t)(((uint64_t)p << 31) / (uint64_t)P);
+        out[3] = p;
+    }
+}
+
+/* Readouts of one trial with mid-anneal best tracking: with track = T > 0
+ * the phases are read out after every sweep s with s mod T = 0 and after
+ * the last sweep S (the energy trajectories of Fig. 10 sample every 1000
+ * sweeps), each readout's energy goes to trace[k] (k = 0 .. ceil(S/T) - 1),
+ * and the replica keeps the readout of lowest energy (ties -> the earlier).
+ * Readouts use the fixed semicircle with fields, else the P bisectors; with
+ * flag OPT_BISECTOR a last readout at S with the optimal bisector competes
+ * too (it replaces the final P-bisector readout when track = 0).
+ * out: [0] cut, [1] energy, [2] B, [3] p or -1, [4] sweep of the kept
+ * readout. Returns the kept energy. */
+int64_t orc_trial_ex(int32_t n, int32_t C, const int64_t *off, const int32_t *src, const int32_t *dst,
+                     const int32_t *w, const int32_t *h, int64_t S, double alpha0, int32_t dwt_period,
+                     double dwt_ratio, double window, int32_t P, uint64_t seed, int64_t replica,
+                     int32_t flags, int32_t storage, int32_t track, double *x, int8_t *spins,
+                     int64_t *out, int64_t *trace)
+{
+    int64_t m = off[C], W = orc_total_weight(m, w);
+    int8_t *s_cur = (int8_t *)malloc((size_t)(n > 0 ? n : 1));
+    if (!s_cur) return INT64_MIN;
+    int opt = (flags & ORC_OPT_BISECTOR) && !h;
+    orc_init_phases(n, seed, replica, x);
+    for (int32_t v = 0; v < n; ++v) {
+        x[v] = orc_store(x[v], storage);
+        if (storage == 2) x[v] = floor(x[v] * 65536.0) / 65536.0; /* top 16 bits */
+    }
+    int64_t kept[5] = {0, INT64_MAX, 0, -1, 0};
+    int64_t k = 0;
+    for (int64_t s = 1; s <= S; ++s) {
+        double a = orc_alpha(s, S, alpha0);
+        orc_sweep_h(n, C, off, src, dst, w, h, x, a, s, dwt_period, dwt_ratio, window, seed, replica,
+                    flags, storage, 0, 0.0, 0, 0);
+        if (track > 0 && (s % track == 0 || s == S)) {
+            int64_t r[4];
+            orc_readout(n, m, src, dst, w, h, W, x, P, 0, r, s_cur);
+            if (trace) trace[k] = r[1];
+            ++k;
+            if (r[1] < kept[1]) {
+                memcpy(kept, r, sizeof(r));
+                kept[4] = s;
+                if (spins) memcpy(spins, s_cur, (size_t)n);
+            }
+        }
+    }
+    if (track <= 0 || opt) {
+        int64_t r[4];
+        orc_readout(n, m, src, dst, w, h, W, x, P, opt, r, s_cur);
+        if (track <= 0 || r[1] < kept[1]) {
+            memcpy(kept, r, sizeof(r));
+            kept[4] = S;
+            if (spins) memcpy(spins, s_cur, (size_t)n);
+        }
+    }
+    if (out) memcpy(out, kept, sizeof(kept));
+    free(s_cur);
+    return kept[1];
 }
 
 /* One full trial of Alg. 1 for one replica: random x, sweeps 1..S with the
@@ -386,6 +667,55 @@ int32_t orc_trials(int32_t n, int32_t C, const int64_t *off, const int32_t *src,
                      seed, flags, storage, t, replicas, threads, cuts, best_p, x_out};
         jobs[t] = j;
         pthread_create(&th[t], 0, orc_worker, &jobs[t]);
+    }
+    for (int32_t t = 0; t < threads; ++t) pthread_join(th[t], 0);
+    free(th); free(jobs);
+    return threads;
+}
+
+/* Many replicas of orc_trial_ex over host threads. out: [replicas][5],
+ * trace: [replicas][ceil(S/track)] (may be NULL), x_out: [replicas][n]. */
+typedef struct {
+    int32_t n, C; const int64_t *off; const int32_t *src, *dst, *w, *h;
+    int64_t S; double alpha0; int32_t dwt_period; double dwt_ratio, window; int32_t P;
+    uint64_t seed; int32_t flags, storage, track;
+    int64_t r0, r1, stride, n_trace; int64_t *out, *trace; double *x_out; int8_t *spins_out;
+} orc_job_ex;
+
+static void *orc_worker_ex(void *arg)
+{
+    orc_job_ex *j = (orc_job_ex *)arg;
+    double *x = (double *)malloc(sizeof(double) * (size_t)(j->n > 0 ? j->n : 1));
+    if (!x) return 0;
+    for (int64_t r = j->r0; r < j->r1; r += j->stride) {
+        orc_trial_ex(j->n, j->C, j->off, j->src, j->dst, j->w, j->h, j->S, j->alpha0, j->dwt_period,
+                     j->dwt_ratio, j->window, j->P, j->seed, r, j->flags, j->storage, j->track, x,
+                     j->spins_out ? j->spins_out + (size_t)r * (size_t)j->n : 0, j->out + 5 * r,
+                     j->trace ? j->trace + (size_t)r * (size_t)j->n_trace : 0);
+        if (j->x_out) memcpy(j->x_out + (size_t)r * (size_t)j->n, x, sizeof(double) * (size_t)j->n);
+    }
+    free(x);
+    return 0;
+}
+
+int32_t orc_trials_ex(int32_t n, int32_t C, const int64_t *off, const int32_t *src, const int32_t *dst,
+                      const int32_t *w, const int32_t *h, int64_t S, double alpha0, int32_t dwt_period,
+                      double dwt_ratio, double window, int32_t P, uint64_t seed, int64_t replicas,
+                      int32_t flags, int32_t storage, int32_t track, int32_t threads, int64_t *out,
+                      int64_t *trace, double *x_out, int8_t *spins_out)
+{
+    if (threads < 1) threads = 1;
+    if (threads > replicas) threads = (int32_t)(replicas > 0 ? replicas : 1);
+    int64_t n_trace = track > 0 ? (S + track - 1) / track : 0;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)threads);
+    orc_job_ex *jobs = (orc_job_ex *)malloc(sizeof(orc_job_ex) * (size_t)threads);
+    if (!th || !jobs) { free(th); free(jobs); return -1; }
+    for (int32_t t = 0; t < threads; ++t) {
+        orc_job_ex j = {n, C, off, src, dst, w, h, S, alpha0, dwt_period, dwt_ratio, window, P,
+                        seed, flags, storage, track, t, replicas, threads, n_trace, out, trace,
+                        x_out, spins_out};
+        jobs[t] = j;
+        pthread_create(&th[t], 0, orc_worker_ex, &jobs[t]);
     }
     for (int32_t t = 0; t < threads; ++t) pthread_join(th[t], 0);
     free(th); free(jobs);
