@@ -3,7 +3,7 @@
  * Collective Switched Motion, a heuristic for sparse Ising / Max-Cut.
  *
  * Problem (eq. (1), Appendix A): a graph G = (V, E) with integer Max-Cut
- * weights w_ij = -J_ij and no local fields. Cosm relaxes each spin to a
+ * weights w_ij = -J_ij and optional integer local fields h_i. Cosm relaxes each spin to a
  * phase on the circle, applies the finite-magnitude pair update of eq. (6)
  * one edge colour (matching) at a time (Section II-C, eqs. (9)-(12)),
  * perturbs with the dual window twist every DWT period sweeps (Section
@@ -54,9 +54,18 @@ extern "C" {
 #define COSM_Q16 2 /* fixed point: phases on the 2^-16-turn grid as u16,
                     * steps rounded to the grid, exact integer arithmetic   */
 
-/* ---- variant flags (ablations of Table VII) ---------------------------- */
-#define COSM_NO_DWT 1 /* no dual window twist                              */
-#define COSM_NO_SCS 2 /* simultaneous generalized-gradient step (eq. (8))  */
+/* ---- variant flags ------------------------------------------------------ */
+#define COSM_NO_DWT 1 /* no dual window twist (ablation, Table VII)         */
+#define COSM_NO_SCS 2 /* simultaneous generalized-gradient step (eq. (8);
+                       * ablation, Table VII)                               */
+#define COSM_DWT_RANDOM_DIR 4 /* draw each twist's direction (Section II-D):
+                       * -1 when the top bit of word 1 of the Philox draw
+                       * that gives the twist angle is set, else +1         */
+#define COSM_OPT_BISECTOR 8 /* final readout with the optimal bisector
+                       * (Section II-B, after Burer, Monteiro and Zhang
+                       * 2002): the best cut over every bisector position,
+                       * not only the n_bisectors equally spaced ones; not
+                       * with local fields                                  */
 
 /* Sparse graph plus its edge partition (Alg. 1 line 1; Section II-C).
  *  n        number of vertices, 2 <= n <= 65536
@@ -72,7 +81,13 @@ extern "C" {
  *           Every edge must be an edge of that torus (a subset is fine);
  *           the hint selects a shared-memory layout, and for the full 2D
  *           torus with +-1 weights and the regular colouring an
- *           implicit-index kernel. A hint that does not match is rejected. */
+ *           implicit-index kernel. A hint that does not match is rejected.
+ *  h        local fields h_i of eq. (1) (n entries, |h_i| <= 32767), or
+ *           NULL for none. A field acts as a coupling J = h_i to a reference
+ *           variable frozen at phase 0: one extra conflict-free sub-sweep
+ *           after the colours, and the readout is the fixed half circle
+ *           [-1/4, 1/4) turn around the reference (s_i = +1 there).
+ *           Single instances only (cosm_create, cosm_solve). */
 typedef struct cosm_graph_desc {
     int32_t n;
     int64_t m;
@@ -82,6 +97,7 @@ typedef struct cosm_graph_desc {
     int32_t n_colors;
     const int32_t *color;
     int32_t dims[3];
+    const int32_t *h;
 } cosm_graph_desc;
 
 /* Solver parameters (Tables IX-X; Appendix C).
@@ -91,7 +107,15 @@ typedef struct cosm_graph_desc {
  *  window_deg   width of each of the two DWT windows, (0, 180] (paper: 90)
  *  n_bisectors  bisectors over a semicircle at readout, 1..256 (paper: 100)
  *  storage      COSM_F32, COSM_F16 or COSM_Q16
- *  flags        COSM_NO_DWT | COSM_NO_SCS                                  */
+ *  flags        COSM_NO_DWT | COSM_NO_SCS | COSM_DWT_RANDOM_DIR |
+ *               COSM_OPT_BISECTOR
+ *  track_period 0: one readout after the last sweep. T > 0: mid-anneal best
+ *               tracking: a readout after every sweep s with s % T == 0 and
+ *               after the last sweep, each replica keeping the readout of
+ *               lowest energy (ties: the earlier) and its spins, and every
+ *               readout's energy recorded (cosm_get_trace; the energy
+ *               trajectories of Fig. 10 sample every 1000 sweeps). Single
+ *               instances only.                                            */
 typedef struct cosm_params {
     double alpha0_deg;
     double dwt_ratio;
@@ -100,7 +124,7 @@ typedef struct cosm_params {
     int32_t n_bisectors;
     int32_t storage;
     int32_t flags;
-    int32_t reserved;
+    int32_t track_period;
 } cosm_params;
 
 typedef struct cosm_handle cosm_handle;
@@ -131,16 +155,36 @@ int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64_t seed, vo
  * (COSM_ERR_TIMEOUT if a bounded wait between work segments gave up). */
 int cosm_sync(cosm_handle *h);
 
-/* Best replica of the last run or readout: maximum cut, ties to the
- * smallest replica index; energy H = sum w s_i s_j = W - 2 cut (eq. (1),
- * h = 0); spins (n entries of +1/-1, host or device) in original vertex
- * order, the rounding of that replica's phases at its best bisector.
+/* Best replica of the last run or readout: lowest energy, ties to the
+ * smallest replica index (without fields: the maximum cut); its cut, its
+ * energy H = sum w s_i s_j - sum h s_i = W - 2 cut - sum h s_i (eq. (1));
+ * spins (n entries of +1/-1, host or device) in original vertex order: the
+ * rounding of that replica's phases at the kept readout's bisector (with
+ * tracking, the spins saved when that readout was taken).
  * Any output pointer may be NULL. Synchronises. */
 int cosm_get_best(cosm_handle *h, int64_t *cut, int64_t *energy, int32_t *replica, int8_t *spins);
 
-/* Per-replica best cut and best bisector index of the last run or readout
- * (`replicas` entries each, host or device; either may be NULL). */
+/* Per-replica cut and bisector index of the kept readout of the last run
+ * or readout (`replicas` entries each, host or device; either may be NULL).
+ * The index is p of the bisector B_p = floor(p 2^31 / P) when the equally
+ * spaced bisectors chose it, -1 for the fixed half circle (local fields)
+ * and for the optimal bisector. */
 int cosm_get_replica_cuts(cosm_handle *h, int64_t *cuts, int32_t *best_p);
+
+/* Per-replica energy of eq. (1), fields included, of the kept readout
+ * (`replicas` entries, host or device). Synchronises. */
+int cosm_get_replica_energies(cosm_handle *h, int64_t *energies);
+
+/* Per-replica position of the kept readout's bisector, in 2^-32 turn: spin
+ * s_v = +1 iff ((floor(x_v 2^32) - B) mod 2^32) < 2^31 (`replicas`
+ * entries, host or device). Synchronises. */
+int cosm_get_replica_bisectors(cosm_handle *h, uint32_t *B);
+
+/* Energy trace of the last run with track_period = T > 0: row-major
+ * [replica][k], k = 0 .. ceil(sweeps / T) - 1, the energy of readout k
+ * (after sweep min((k + 1) T, sweeps)); `count` must equal replicas times
+ * that number (host or device). COSM_ERR_STATE without tracking. */
+int cosm_get_trace(cosm_handle *h, int64_t *trace, int64_t count);
 
 /* Exports all replicas' phases as FP64 turns in [0, 1), row-major
  * [replica][vertex] in original vertex order (host or device pointer).
@@ -158,9 +202,10 @@ int cosm_set_state(cosm_handle *h, const double *phases, int32_t replicas, uint6
  * COSM_Q16 both are rounded to the nearest 2^-16-turn quantum. */
 int cosm_step(cosm_handle *h, int64_t sweep, float alpha, void *stream);
 
-/* Bisector readout of the current state without sweeping (Alg. 1 final
- * loop), for replayed-state checks; results via cosm_get_best and
- * cosm_get_replica_cuts. */
+/* Readout of the current state without sweeping (Alg. 1 final loop: the
+ * equally spaced bisectors, the optimal bisector with COSM_OPT_BISECTOR,
+ * the fixed half circle with local fields), for replayed-state checks;
+ * results via cosm_get_best and cosm_get_replica_*. */
 int cosm_readout(cosm_handle *h, void *stream);
 
 /* One-shot call for host-resident inputs and outputs: create, run, read
@@ -175,7 +220,9 @@ typedef struct cosm_batch cosm_batch;
 
 /* Creates `count` instances, each exactly as cosm_create would (graphs[i];
  * params[i], or params[0] for all when shared_params != 0). Inputs are
- * copied. Errors as cosm_create, with the failing instance in the message. */
+ * copied. Local fields, tracking and COSM_OPT_BISECTOR are single-instance
+ * features (COSM_ERR_INVALID_ARG here). Errors as cosm_create, with the
+ * failing instance in the message. */
 int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, const cosm_params *params,
                       int32_t shared_params, cosm_batch **out);
 
@@ -268,7 +315,9 @@ int cosm_server_create(const cosm_server_config *cfg, cosm_server **out);
 /* Queues a request (the graph is copied): trials of `sweeps` sweeps and
  * `replicas` replicas each (Alg. 1 per replica), until a trial's best cut
  * >= target_cut or max_trials trials. Returns at once with *id.
- * COSM_ERR_TOO_LARGE if its footprint exceeds the whole budget. */
+ * COSM_ERR_TOO_LARGE if its footprint exceeds the whole budget;
+ * COSM_ERR_INVALID_ARG for local fields, tracking or COSM_OPT_BISECTOR
+ * (single-instance features). */
 int cosm_server_submit(cosm_server *s, const cosm_graph_desc *g, const cosm_params *p, int64_t sweeps,
                        int32_t replicas, uint64_t seed, int64_t target_cut, int32_t max_trials,
                        int64_t *id);
@@ -324,6 +373,19 @@ int cosm_color_torus3d(int32_t L1, int32_t L2, int32_t L3, int64_t m, const int3
 int cosm_validate_partition(int32_t n, int64_t m, const int32_t *src, const int32_t *dst,
                             int32_t n_colors, const int32_t *color);
 
+/* QUBO input (the general Ising form of eq. (1)): minimise
+ * f(x) = sum_k qv[k] x_qi[k] x_qj[k] over x in {0,1}^n, given as nnz
+ * triplets (duplicates add up; i == j is a linear term). With
+ * x_i = (1 + s_i) / 2 it becomes 4 f(x) = H(s) + offset, H of eq. (1) with
+ * Max-Cut weights w_ij = c_ij = Q_ij + Q_ji (i < j) and fields
+ * h_i = -(sum_j c_ij + 2 Q_ii), offset = sum c_ij + 2 sum Q_ii. Host code,
+ * no device work. src, dst, w: room for nnz edges (caller-owned, host);
+ * *m gets the edge count (pairs with c_ij != 0, sorted by (src, dst));
+ * h: n entries. Errors: INVALID_ARG (an index outside [0, n)), TOO_LARGE
+ * (a weight above 127 or a field above 32767 in magnitude). */
+int cosm_qubo_to_ising(int32_t n, int64_t nnz, const int32_t *qi, const int32_t *qj, const int64_t *qv,
+                       int32_t *src, int32_t *dst, int32_t *w, int64_t *m, int32_t *h, int64_t *offset);
+
 /* Measurement support (no counterpart in the paper): shared-memory read
  * bandwidth of the current device, for the roofline of the sweep kernel.
  * Two CTAs of 1024 threads per SM stream conflict-free 16-byte words
@@ -344,7 +406,9 @@ int cosm_probe_smem(int32_t iters, double *bytes_per_clk_per_sm, double *gbps);
  * (each part rounded up to 256 bytes); larger problems fail with
  * COSM_ERR_TOO_LARGE before any device work. It calls no cudaMalloc or
  * cudaFree. Inputs are host arrays as for cosm_create (the lattice hint is
- * ignored; color may be NULL for the greedy colouring); outputs are
+ * ignored; color may be NULL for the greedy colouring; no local fields,
+ * COSM_F32 or COSM_F16 storage, flags COSM_NO_DWT | COSM_NO_SCS only,
+ * track_period 0, else COSM_ERR_INVALID_ARG); outputs are
  * caller-owned DEVICE buffers of `replicas` entries: each replica's best
  * cut and best bisector index, the same values cosm_run + cosm_get_replica_cuts
  * give for that graph without a lattice hint. Asynchronous on `stream`.

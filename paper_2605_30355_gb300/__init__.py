@@ -36,6 +36,8 @@ F16 = 1
 Q16 = 2
 NO_DWT = 1
 NO_SCS = 2
+DWT_RANDOM_DIR = 4
+OPT_BISECTOR = 8
 
 #: every symbol include/cosm.h declares
 EXPORTS = (
@@ -47,7 +49,8 @@ EXPORTS = (
     "cosm_batch_get_best", "cosm_batch_get_replica_cuts", "cosm_batch_get_state", "cosm_batch_tune",
     "cosm_batch_info", "cosm_batch_destroy", "cosm_server_default_config", "cosm_server_create",
     "cosm_server_submit", "cosm_server_poll", "cosm_server_wait", "cosm_server_get_spins",
-    "cosm_server_stats", "cosm_server_destroy", "cosm_last_error",
+    "cosm_server_stats", "cosm_server_destroy", "cosm_last_error", "cosm_get_replica_energies",
+    "cosm_get_replica_bisectors", "cosm_get_trace", "cosm_qubo_to_ising",
 )
 
 
@@ -60,7 +63,7 @@ class CosmError(RuntimeError):
 class GraphDesc(C.Structure):
     _fields_ = [("n", C.c_int32), ("m", C.c_int64), ("src", C.c_void_p), ("dst", C.c_void_p),
                 ("w", C.c_void_p), ("n_colors", C.c_int32), ("color", C.c_void_p),
-                ("dims", C.c_int32 * 3)]
+                ("dims", C.c_int32 * 3), ("h", C.c_void_p)]
 
 
 class ServerConfig(C.Structure):
@@ -81,7 +84,7 @@ class RequestResult(C.Structure):
 class Params(C.Structure):
     _fields_ = [("alpha0_deg", C.c_double), ("dwt_ratio", C.c_double), ("dwt_period", C.c_int32),
                 ("window_deg", C.c_double), ("n_bisectors", C.c_int32), ("storage", C.c_int32),
-                ("flags", C.c_int32), ("reserved", C.c_int32)]
+                ("flags", C.c_int32), ("track_period", C.c_int32)]
 
 
 def _load():
@@ -129,6 +132,10 @@ def _load():
         "cosm_server_stats": (C.c_int, [P, P]),
         "cosm_server_destroy": (None, [P]),
         "cosm_last_error": (C.c_char_p, []),
+        "cosm_get_replica_energies": (C.c_int, [P, P]),
+        "cosm_get_replica_bisectors": (C.c_int, [P, P]),
+        "cosm_get_trace": (C.c_int, [P, P, i64]),
+        "cosm_qubo_to_ising": (C.c_int, [i32, i64, P, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -192,7 +199,7 @@ def default_params(**kw) -> Params:
     return p
 
 
-def _desc(n, src, dst, w, color=None, n_colors=0, dims=()):
+def _desc(n, src, dst, w, color=None, n_colors=0, dims=(), h=None):
     keep = [_i32(src), _i32(dst), _i32(w)]
     d = GraphDesc()
     d.n = int(n)
@@ -202,6 +209,9 @@ def _desc(n, src, dst, w, color=None, n_colors=0, dims=()):
         keep.append(_i32(color))
         d.color = keep[-1].ctypes.data
         d.n_colors = int(n_colors)
+    if h is not None:
+        keep.append(_i32(h))
+        d.h = keep[-1].ctypes.data
     dd = list(dims) + [0] * (3 - len(dims))
     d.dims = (C.c_int32 * 3)(*dd[:3])
     return d, keep
@@ -210,9 +220,9 @@ def _desc(n, src, dst, w, color=None, n_colors=0, dims=()):
 class Solver:
     """One instance on the current CUDA device (cosm_create ... cosm_destroy)."""
 
-    def __init__(self, n, src, dst, w, color=None, n_colors=0, dims=(), params=None, **kw):
+    def __init__(self, n, src, dst, w, color=None, n_colors=0, dims=(), params=None, h=None, **kw):
         self.params = params if params is not None else default_params(**kw)
-        desc, keep = _desc(n, src, dst, w, color, n_colors, dims)
+        desc, keep = _desc(n, src, dst, w, color, n_colors, dims, h)
         h = C.c_void_p()
         _check(_lib.cosm_create(C.byref(desc), C.byref(self.params), C.byref(h)))
         self._h = h
@@ -237,7 +247,26 @@ class Solver:
 
     def run(self, sweeps, replicas, seed, stream=None):
         self.replicas = int(replicas)
+        self.sweeps = int(sweeps)
         _check(_lib.cosm_run(self._h, int(sweeps), int(replicas), int(seed), _stream(stream)))
+
+    def replica_energies(self):
+        out = np.zeros(self.replicas, dtype=np.int64)
+        _check(_lib.cosm_get_replica_energies(self._h, _p(out)))
+        return out
+
+    def replica_bisectors(self):
+        out = np.zeros(self.replicas, dtype=np.uint32)
+        _check(_lib.cosm_get_replica_bisectors(self._h, _p(out)))
+        return out
+
+    def trace(self):
+        """[replica][readout] energies of the last tracked run."""
+        T = int(self.params.track_period)
+        k = -(-self.sweeps // T) if T > 0 else 0
+        out = np.zeros((self.replicas, max(k, 1)), dtype=np.int64)
+        _check(_lib.cosm_get_trace(self._h, _p(out), self.replicas * k))
+        return out[:, :k]
 
     def sync(self):
         _check(_lib.cosm_sync(self._h))
@@ -409,6 +438,23 @@ class Server:
         keys = ("queued", "active", "retired", "chunks", "launches", "max_concurrent",
                 "peak_footprint", "footprint")
         return dict(zip(keys, list(out)))
+
+
+def qubo_to_ising(n, qi, qj, qv):
+    """QUBO triplets -> (src, dst, w, h, offset) with 4 f(x) = H(s) + offset
+    (cosm_qubo_to_ising)."""
+    qi, qj = _i32(qi), _i32(qj)
+    qv = np.ascontiguousarray(qv, dtype=np.int64)
+    nnz = int(qi.shape[0])
+    src = np.zeros(max(nnz, 1), np.int32)
+    dst = np.zeros(max(nnz, 1), np.int32)
+    w = np.zeros(max(nnz, 1), np.int32)
+    h = np.zeros(int(n), np.int32)
+    m, off = C.c_int64(), C.c_int64()
+    _check(_lib.cosm_qubo_to_ising(int(n), nnz, _p(qi), _p(qj), _p(qv), _p(src), _p(dst), _p(w),
+                                   C.byref(m), _p(h), C.byref(off)))
+    k = int(m.value)
+    return src[:k].copy(), dst[:k].copy(), w[:k].copy(), h, int(off.value)
 
 
 def solve(n, src, dst, w, sweeps, replicas, seed, color=None, n_colors=0, dims=(), params=None,

@@ -296,3 +296,65 @@ bool lattice_relabel(const Graph &g, std::vector<int32_t> &slot_of, std::string 
 }
 
 }  // namespace cosm
+
+// QUBO -> Ising (eq. (1)) with x_i = (1 + s_i) / 2: for i < j the pair
+// coefficient c_ij = Q_ij + Q_ji gives x_i x_j = (1 + s_i + s_j + s_i s_j) / 4,
+// and a diagonal Q_ii gives x_i = (1 + s_i) / 2; collecting terms,
+//   4 f(x) = sum_{i<j} c_ij s_i s_j + sum_i s_i (sum_j c_ij + 2 Q_ii)
+//            + sum_{i<j} c_ij + 2 sum_i Q_ii,
+// i.e. Max-Cut weights w_ij = c_ij, fields h_i = -(sum_j c_ij + 2 Q_ii).
+extern "C" int cosm_qubo_to_ising(int32_t n, int64_t nnz, const int32_t *qi, const int32_t *qj,
+                                  const int64_t *qv, int32_t *src, int32_t *dst, int32_t *w, int64_t *m,
+                                  int32_t *h, int64_t *offset)
+{
+    using namespace cosm;
+    if (n < 1 || nnz < 0 || (nnz > 0 && (!qi || !qj || !qv)) || !src || !dst || !w || !m || !h ||
+        !offset) {
+        set_last_error("bad arguments");
+        return COSM_ERR_INVALID_ARG;
+    }
+    std::vector<std::pair<int64_t, int64_t>> pairs;  // (i n + j, c) with i < j
+    pairs.reserve((size_t)nnz);
+    std::vector<int64_t> diag((size_t)n, 0), hsum((size_t)n, 0);
+    for (int64_t k = 0; k < nnz; ++k) {
+        const int32_t i = qi[k], j = qj[k];
+        if (i < 0 || i >= n || j < 0 || j >= n) {
+            set_last_error("triplet " + std::to_string(k) + " has an index outside [0, n)");
+            return COSM_ERR_INVALID_ARG;
+        }
+        if (i == j) diag[(size_t)i] += qv[k];
+        else pairs.emplace_back((int64_t)std::min(i, j) * n + std::max(i, j), qv[k]);
+    }
+    std::sort(pairs.begin(), pairs.end());
+    int64_t cnt = 0, off = 0;
+    for (size_t a = 0; a < pairs.size();) {
+        const int64_t key = pairs[a].first;
+        int64_t c = 0;
+        while (a < pairs.size() && pairs[a].first == key) c += pairs[a++].second;
+        if (c == 0) continue;
+        if (c > 127 || c < -127) {
+            set_last_error("pair weight " + std::to_string(c) + " exceeds 127 in magnitude");
+            return COSM_ERR_TOO_LARGE;
+        }
+        const int32_t i = (int32_t)(key / n), j = (int32_t)(key % n);
+        src[cnt] = i;
+        dst[cnt] = j;
+        w[cnt] = (int32_t)c;
+        ++cnt;
+        hsum[(size_t)i] += c;
+        hsum[(size_t)j] += c;
+        off += c;
+    }
+    for (int32_t v = 0; v < n; ++v) {
+        const int64_t hv = -(hsum[(size_t)v] + 2 * diag[(size_t)v]);
+        if (hv > 32767 || hv < -32767) {
+            set_last_error("field of vertex " + std::to_string(v) + " exceeds 32767 in magnitude");
+            return COSM_ERR_TOO_LARGE;
+        }
+        h[v] = (int32_t)hv;
+        off += 2 * diag[(size_t)v];
+    }
+    *m = cnt;
+    *offset = off;
+    return COSM_OK;
+}

@@ -75,6 +75,8 @@ struct cosm_handle {
     int mode = cosm::MODE_GENERAL_;       // kernel variant
     int32_t Q = 0, Wd = 0;          // 2D lattice geometry
     DevBuf<uint8_t> d_wnib;         // 2D lattice block weight bits
+    bool fields = false;            // local fields given
+    DevBuf<int32_t> d_h;            // local field per slot
     // per run
     DevBuf<unsigned char> d_state;
     DevBuf<int64_t> d_cut;
@@ -86,6 +88,16 @@ struct cosm_handle {
     DevBuf<int32_t> d_err;
     DevBuf<int64_t> d_best;
     DevBuf<int8_t> d_spins;
+    DevBuf<int64_t> d_energy;       // per replica: energy of the kept readout
+    DevBuf<uint32_t> d_bisB;        // per replica: its bisector position
+    DevBuf<int64_t> d_trace;        // tracking: [replica][readout] energies
+    DevBuf<uint32_t> d_bits;        // tracking: [replica][words] kept spins
+    DevBuf<uint32_t> d_qbuf;        // optimal bisector scratch
+    DevBuf<int32_t> d_delta;
+    DevBuf<uint64_t> d_items;
+    int32_t n_trace = 0;            // readouts per trial of the last tracked run
+    bool have_trace = false;
+    bool bits_valid = false;        // d_bits holds the kept spins of the last run
     // cached host tables
     int64_t alpha_S = -1;
     double alpha_a0 = -1, alpha_ratio = -1;
@@ -112,5 +124,7 @@ int ensure_run_buffers(cosm_handle *h, int replicas);
 InstView inst_view(cosm_handle *h);
 int upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st);
 int launch_finalize(cosm_handle *h, cudaStream_t st);
+int launch_opt_readout(cosm_handle *h, bool keep_better, cudaStream_t st);
+int single_only(const cosm_graph_desc *g, const cosm_params *p);
 
 }  // namespace cosm

@@ -59,8 +59,19 @@ struct InstView {
     uint32_t qwin;        // DWT window width in 2^-32 turns (fixed point)
     void *state;          // [tiles][n_pad][K] phases in the storage type
     int64_t state_tile_stride;  // elements of the storage type per tile
-    int64_t *cut;         // [replicas] best cut
-    int32_t *bestp;       // [replicas] best bisector
+    int64_t *cut;         // [replicas] cut of the kept readout
+    int32_t *bestp;       // [replicas] its bisector index (-1: not an equally spaced one)
+    // local fields and readout bookkeeping (nullptr / 0 where unused)
+    const int32_t *hv;    // [n] local field per slot (eq. (1)), nullptr = none
+    int64_t W;            // total Max-Cut weight
+    int64_t *energy;      // [replicas] energy (eq. (1)) of the kept readout
+    uint32_t *bisB;       // [replicas] position of its bisector (2^-32 turn)
+    int32_t track;        // readout period in sweeps, 0 = last sweep only
+    int32_t n_trace;      // readouts per trial with tracking
+    int64_t *trace;       // [replicas][n_trace] readout energies
+    uint32_t *bits;       // [replicas][words] spins of the kept readout (slot order)
+    int32_t words;        // (n + 31) / 32
+    int32_t pad_;
 };
 
 // Single-instance launch: the instance plus the CTAs' segment lists.
@@ -136,10 +147,29 @@ struct FinalArgs {
     const int32_t *orig_of;
     const int64_t *cut;
     const int32_t *bestp;
+    const int64_t *energy;  // nullptr: select by cut
+    const uint32_t *bisB;   // nullptr: bisector from bestp
+    const uint32_t *bits;   // nullptr: spins from the phases
+    int32_t words;
     int64_t *best;        // [0] cut, [1] energy, [2] replica
     int8_t *spins;        // n, original vertex order
 };
 int finalize_launch(const FinalArgs &a, void *stream);
+
+// Optimal-bisector readout (Section II-B; Burer, Monteiro and Zhang 2002):
+// per replica, the best cut over every bisector position, from the stored
+// phases; one CTA per replica at a time, scratch in global memory.
+struct OptArgs {
+    InstView v;           // graph, state, outputs
+    uint32_t *qbuf;       // [grid][n] phase positions of the current replica
+    int32_t *delta;       // [grid][n] cut change at each vertex's position
+    uint64_t *items;      // [grid][npow2] (position << 32 | delta), sorted
+    int32_t npow2;        // power of two >= n
+    int32_t keep_better;  // 1: replace the kept readout only if strictly lower in energy
+    int32_t storage;      // 0 f32, 1 f16, 2 u16 fixed point
+    int32_t pad_;
+};
+int opt_readout_launch(const OptArgs &a, int grid, void *stream);
 
 // Records the message that cosm_last_error() returns on this thread.
 void set_last_error(const std::string &msg);

@@ -51,11 +51,13 @@ __device__ __forceinline__ float u24_centered(uint32_t word)
     return x >= 0.5f ? x - 1.0f : x;
 }
 
-// DWT reference angle for (seed, replica, sweep): counter (s, r, 0, 1).
-__device__ __forceinline__ float dwt_theta(uint64_t seed, uint32_t replica, int64_t sweep)
+// DWT reference angle for (seed, replica, sweep): counter (s, r, 0, 1),
+// word 0; the top bit of word 1 is the drawn twist direction (set: -1).
+__device__ __forceinline__ float dwt_theta(uint64_t seed, uint32_t replica, int64_t sweep, bool *neg = nullptr)
 {
     uint32_t c[4] = {(uint32_t)sweep, replica, 0u, 1u};
     philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+    if (neg) *neg = (c[1] >> 31) != 0;
     return (float)(c[0] >> 8) * 0x1p-24f;  // [0, 1), exact
 }
 
@@ -204,12 +206,13 @@ __host__ __device__ constexpr size_t phase_bytes(int n)
 }
 
 // Shared layout: phases | NO_SCS accumulators (FP32, n*K) | readout
-// difference arrays (int32, K*(P+1)) | DWT angles (K floats).
+// difference arrays (int32, K*(P+1)) | per-replica words: DWT offsets,
+// twist steps, readout flags and bisector positions (4K words).
 template <typename Store, int K>
 __host__ __device__ constexpr size_t smem_bytes(int n, int P, bool accum)
 {
     return phase_bytes<Store, K>(n) + (accum ? round16((size_t)n * K * 4) : 0) +
-           round16((size_t)K * (P + 1) * 4) + round16((size_t)K * 4);
+           round16((size_t)K * (P + 1) * 4) + round16((size_t)K * 16);
 }
 
 // ---------------------------------------------------------------- pair update
@@ -234,14 +237,14 @@ __device__ __forceinline__ void pair_update(float (&xi)[K], float (&xj)[K], floa
 // antipode; x is inside iff ((x - th + W/2) mod 1/2) < W. With y = 2x + c,
 // c = 2 (W/2 - th) precomputed per replica, the test is frac(y) < 2W.
 template <int K>
-__device__ __forceinline__ void dwt_apply(float (&x)[K], const float *thc, float W2, float step)
+__device__ __forceinline__ void dwt_apply(float (&x)[K], const float *thc, float W2, const float (&st)[K])
 {
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         const float y = fmaf(2.0f, x[r], thc[r]);
         const float u = __fadd_rn(y, -rint_fast(y));
         const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
-        if (in) x[r] = wrap_c(__fadd_rn(x[r], step));
+        if (in) x[r] = wrap_c(__fadd_rn(x[r], st[r]));
     }
 }
 
@@ -254,6 +257,9 @@ struct Tile {
     float *acc;    // [n][K] NO_SCS accumulators (mode 1 only)
     int *D;        // [K][P+1] readout difference arrays
     float *thc;    // [K] DWT offsets 2 (W/2 - theta)
+    float *stp;    // [K] twist step of each replica (sign drawn or +1)
+    int *imp;      // [K] readout: the replica's kept readout changed
+    uint32_t *Bs;  // [K] readout: bisector position of the replica
     size_t vec_bytes;
 };
 
@@ -269,6 +275,9 @@ __device__ __forceinline__ Tile<Store, K> carve(unsigned char *smem, int n, int 
     t.D = reinterpret_cast<int *>(smem + off);
     off += round16((size_t)K * (P + 1) * 4);
     t.thc = reinterpret_cast<float *>(smem + off);
+    t.stp = t.thc + K;
+    t.imp = reinterpret_cast<int *>(t.thc + 2 * K);
+    t.Bs = reinterpret_cast<uint32_t *>(t.thc + 3 * K);
     return t;
 }
 
@@ -314,6 +323,9 @@ __device__ bool seg_begin(const InstView &v, const Segment &sg, const Tile<Store
             else if constexpr (sizeof(Store) == 4) t.xs[k] = u24_centered(word);
             else t.xs[k] = __float2half_rn(u24_centered(word));
         }
+        // mid-anneal tracking keeps the lowest-energy readout of the trial
+        if (v.track > 0 && v.energy && tid < K && rep0 + tid < (uint32_t)v.replicas)
+            v.energy[rep0 + tid] = LLONG_MAX;
     } else if (sg.flags & SEG_LOAD) {
         const uint4 *src = reinterpret_cast<const uint4 *>(gst);
         uint4 *dst = reinterpret_cast<uint4 *>(t.xs);
@@ -327,70 +339,166 @@ __device__ bool seg_begin(const InstView &v, const Segment &sg, const Tile<Store
 // at bisector p is [p < f_v] xor h_v, with h_v the top bit of
 // q_v = floor(x_v 2^32) and f_v = #{p : floor(p 2^31 / P) <= q_v mod 2^31};
 // an edge is therefore cut on one interval of p or on its complement, which
-// a difference array over p accumulates exactly.
+// a difference array over p accumulates exactly. With local fields the
+// readout is the fixed half circle [-1/4, 1/4) turn around the reference
+// phase 0 (s_v = +1 iff ((q_v + 2^30) mod 2^32) < 2^31), and the energy of
+// eq. (1) adds the field term. Each replica's readout then replaces its
+// kept one (keep_better: only if strictly lower in energy), its energy goes
+// to trace[k] (k >= 0), and with tracking the spins of a replaced readout
+// are saved as bits.
 template <typename Store, int K>
-__device__ void seg_readout(const InstView &a, const Segment &sg, const Tile<Store, K> &t)
+__device__ __noinline__ void tile_readout(const InstView &a, int tile, const Tile<Store, K> &t, int k, bool keep_better)
 {
     const int tid = threadIdx.x, nt = blockDim.x, P = a.P;
-    const uint32_t rep0 = (uint32_t)sg.tile * K;
-    for (int k = tid; k < K * (P + 1); k += nt) t.D[k] = 0;
+    const uint32_t rep0 = (uint32_t)tile * K;
     __syncthreads();
-    int base[K];
-#pragma unroll
-    for (int r = 0; r < K; ++r) base[r] = 0;
+    for (int i = tid; i < K * (P + 1); i += nt) t.D[i] = 0;
+    __syncthreads();
     const int m = __ldg(a.off + a.C);
-    for (int e = tid; e < m; e += nt) {
-        const uint32_t rec = __ldg(a.ij + e);
-        const int wv = (int)__ldg(a.w + e);
-        const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
-        uint32_t qis[K], qjs[K];
-        ld_q32<Store, K>(t.xs + (size_t)i * K, qis);
-        ld_q32<Store, K>(t.xs + (size_t)j * K, qjs);
+    if (a.hv) {
+        int cs[K], fs[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) cs[r] = fs[r] = 0;
+        for (int e = tid; e < m; e += nt) {
+            const uint32_t rec = __ldg(a.ij + e);
+            const int wv = (int)__ldg(a.w + e);
+            uint32_t qis[K], qjs[K];
+            ld_q32<Store, K>(t.xs + (size_t)(rec & 0xFFFFu) * K, qis);
+            ld_q32<Store, K>(t.xs + (size_t)(rec >> 16) * K, qjs);
+#pragma unroll
+            for (int r = 0; r < K; ++r)
+                if (((qis[r] + 0x40000000u) ^ (qjs[r] + 0x40000000u)) >> 31) cs[r] += wv;
+        }
+        for (int u = tid; u < a.n; u += nt) {
+            const int hvu = __ldg(a.hv + u);
+            uint32_t q[K];
+            ld_q32<Store, K>(t.xs + (size_t)u * K, q);
+#pragma unroll
+            for (int r = 0; r < K; ++r) fs[r] += ((q[r] + 0x40000000u) >> 31) ? -hvu : hvu;
+        }
 #pragma unroll
         for (int r = 0; r < K; ++r) {
-            const uint32_t qi = qis[r], qj = qjs[r];
-            const int fi = (int)(((uint64_t)((qi & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
-            const int fj = (int)(((uint64_t)((qj & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
-            const int lo = min(fi, fj), hi = max(fi, fj);
-            int *Dr = t.D + r * (P + 1);
-            if ((qi >> 31) == (qj >> 31)) {
-                if (lo < hi) {  // cut for p in [lo, hi)
-                    atomicAdd(Dr + lo, wv);
-                    atomicAdd(Dr + hi, -wv);
-                }
-            } else {  // cut for p in [0, lo) and [hi, P)
-                base[r] += wv;
-                if (lo < P) atomicAdd(Dr + lo, -wv);
-                if (hi < P) atomicAdd(Dr + hi, wv);
+            int c = cs[r], f = fs[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+                f += __shfl_xor_sync(0xFFFFFFFFu, f, o);
+            }
+            if ((tid & 31) == 0) {
+                if (c) atomicAdd(t.D + r * (P + 1), c);
+                if (f) atomicAdd(t.D + r * (P + 1) + 1, f);
             }
         }
-    }
+    } else {
+        int base[K];
 #pragma unroll
-    for (int r = 0; r < K; ++r) {
-        int b = base[r];
+        for (int r = 0; r < K; ++r) base[r] = 0;
+        for (int e = tid; e < m; e += nt) {
+            const uint32_t rec = __ldg(a.ij + e);
+            const int wv = (int)__ldg(a.w + e);
+            const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+            uint32_t qis[K], qjs[K];
+            ld_q32<Store, K>(t.xs + (size_t)i * K, qis);
+            ld_q32<Store, K>(t.xs + (size_t)j * K, qjs);
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
-        if ((tid & 31) == 0 && b) atomicAdd(t.D + r * (P + 1), b);
+            for (int r = 0; r < K; ++r) {
+                const uint32_t qi = qis[r], qj = qjs[r];
+                const int fi = (int)(((uint64_t)((qi & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
+                const int fj = (int)(((uint64_t)((qj & 0x7FFFFFFFu) + 1u) * (uint64_t)P + 0x7FFFFFFFull) >> 31);
+                const int lo = min(fi, fj), hi = max(fi, fj);
+                int *Dr = t.D + r * (P + 1);
+                if ((qi >> 31) == (qj >> 31)) {
+                    if (lo < hi) {  // cut for p in [lo, hi)
+                        atomicAdd(Dr + lo, wv);
+                        atomicAdd(Dr + hi, -wv);
+                    }
+                } else {  // cut for p in [0, lo) and [hi, P)
+                    base[r] += wv;
+                    if (lo < P) atomicAdd(Dr + lo, -wv);
+                    if (hi < P) atomicAdd(Dr + hi, wv);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            int b = base[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xFFFFFFFFu, b, o);
+            if ((tid & 31) == 0 && b) atomicAdd(t.D + r * (P + 1), b);
+        }
     }
     __syncthreads();
-    if (tid < K && rep0 + tid < (uint32_t)a.replicas) {
+    if (tid < K) {
+        const uint32_t rep = rep0 + tid;
         const int *Dr = t.D + tid * (P + 1);
-        long long accv = 0, best = LLONG_MIN;
-        int bp = 0;
-        for (int p = 0; p < P; ++p) {
-            accv += Dr[p];
-            if (accv > best) { best = accv; bp = p; }
+        long long cut, F = 0;
+        int bp;
+        uint32_t B;
+        if (a.hv) {
+            cut = Dr[0];
+            F = Dr[1];
+            bp = -1;
+            B = 0xC0000000u;
+        } else {
+            long long accv = 0;
+            cut = LLONG_MIN;
+            bp = 0;
+            for (int p = 0; p < P; ++p) {
+                accv += Dr[p];
+                if (accv > cut) { cut = accv; bp = p; }
+            }
+            B = (uint32_t)(((uint64_t)bp << 31) / (uint64_t)P);
         }
-        a.cut[rep0 + tid] = best;
-        a.bestp[rep0 + tid] = bp;
+        int take = 0;
+        if (rep < (uint32_t)a.replicas) {
+            const long long E = a.W - 2 * cut - F;
+            if (k >= 0 && a.trace) a.trace[(size_t)rep * a.n_trace + k] = E;
+            // __ldcg: the value may come from a segment of this tile run on another SM
+            take = !keep_better || !a.energy || E < __ldcg(a.energy + rep);
+            if (take) {
+                a.cut[rep] = cut;
+                a.bestp[rep] = bp;
+                if (a.energy) a.energy[rep] = E;
+                if (a.bisB) a.bisB[rep] = B;
+            }
+        }
+        t.imp[tid] = take;
+        t.Bs[tid] = B;
     }
+    if (!a.bits) return;
+    __syncthreads();
+    int any = 0;
+#pragma unroll
+    for (int r = 0; r < K; ++r) any |= t.imp[r];
+    if (!any) return;
+    uint32_t Bl[K];
+#pragma unroll
+    for (int r = 0; r < K; ++r) Bl[r] = t.Bs[r];
+    for (int wi = tid; wi < a.words; wi += nt) {
+        uint32_t word[K];
+#pragma unroll
+        for (int r = 0; r < K; ++r) word[r] = 0u;
+        const int v0 = wi * 32, v1 = min(a.n, v0 + 32);
+        for (int u = v0; u < v1; ++u) {
+            uint32_t q[K];
+            ld_q32<Store, K>(t.xs + (size_t)u * K, q);
+#pragma unroll
+            for (int r = 0; r < K; ++r)
+                if ((uint32_t)(q[r] - Bl[r]) < 0x80000000u) word[r] |= 1u << (u - v0);
+        }
+#pragma unroll
+        for (int r = 0; r < K; ++r)
+            if (t.imp[r]) a.bits[(size_t)(rep0 + r) * a.words + wi] = word[r];
+    }
+    __syncthreads();  // the next sweep rewrites the phases read above
 }
 
 template <typename Store, int K>
 __device__ void seg_end(const InstView &a, const Segment &sg, const Tile<Store, K> &t, int32_t *ready)
 {
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (sg.flags & SEG_READOUT) seg_readout<Store, K>(a, sg, t);
+    // with tracking the readout after the last sweep ran inside the sweep loop
+    if ((sg.flags & SEG_READOUT) && a.track <= 0) tile_readout<Store, K>(a, sg.tile, t, -1, false);
     if (sg.flags & SEG_STORE) {
         Store *gst = reinterpret_cast<Store *>(a.state) + (size_t)sg.tile * a.state_tile_stride;
         const uint4 *src = reinterpret_cast<const uint4 *>(t.xs);
@@ -506,14 +614,14 @@ __device__ __forceinline__ void wrap_all(float (&x)[K])
 }
 
 template <int K>
-__device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, float W2, float step)
+__device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, float W2, const float (&st)[K])
 {
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         const float y = fmaf(2.0f, x[r], thc[r]);
         const float u = __fadd_rn(y, -rint_fast(y));
         const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
-        if (in) x[r] = __fadd_rn(x[r], step);
+        if (in) x[r] = __fadd_rn(x[r], st[r]);
     }
 }
 
@@ -563,8 +671,11 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
 template <typename Store, int K, bool kFixedColumn>
 __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
                                                int m0, int dm, bool dwt, const float *thc, float W2,
-                                               float step)
+                                               const float *stp)
 {
+    float st[K];  // the twist step of each replica
+#pragma unroll
+    for (int r = 0; r < K; ++r) st[r] = dwt ? stp[r] : 0.0f;
     int m = m0;  // column of block f within its row
     const bool cw0 = (m0 == Wd - 1);
     const int goff0 = cw0 ? 1 - Wd : 1;
@@ -600,15 +711,15 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
             // the DWT follows the last colour of the sweep; every vertex is in
             // exactly one shifted block
             if constexpr (sizeof(Store) == 4) {
-                dwt_nowrap<K>(xd, thc, W2, step);
-                dwt_nowrap<K>(xc, thc, W2, step);
-                dwt_nowrap<K>(xb, thc, W2, step);
-                dwt_nowrap<K>(xa, thc, W2, step);
+                dwt_nowrap<K>(xd, thc, W2, st);
+                dwt_nowrap<K>(xc, thc, W2, st);
+                dwt_nowrap<K>(xb, thc, W2, st);
+                dwt_nowrap<K>(xa, thc, W2, st);
             } else {
-                dwt_apply<K>(xd, thc, W2, step);
-                dwt_apply<K>(xc, thc, W2, step);
-                dwt_apply<K>(xb, thc, W2, step);
-                dwt_apply<K>(xa, thc, W2, step);
+                dwt_apply<K>(xd, thc, W2, st);
+                dwt_apply<K>(xc, thc, W2, st);
+                dwt_apply<K>(xb, thc, W2, st);
+                dwt_apply<K>(xa, thc, W2, st);
             }
         }
         wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
@@ -638,11 +749,11 @@ __device__ __forceinline__ void pair_q(uint32_t (&xi)[K], uint32_t (&xj)[K], uin
 // Dual window twist on the grid: inside iff ((q - q_theta + QW/2) mod 2^31)
 // < QW; c = QW/2 - q_theta per replica.
 template <int K>
-__device__ __forceinline__ void dwt_q(uint32_t (&x)[K], const uint32_t *c, uint32_t qw, uint32_t stepq)
+__device__ __forceinline__ void dwt_q(uint32_t (&x)[K], const uint32_t *c, uint32_t qw, const uint32_t (&sq)[K])
 {
 #pragma unroll
     for (int r = 0; r < K; ++r)
-        if (((x[r] + c[r]) & 0x7FFFFFFFu) < qw) x[r] += stepq;
+        if (((x[r] + c[r]) & 0x7FFFFFFFu) < qw) x[r] += sq[r];
 }
 
 template <int K>
@@ -717,8 +828,11 @@ __device__ __forceinline__ void pair_q_oriented(uint32_t (&x1)[K], uint32_t (&x2
 template <int K>
 __device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wnib, uint32_t ap, int Q, int Wd,
                                                  int m0, int dm, bool dwt, const uint32_t *c, uint32_t qw,
-                                                 uint32_t stepq)
+                                                 const uint32_t *sqs)
 {
+    uint32_t sq[K];  // the twist step of each replica
+#pragma unroll
+    for (int r = 0; r < K; ++r) sq[r] = dwt ? sqs[r] : 0u;
     int m = m0;
     for (int f = threadIdx.x; f < Q; f += blockDim.x) {
         const bool cw = (m == Wd - 1);
@@ -738,10 +852,10 @@ __device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wn
         pair_q_oriented<K>(xd, xb, signed_q(wb, 4u, ap), rw);
         pair_q_oriented<K>(xc, xa, signed_q(wb, 8u, ap), rw);
         if (dwt) {
-            dwt_q<K>(xd, c, qw, stepq);
-            dwt_q<K>(xc, c, qw, stepq);
-            dwt_q<K>(xb, c, qw, stepq);
-            dwt_q<K>(xa, c, qw, stepq);
+            dwt_q<K>(xd, c, qw, sq);
+            dwt_q<K>(xc, c, qw, sq);
+            dwt_q<K>(xb, c, qw, sq);
+            dwt_q<K>(xa, c, qw, sq);
         }
         stq<K>(xs + (size_t)(3 * Q + f) * K, xd);
         stq<K>(xs + (size_t)(2 * Q + g) * K, xc);
@@ -753,6 +867,50 @@ __device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wn
 // ---------------------------------------------------------------- segment body
 enum { MODE_GENERAL = 0, MODE_ACCUM = 1, MODE_LATTICE2D = 2 };
 
+// Local fields (eq. (1)) as couplings J = h to a reference phase frozen at
+// 0: eq. (6) on x_v alone with x_j = 0, i.e. the step alpha (-h) s with
+// s = +1 iff the minimum angular difference of x_v from 0 is >= 0. Each
+// vertex appears once, so the field updates form one more conflict-free
+// sub-sweep, after the colours.
+template <typename Store, int K>
+__device__ __forceinline__ void field_pass(const InstView &a, Store *xs, float alpha)
+{
+    for (int u = threadIdx.x; u < a.n; u += blockDim.x) {
+        const int hvu = __ldg(a.hv + u);
+        if (hvu == 0) continue;
+        const float aw = alpha * (float)(-hvu);
+        float x[K];
+        ldk<K>(xs + (size_t)u * K, x);
+#pragma unroll
+        for (int r = 0; r < K; ++r) {
+            const float st = (__fadd_rn(x[r], -rint_fast(x[r])) >= 0.0f) ? aw : -aw;
+            x[r] = wrap_c(__fadd_rn(x[r], st));
+        }
+        stk<K>(xs + (size_t)u * K, x);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void field_pass_q(const InstView &a, uint16_t *xs, uint32_t aq)
+{
+    for (int u = threadIdx.x; u < a.n; u += blockDim.x) {
+        const int hvu = __ldg(a.hv + u);
+        if (hvu == 0) continue;
+        const uint32_t ap = (aq * (uint32_t)(-hvu)) << 16;
+        uint32_t x[K];
+        ldq<K>(xs + (size_t)u * K, x);
+#pragma unroll
+        for (int r = 0; r < K; ++r) x[r] += ((int32_t)x[r] >= 0) ? ap : 0u - ap;
+        stq<K>(xs + (size_t)u * K, x);
+    }
+}
+
+// True after the sweeps at which a tracking readout is due.
+__device__ __forceinline__ bool readout_due(const InstView &v, int64_t s)
+{
+    return v.track > 0 && (s % v.track == 0 || s == v.S);
+}
+
 // Fixed-point (COSM_Q16) segment: as run_segment below, on the grid.
 template <int K, int kMode>
 __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment &sg, unsigned char *smem,
@@ -762,8 +920,10 @@ __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment
     const Tile<uint16_t, K> t = carve<uint16_t, K>(smem, v.n, v.P, kMode == MODE_ACCUM);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n = v.n;
-    const bool dwt_on = !(v.flags & 1) && v.dwt_period > 0;
+    const bool dwt_on = !(v.flags & COSM_NO_DWT) && v.dwt_period > 0;
+    const bool randdir = (v.flags & COSM_DWT_RANDOM_DIR) != 0;
     uint32_t *cq = reinterpret_cast<uint32_t *>(t.thc);
+    uint32_t *sqs = reinterpret_cast<uint32_t *>(t.stp);
     int m0 = 0, dm = 0;
     if (kMode == MODE_LATTICE2D) {
         m0 = tid % v.Wd;
@@ -777,18 +937,24 @@ __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment
         const uint32_t aq = (uint32_t)__float2int_rn(at.x), stepq = (uint32_t)__float2int_rn(at.y) << 16;
         const bool dwt = dwt_on && phase == 0;
         if (dwt && tid < K) {
-            const uint32_t qth = (uint32_t)__float2uint_rn(dwt_theta(v.seed, rep0 + tid, s) * 16777216.0f) << 8;
+            bool neg = false;
+            const uint32_t qth = (uint32_t)__float2uint_rn(dwt_theta(v.seed, rep0 + tid, s, &neg) * 16777216.0f) << 8;
             cq[tid] = (v.qwin >> 1) - qth;
+            sqs[tid] = (randdir && neg) ? 0u - stepq : stepq;
         }
         if (kMode == MODE_LATTICE2D) {
             block_pass_even_q<K>(t.xs, v.wnib, aq << 16, v.Q);
             __syncthreads();
-            block_pass_odd_q<K>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, stepq);
+            block_pass_odd_q<K>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
             __syncthreads();
         } else {
             if (kMode == MODE_GENERAL) {
                 for (int c = 0; c < v.C; ++c) {
                     general_colour_q<K>(v, t.xs, c, aq);
+                    __syncthreads();
+                }
+                if (v.hv) {
+                    field_pass_q<K>(v, t.xs, aq);
                     __syncthreads();
                 }
             } else {
@@ -817,23 +983,32 @@ __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment
                 for (int u = tid; u < n; u += nt) {
                     uint32_t x[K];
                     ldq<K>(t.xs + (size_t)u * K, x);
+                    const int hvu = v.hv ? __ldg(v.hv + u) : 0;
+                    const uint32_t ap = (aq * (uint32_t)(-hvu)) << 16;
 #pragma unroll
-                    for (int r = 0; r < K; ++r) x[r] += acc[(size_t)u * K + r];
+                    for (int r = 0; r < K; ++r) {
+                        const uint32_t fs = hvu ? (((int32_t)x[r] >= 0) ? ap : 0u - ap) : 0u;
+                        x[r] += acc[(size_t)u * K + r] + fs;
+                    }
                     stq<K>(t.xs + (size_t)u * K, x);
                 }
                 __syncthreads();
             }
             if (dwt) {
                 if (v.C == 0) __syncthreads();
+                uint32_t sq[K];
+#pragma unroll
+                for (int r = 0; r < K; ++r) sq[r] = sqs[r];
                 for (int u = tid; u < n; u += nt) {
                     uint32_t x[K];
                     ldq<K>(t.xs + (size_t)u * K, x);
-                    dwt_q<K>(x, cq, v.qwin, stepq);
+                    dwt_q<K>(x, cq, v.qwin, sq);
                     stq<K>(t.xs + (size_t)u * K, x);
                 }
                 __syncthreads();
             }
         }
+        if (readout_due(v, s)) tile_readout<uint16_t, K>(v, sg.tile, t, (int)((s - 1) / v.track), true);
         if (dwt_on && ++phase == v.dwt_period) phase = 0;
     }
     seg_end<uint16_t, K>(v, sg, t, ready);
@@ -849,7 +1024,8 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
     const Tile<Store, K> t = carve<Store, K>(smem, v.n, v.P, kMode == MODE_ACCUM);
     const int tid = threadIdx.x, nt = blockDim.x;
     const int n = v.n;
-    const bool dwt_on = !(v.flags & 1) && v.dwt_period > 0;
+    const bool dwt_on = !(v.flags & COSM_NO_DWT) && v.dwt_period > 0;
+    const bool randdir = (v.flags & COSM_DWT_RANDOM_DIR) != 0;
     const float W2 = 2.0f * v.window, hw = 0.5f * v.window;
     constexpr bool kLattice = (kMode == MODE_LATTICE2D);
     int m0 = 0, dm = 0;
@@ -863,23 +1039,30 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
     for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
         const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));
         const bool dwt = dwt_on && phase == 0;
-        if (dwt && tid < K)
-            t.thc[tid] = 2.0f * (hw - dwt_theta(v.seed, rep0 + tid, s));
+        if (dwt && tid < K) {
+            bool neg = false;
+            t.thc[tid] = 2.0f * (hw - dwt_theta(v.seed, rep0 + tid, s, &neg));
+            t.stp[tid] = (randdir && neg) ? -at.y : at.y;
+        }
         if (kLattice) {
             // colours 0, 1 in the 2x2 blocks; colours 2, 3 (+ DWT) in the
             // shifted blocks
             block_pass_even<Store, K>(t.xs, v.wnib, at.x, v.Q);
             __syncthreads();
             if (dm == 0)
-                block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, at.y);
+                block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
             else
-                block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, at.y);
+                block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
             __syncthreads();
         } else {
             if (kMode == MODE_GENERAL) {
                 // sequential conflict-free search: colours in order (eq. (11))
                 for (int c = 0; c < v.C; ++c) {
                     general_colour<Store, K>(v, t.xs, c, at.x);
+                    __syncthreads();
+                }
+                if (v.hv) {
+                    field_pass<Store, K>(v, t.xs, at.x);
                     __syncthreads();
                 }
             } else {
@@ -909,23 +1092,33 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 for (int u = tid; u < n; u += nt) {
                     float x[K];
                     ldk<K>(t.xs + (size_t)u * K, x);
+                    const int hvu = v.hv ? __ldg(v.hv + u) : 0;
+                    const float aw = at.x * (float)(-hvu);
 #pragma unroll
-                    for (int r = 0; r < K; ++r) x[r] = wrap_c(__fadd_rn(x[r], t.acc[(size_t)u * K + r]));
+                    for (int r = 0; r < K; ++r) {
+                        float dx = t.acc[(size_t)u * K + r];
+                        if (hvu) dx = __fadd_rn(dx, (__fadd_rn(x[r], -rint_fast(x[r])) >= 0.0f) ? aw : -aw);
+                        x[r] = wrap_c(__fadd_rn(x[r], dx));
+                    }
                     stk<K>(t.xs + (size_t)u * K, x);
                 }
                 __syncthreads();
             }
             if (dwt) {
                 if (v.C == 0) __syncthreads();
+                float st[K];
+#pragma unroll
+                for (int r = 0; r < K; ++r) st[r] = t.stp[r];
                 for (int u = tid; u < n; u += nt) {
                     float x[K];
                     ldk<K>(t.xs + (size_t)u * K, x);
-                    dwt_apply<K>(x, t.thc, W2, at.y);
+                    dwt_apply<K>(x, t.thc, W2, st);
                     stk<K>(t.xs + (size_t)u * K, x);
                 }
                 __syncthreads();
             }
         }
+        if (readout_due(v, s)) tile_readout<Store, K>(v, sg.tile, t, (int)((s - 1) / v.track), true);
         if (dwt_on && ++phase == v.dwt_period) phase = 0;
     }
     seg_end<Store, K>(v, sg, t, ready);
@@ -981,11 +1174,22 @@ __global__ void __launch_bounds__(512) batch_kernel(const BatchArgs b)
 }
 
 // ---------------------------------------------------------------- finalize
-// Best replica (max cut, ties -> lowest index), energy H = W - 2 cut, and
-// the spins of that replica at its best bisector, in original vertex order.
+// Best replica (lowest energy of its kept readout, or the largest cut when
+// no energies are kept; ties -> lowest index), its energy, and its spins in
+// original vertex order: the saved bits of the kept readout with tracking,
+// else the rounding of the final phases at the kept bisector.
+__device__ __forceinline__ uint32_t stored_q(const void *state, int storage, size_t idx)
+{
+    if (storage == 0) return phase_q(reinterpret_cast<const float *>(state)[idx]);
+    if (storage == 1) return phase_q(__half2float(reinterpret_cast<const __half *>(state)[idx]));
+    return (uint32_t)reinterpret_cast<const uint16_t *>(state)[idx] << 16;
+}
+
 __device__ void finalize_body(int replicas, int K, int storage, int P, int n, int64_t W,
                               const void *state, int64_t stride, const int32_t *orig_of,
-                              const int64_t *cut, const int32_t *bestp, int64_t *best, int8_t *spins)
+                              const int64_t *cut, const int32_t *bestp, const int64_t *energy,
+                              const uint32_t *bisB, const uint32_t *bits, int words, int64_t *best,
+                              int8_t *spins)
 {
     __shared__ long long s_cut[1024];
     __shared__ int s_rep[1024];
@@ -993,7 +1197,7 @@ __device__ void finalize_body(int replicas, int K, int storage, int P, int n, in
     long long bc = LLONG_MIN;
     int br = 0x7FFFFFFF;
     for (int r = tid; r < replicas; r += nt) {
-        const long long c = cut[r];
+        const long long c = energy ? -energy[r] : cut[r];
         if (c > bc || (c == bc && r < br)) { bc = c; br = r; }
     }
     s_cut[tid] = bc;
@@ -1011,20 +1215,21 @@ __device__ void finalize_body(int replicas, int K, int storage, int P, int n, in
         __syncthreads();
     }
     const int rb = s_rep[0];
-    const long long cb = s_cut[0];
+    const long long cb = cut[rb];
     if (tid == 0) {
         best[0] = cb;
-        best[1] = W - 2 * cb;
+        best[1] = energy ? energy[rb] : W - 2 * cb;
         best[2] = rb;
     }
+    if (bits) {
+        const uint32_t *bw = bits + (size_t)rb * words;
+        for (int v = tid; v < n; v += nt) spins[orig_of[v]] = ((bw[v >> 5] >> (v & 31)) & 1u) ? 1 : -1;
+        return;
+    }
     const int tile = rb / K, lane = rb % K;
-    const uint32_t B = (uint32_t)(((uint64_t)bestp[rb] << 31) / (uint64_t)P);
+    const uint32_t B = bisB ? bisB[rb] : (uint32_t)(((uint64_t)bestp[rb] << 31) / (uint64_t)P);
     for (int v = tid; v < n; v += nt) {
-        const size_t idx = (size_t)tile * stride + (size_t)v * K + lane;
-        uint32_t q;
-        if (storage == 0) q = phase_q(reinterpret_cast<const float *>(state)[idx]);
-        else if (storage == 1) q = phase_q(__half2float(reinterpret_cast<const __half *>(state)[idx]));
-        else q = (uint32_t)reinterpret_cast<const uint16_t *>(state)[idx] << 16;
+        const uint32_t q = stored_q(state, storage, (size_t)tile * stride + (size_t)v * K + lane);
         spins[orig_of[v]] = ((uint32_t)(q - B) < 0x80000000u) ? 1 : -1;
     }
 }
@@ -1032,7 +1237,7 @@ __device__ void finalize_body(int replicas, int K, int storage, int P, int n, in
 __global__ void __launch_bounds__(1024) finalize_kernel(const FinalArgs a)
 {
     finalize_body(a.replicas, a.K, a.storage, a.P, a.n, a.W, a.state, a.state_tile_stride, a.orig_of,
-                  a.cut, a.bestp, a.best, a.spins);
+                  a.cut, a.bestp, a.energy, a.bisB, a.bits, a.words, a.best, a.spins);
 }
 
 __global__ void __launch_bounds__(1024) batch_finalize_kernel(const InstView *insts, const BatchFinal *fin)
@@ -1040,7 +1245,147 @@ __global__ void __launch_bounds__(1024) batch_finalize_kernel(const InstView *in
     const InstView &v = insts[blockIdx.x];
     const BatchFinal &f = fin[blockIdx.x];
     finalize_body(v.replicas, v.K, f.storage, v.P, v.n, f.W, v.state, v.state_tile_stride, v.orig_of,
-                  v.cut, v.bestp, f.best, f.spins);
+                  v.cut, v.bestp, v.energy, v.bisB, nullptr, 0, f.best, f.spins);
+}
+
+// ---------------------------------------------------------------- optimal bisector
+// Exact best bisector of each replica (Section II-B; the sorted sweep of
+// Burer, Monteiro and Zhang 2002). With phi_v = q_v mod 2^31 and t_v the top
+// bit of q_v, s_v(B) = +1 iff [B <= phi_v] xor t_v for B in [0, 2^31), so an
+// edge's cut state flips on the interval (lo, hi] of its endpoints'
+// positions: d_e = w_e (1 - 2 (t_i xor t_j)) enters at lo + 1 and leaves at
+// hi + 1. Each vertex collects the changes that happen at its position,
+// the (position, change) pairs are sorted (bitonic network over a power of
+// two, in global scratch), and a block-wide prefix sum gives the cut at
+// every position where it can change; the best (ties: the smallest B)
+// competes with the replica's kept readout.
+__global__ void __launch_bounds__(1024) opt_readout_kernel(const OptArgs o)
+{
+    __shared__ long long s_part[1024];
+    __shared__ long long s_best[1024];
+    __shared__ uint32_t s_B[1024];
+    __shared__ unsigned long long s_c0;
+    __shared__ int s_take;
+    const InstView &v = o.v;
+    const int tid = threadIdx.x, nt = blockDim.x, n = v.n, N = o.npow2;
+    uint32_t *qb = o.qbuf + (size_t)blockIdx.x * n;
+    int32_t *dl = o.delta + (size_t)blockIdx.x * n;
+    uint64_t *it = o.items + (size_t)blockIdx.x * N;
+    const int m = __ldg(v.off + v.C);
+    const int storage = o.storage;
+    for (int r = blockIdx.x; r < v.replicas; r += gridDim.x) {
+        const int tile = r / v.K, lane = r % v.K;
+        if (tid == 0) s_c0 = 0ull;
+        for (int u = tid; u < n; u += nt) {
+            qb[u] = stored_q(v.state, storage, (size_t)tile * v.state_tile_stride + (size_t)u * v.K + lane);
+            dl[u] = 0;
+        }
+        __syncthreads();
+        long long c0 = 0;
+        for (int e = tid; e < m; e += nt) {
+            const uint32_t rec = __ldg(v.ij + e);
+            const int wv = (int)__ldg(v.w + e);
+            const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
+            const uint32_t qi = qb[i], qj = qb[j];
+            const bool cross = ((qi ^ qj) >> 31) != 0;
+            if (cross) c0 += wv;
+            const uint32_t pi = qi & 0x7FFFFFFFu, pj = qj & 0x7FFFFFFFu;
+            if (pi == pj) continue;
+            const int d = cross ? -wv : wv;
+            atomicAdd(dl + (pi < pj ? i : j), d);
+            atomicAdd(dl + (pi < pj ? j : i), -d);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) c0 += __shfl_xor_sync(0xFFFFFFFFu, c0, off);
+        if ((tid & 31) == 0) atomicAdd(&s_c0, (unsigned long long)c0);
+        __syncthreads();
+        for (int u = tid; u < N; u += nt)
+            it[u] = u < n ? ((uint64_t)(qb[u] & 0x7FFFFFFFu) << 32) | (uint32_t)dl[u] : 0xFFFFFFFF00000000ull;
+        __syncthreads();
+        for (int k = 2; k <= N; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = tid; i < N; i += nt) {
+                    const int l = i ^ j;
+                    if (l > i) {
+                        const uint64_t x = it[i], y = it[l];
+                        if ((x > y) == ((i & k) == 0)) {
+                            it[i] = y;
+                            it[l] = x;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        // block prefix sum over contiguous chunks of the sorted pairs
+        const int chunk = (n + nt - 1) / nt;
+        const int a0 = min(n, tid * chunk), a1 = min(n, a0 + chunk);
+        long long sum = 0;
+        for (int i = a0; i < a1; ++i) sum += (int32_t)(uint32_t)it[i];
+        s_part[tid] = sum;
+        __syncthreads();
+        if (tid == 0) {
+            long long acc = 0;
+            for (int i = 0; i < nt; ++i) {
+                const long long t0 = s_part[i];
+                s_part[i] = acc;
+                acc += t0;
+            }
+        }
+        __syncthreads();
+        const long long C0 = (long long)s_c0;
+        long long run = C0 + s_part[tid], best = LLONG_MIN;
+        uint32_t bB = 0xFFFFFFFFu;
+        if (tid == 0) { best = C0; bB = 0; }
+        for (int i = a0; i < a1; ++i) {
+            const uint64_t x = it[i];
+            run += (int32_t)(uint32_t)x;
+            const uint32_t pos = (uint32_t)(x >> 32);
+            const bool end = (i == n - 1) || ((uint32_t)(it[i + 1] >> 32) != pos);
+            if (end && pos + 1u < 0x80000000u && run > best) {
+                best = run;
+                bB = pos + 1u;
+            }
+        }
+        s_best[tid] = best;
+        s_B[tid] = bB;
+        __syncthreads();
+        for (int off = nt / 2; off > 0; off >>= 1) {
+            if (tid < off) {
+                const long long c = s_best[tid + off];
+                const uint32_t b2 = s_B[tid + off];
+                if (c > s_best[tid] || (c == s_best[tid] && b2 < s_B[tid])) {
+                    s_best[tid] = c;
+                    s_B[tid] = b2;
+                }
+            }
+            __syncthreads();
+        }
+        const long long cut = s_best[0];
+        const uint32_t B = s_B[0];
+        if (tid == 0) {
+            const long long E = v.W - 2 * cut;
+            const int take = !o.keep_better || !v.energy || E < v.energy[r];
+            if (take) {
+                v.cut[r] = cut;
+                v.bestp[r] = -1;
+                if (v.energy) v.energy[r] = E;
+                if (v.bisB) v.bisB[r] = B;
+            }
+            s_take = take;
+        }
+        __syncthreads();
+        if (s_take && v.bits) {
+            for (int wi = tid; wi < v.words; wi += nt) {
+                uint32_t word = 0u;
+                const int v0 = wi * 32, v1 = min(n, v0 + 32);
+                for (int u = v0; u < v1; ++u)
+                    if ((uint32_t)(qb[u] - B) < 0x80000000u) word |= 1u << (u - v0);
+                v.bits[(size_t)r * v.words + wi] = word;
+            }
+        }
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -1130,6 +1475,12 @@ int sweep_launch(const LaunchCfg &cfg, const KernelArgs &a, void *stream)
 int finalize_launch(const FinalArgs &a, void *stream)
 {
     finalize_kernel<<<1, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int opt_readout_launch(const OptArgs &a, int grid, void *stream)
+{
+    opt_readout_kernel<<<grid, 1024, 0, reinterpret_cast<cudaStream_t>(stream)>>>(a);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

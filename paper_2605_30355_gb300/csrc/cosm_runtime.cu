@@ -56,7 +56,21 @@ static int check_params(const cosm_params *p)
         return fail(COSM_ERR_INVALID_ARG, "n_bisectors must be in [1, 256]");
     if (p->storage != COSM_F32 && p->storage != COSM_F16 && p->storage != COSM_Q16)
         return fail(COSM_ERR_INVALID_ARG, "storage must be COSM_F32, COSM_F16 or COSM_Q16");
-    if (p->flags & ~(COSM_NO_DWT | COSM_NO_SCS)) return fail(COSM_ERR_INVALID_ARG, "unknown flags");
+    if (p->flags & ~(COSM_NO_DWT | COSM_NO_SCS | COSM_DWT_RANDOM_DIR | COSM_OPT_BISECTOR))
+        return fail(COSM_ERR_INVALID_ARG, "unknown flags");
+    if (p->track_period < 0) return fail(COSM_ERR_INVALID_ARG, "track_period must be >= 0");
+    return COSM_OK;
+}
+
+// Features of single-instance runs only (local fields, tracking, optimal
+// bisector): the batch and serving paths reject them up front.
+int cosm::single_only(const cosm_graph_desc *g, const cosm_params *p)
+{
+    if (g && g->h) return fail(COSM_ERR_INVALID_ARG, "local fields are supported by single instances only");
+    if (p && p->track_period > 0)
+        return fail(COSM_ERR_INVALID_ARG, "mid-anneal tracking is supported by single instances only");
+    if (p && (p->flags & COSM_OPT_BISECTOR))
+        return fail(COSM_ERR_INVALID_ARG, "the optimal bisector is supported by single instances only");
     return COSM_OK;
 }
 
@@ -123,6 +137,8 @@ extern "C" void cosm_destroy(cosm_handle *h)
     h->d_segoff.release(); h->d_ready.release(); h->d_err.release(); h->d_best.release();
     h->d_spins.release();
     h->d_wnib.release();
+    h->d_h.release(); h->d_energy.release(); h->d_bisB.release(); h->d_trace.release();
+    h->d_bits.release(); h->d_qbuf.release(); h->d_delta.release(); h->d_items.release();
     delete h;
 }
 
@@ -136,7 +152,7 @@ static int setup_lattice2d(cosm_handle *h)
 {
     const Graph &g = h->g;
     h->mode = (h->prm.flags & COSM_NO_SCS) ? MODE_ACCUM_ : MODE_GENERAL_;
-    if (std::getenv("COSM_NO_LATTICE")) return COSM_OK;
+    if (std::getenv("COSM_NO_LATTICE") || h->fields) return COSM_OK;
     // the full torus only (every block needs its four edges)
     if (!h->lattice || g.dims[2] != 0 || h->mode != MODE_GENERAL_ || h->C != 4 || g.m != 2 * (int64_t)g.n)
         return COSM_OK;
@@ -201,6 +217,26 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
     std::string why;
     rc = validate_graph(g, why);
     if (rc) { delete h; return fail(rc, why); }
+    if (gd->h) {
+        if (p->flags & COSM_OPT_BISECTOR) {
+            delete h;
+            return fail(COSM_ERR_INVALID_ARG, "local fields fix the readout; COSM_OPT_BISECTOR does not apply");
+        }
+        int64_t mag = 0;
+        for (int64_t e = 0; e < g.m; ++e) mag += std::abs(g.w[(size_t)e]);
+        for (int32_t v = 0; v < g.n; ++v) {
+            if (gd->h[v] > 32767 || gd->h[v] < -32767) {
+                delete h;
+                return fail(COSM_ERR_INVALID_ARG, "local field " + std::to_string(v) + " exceeds 32767 in magnitude");
+            }
+            mag += std::abs(gd->h[v]);
+        }
+        if (mag >= ((int64_t)1 << 31)) {
+            delete h;
+            return fail(COSM_ERR_INVALID_ARG, "sum of |w| and |h| must be below 2^31");
+        }
+        h->fields = true;
+    }
     // partition: given, or coloured here (lattice pattern, else greedy)
     g.color.assign((size_t)g.m, 0);
     if (gd->color) {
@@ -266,6 +302,18 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
         cudaMemset(h->d_err.p, 0, 4) != cudaSuccess) {
         cosm_destroy(h);
         return fail(COSM_ERR_CUDA, "copying the graph to the device failed");
+    }
+    if (h->fields) {
+        std::vector<int32_t> hs((size_t)g.n);
+        for (int32_t v = 0; v < g.n; ++v) hs[(size_t)h->slot_of[(size_t)v]] = gd->h[v];
+        if ((rc = h->d_h.ensure((size_t)g.n))) {
+            cosm_destroy(h);
+            return rc;
+        }
+        if (cudaMemcpy(h->d_h.p, hs.data(), hs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cosm_destroy(h);
+            return fail(COSM_ERR_CUDA, "copying the local fields to the device failed");
+        }
     }
     if ((rc = setup_lattice2d(h))) {
         cosm_destroy(h);
@@ -346,7 +394,11 @@ int cosm::ensure_run_buffers(cosm_handle *h, int replicas)
     int rc;
     if ((rc = h->d_state.ensure((size_t)tiles * (size_t)h->tile_stride * esz)) ||
         (rc = h->d_cut.ensure((size_t)replicas)) || (rc = h->d_bestp.ensure((size_t)replicas)) ||
+        (rc = h->d_energy.ensure((size_t)replicas)) || (rc = h->d_bisB.ensure((size_t)replicas)) ||
         (rc = h->d_ready.ensure((size_t)tiles)))
+        return rc;
+    if (h->prm.track_period > 0 &&
+        (rc = h->d_bits.ensure((size_t)replicas * (size_t)((h->g.n + 31) / 32))))
         return rc;
     return COSM_OK;
 }
@@ -377,6 +429,11 @@ InstView cosm::inst_view(cosm_handle *h)
     v.state_tile_stride = h->tile_stride;
     v.cut = h->d_cut.p;
     v.bestp = h->d_bestp.p;
+    v.hv = h->fields ? h->d_h.p : nullptr;
+    v.W = h->W;
+    v.energy = h->d_energy.p;
+    v.bisB = h->d_bisB.p;
+    v.words = (h->g.n + 31) / 32;
     return v;
 }
 
@@ -485,6 +542,33 @@ int cosm::upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st)
     return COSM_OK;
 }
 
+// Optimal-bisector readout of every replica from the stored state, one CTA
+// of 1024 threads per replica at a time, one CTA per SM.
+int cosm::launch_opt_readout(cosm_handle *h, bool keep_better, cudaStream_t st)
+{
+    const int n = h->g.n;
+    int npow2 = 1;
+    while (npow2 < n) npow2 <<= 1;
+    const int grid = std::max(1, std::min(h->replicas, h->num_sms));
+    int rc;
+    if ((rc = h->d_qbuf.ensure((size_t)grid * n)) || (rc = h->d_delta.ensure((size_t)grid * n)) ||
+        (rc = h->d_items.ensure((size_t)grid * npow2)))
+        return rc;
+    OptArgs o;
+    std::memset(&o, 0, sizeof(o));
+    o.v = inst_view(h);
+    if (keep_better && h->prm.track_period > 0) o.v.bits = h->d_bits.p;
+    o.qbuf = h->d_qbuf.p;
+    o.delta = h->d_delta.p;
+    o.items = h->d_items.p;
+    o.npow2 = npow2;
+    o.keep_better = keep_better ? 1 : 0;
+    o.storage = h->prm.storage;
+    if (opt_readout_launch(o, grid, st))
+        return fail(COSM_ERR_CUDA, std::string("optimal-bisector launch: ") + cudaGetErrorString(cudaGetLastError()));
+    return COSM_OK;
+}
+
 int cosm::launch_finalize(cosm_handle *h, cudaStream_t st)
 {
     FinalArgs f;
@@ -499,6 +583,10 @@ int cosm::launch_finalize(cosm_handle *h, cudaStream_t st)
     f.orig_of = h->d_orig.p;
     f.cut = h->d_cut.p;
     f.bestp = h->d_bestp.p;
+    f.energy = h->d_energy.p;
+    f.bisB = h->d_bisB.p;
+    f.bits = h->bits_valid ? h->d_bits.p : nullptr;
+    f.words = (h->g.n + 31) / 32;
     f.best = h->d_best.p;
     f.spins = h->d_spins.p;
     if (finalize_launch(f, st)) return fail(COSM_ERR_CUDA, std::string("finalize launch: ") +
@@ -529,21 +617,37 @@ extern "C" int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64
     const bool waits = tiles > cap;
     if (waits) CK(cudaMemsetAsync(h->d_ready.p, 0, (size_t)tiles * 4, st));
     CK(cudaMemsetAsync(h->d_err.p, 0, 4, st));
+    const int track = h->prm.track_period;
+    const int32_t n_trace = track > 0 ? (int32_t)((sweeps + track - 1) / track) : 0;
+    if (track > 0 && (rc = h->d_trace.ensure((size_t)replicas * (size_t)n_trace))) return rc;
     KernelArgs a = base_args(h);
     a.v.alpha_tab = h->d_alpha.p;
     a.v.alpha_base = 1;
     a.v.S = sweeps;
+    if (track > 0) {
+        a.v.track = track;
+        a.v.n_trace = n_trace;
+        a.v.trace = h->d_trace.p;
+        a.v.bits = h->d_bits.p;
+    }
     a.segs = h->d_segs.p;
     a.seg_off = h->d_segoff.p;
     LaunchCfg cfg{h->mode, h->prm.storage, h->K, h->threads, (int)(h->h_segoff.size() - 1), h->smem, waits};
     h->grid = cfg.grid;
     if (sweep_launch(cfg, a, st))
         return fail(COSM_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(cudaGetLastError()));
+    h->launches = 2;
+    if (h->prm.flags & COSM_OPT_BISECTOR) {
+        if ((rc = launch_opt_readout(h, track > 0, st))) return rc;
+        h->launches = 3;
+    }
+    h->bits_valid = track > 0;
+    h->n_trace = n_trace;
+    h->have_trace = track > 0;
     if ((rc = launch_finalize(h, st))) return rc;
     h->stream = st;
     h->have_state = true;
     h->have_result = true;
-    h->launches = 2;
     return COSM_OK;
 }
 
@@ -569,6 +673,39 @@ extern "C" int cosm_get_best(cosm_handle *h, int64_t *cut, int64_t *energy, int3
     if (energy) *energy = best[1];
     if (replica) *replica = (int32_t)best[2];
     if (spins) CK(cudaMemcpy(spins, h->d_spins.p, (size_t)h->g.n, cudaMemcpyDefault));
+    return COSM_OK;
+}
+
+extern "C" int cosm_get_replica_energies(cosm_handle *h, int64_t *energies)
+{
+    if (!h || !energies) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    if (!h->have_result) return fail(COSM_ERR_STATE, "no run or readout yet");
+    int rc = cosm_sync(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(energies, h->d_energy.p, (size_t)h->replicas * 8, cudaMemcpyDefault));
+    return COSM_OK;
+}
+
+extern "C" int cosm_get_replica_bisectors(cosm_handle *h, uint32_t *B)
+{
+    if (!h || !B) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    if (!h->have_result) return fail(COSM_ERR_STATE, "no run or readout yet");
+    int rc = cosm_sync(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(B, h->d_bisB.p, (size_t)h->replicas * 4, cudaMemcpyDefault));
+    return COSM_OK;
+}
+
+extern "C" int cosm_get_trace(cosm_handle *h, int64_t *trace, int64_t count)
+{
+    if (!h || !trace) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    if (!h->have_trace) return fail(COSM_ERR_STATE, "the last run had no tracking");
+    if (count != (int64_t)h->replicas * h->n_trace)
+        return fail(COSM_ERR_INVALID_ARG, "count must be replicas x ceil(sweeps / track_period) = " +
+                                              std::to_string((int64_t)h->replicas * h->n_trace));
+    int rc = cosm_sync(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(trace, h->d_trace.p, (size_t)count * 8, cudaMemcpyDefault));
     return COSM_OK;
 }
 
@@ -665,6 +802,8 @@ extern "C" int cosm_set_state(cosm_handle *h, const double *phases, int32_t repl
     CK(cudaMemcpy(h->d_state.p, raw.data(), raw.size(), cudaMemcpyHostToDevice));
     h->have_state = true;
     h->have_result = false;
+    h->have_trace = false;
+    h->bits_valid = false;
     return COSM_OK;
 }
 
@@ -721,6 +860,8 @@ extern "C" int cosm_step(cosm_handle *h, int64_t sweep, float alpha, void *strea
     if (!rc) rc = cudaStreamSynchronize(st) == cudaSuccess ? COSM_OK : fail(COSM_ERR_CUDA, "step failed");
     tab.release();
     h->have_result = false;
+    h->have_trace = false;
+    h->bits_valid = false;
     h->launches = 1;
     return rc;
 }
@@ -732,9 +873,15 @@ extern "C" int cosm_readout(cosm_handle *h, void *stream)
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int rc = launch_on_state(h, SEG_LOAD | SEG_READOUT, 1, 0, h->d_alpha.p, 1, st);
     if (rc) return rc;
+    h->launches = 2;
+    if (h->prm.flags & COSM_OPT_BISECTOR) {
+        if ((rc = launch_opt_readout(h, false, st))) return rc;
+        h->launches = 3;
+    }
+    h->bits_valid = false;
+    h->have_trace = false;
     if ((rc = launch_finalize(h, st))) return rc;
     h->have_result = true;
-    h->launches = 2;
     return COSM_OK;
 }
 
@@ -834,7 +981,8 @@ extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, c
     if (!b) return fail(COSM_ERR_NOMEM, "host allocation failed");
     for (int32_t i = 0; i < count; ++i) {
         cosm_handle *h = nullptr;
-        int rc = cosm_create(&graphs[i], shared_params ? &params[0] : &params[i], &h);
+        int rc = single_only(&graphs[i], shared_params ? &params[0] : &params[i]);
+        if (!rc) rc = cosm_create(&graphs[i], shared_params ? &params[0] : &params[i], &h);
         if (rc) {
             std::string msg = "instance " + std::to_string(i) + ": " + g_err;
             cosm_batch_destroy(b);

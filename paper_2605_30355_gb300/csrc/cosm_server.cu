@@ -96,7 +96,8 @@ static size_t estimate_footprint(const Request &r)
     const size_t esz = r.prm.storage == COSM_F32 ? 4 : 2;
     const size_t m = r.src.size();
     const size_t state = (size_t)r.R * ((size_t)r.n * esz + 16 * 4);
-    return 5 * m + 4 * (size_t)r.n + 4 * 65 + state + 12 * (size_t)r.R + 8 * (size_t)r.S + (size_t)r.n +
+    // per replica: cut, bisector index, energy, bisector position (24 bytes)
+    return 5 * m + 4 * (size_t)r.n + 4 * 65 + state + 24 * (size_t)r.R + 8 * (size_t)r.S + (size_t)r.n +
            (size_t)r.n / 2 + 4096;
 }
 
@@ -363,6 +364,7 @@ extern "C" int cosm_server_submit(cosm_server *s, const cosm_graph_desc *g, cons
         return fail(COSM_ERR_INVALID_ARG, "bad graph");
     if (sweeps < 1 || sweeps >= ((int64_t)1 << 31) || replicas < 1 || replicas >= (1 << 24) || max_trials < 1)
         return fail(COSM_ERR_INVALID_ARG, "bad sweeps, replicas or max_trials");
+    if (int rc = single_only(g, p)) return rc;
     Request *r = new (std::nothrow) Request();
     if (!r) return fail(COSM_ERR_NOMEM, "host allocation failed");
     r->n = g->n;

@@ -72,8 +72,9 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
     if (!(p->alpha0_deg >= 0.0 && p->alpha0_deg < 180.0) || !(p->dwt_ratio >= 0.0 && p->dwt_ratio <= 16.0) ||
         p->dwt_period < 0 || !(p->window_deg > 0.0 && p->window_deg <= 180.0) || p->n_bisectors < 1 ||
         p->n_bisectors > kMaxBisectors || (p->storage != COSM_F32 && p->storage != COSM_F16) ||
-        (p->flags & ~(COSM_NO_DWT | COSM_NO_SCS)))
+        (p->flags & ~(COSM_NO_DWT | COSM_NO_SCS)) || p->track_period != 0)
         return fail(COSM_ERR_INVALID_ARG, "invalid parameters");
+    if (gd->h) return fail(COSM_ERR_INVALID_ARG, "local fields are not supported without allocation");
     if (gd->n < 2 || gd->n > kMaxVertices || gd->m < 1 || gd->m > ((int64_t)1 << 26))
         return fail(COSM_ERR_INVALID_ARG, "n must be in [2, 65536] and m in [1, 2^26]");
 

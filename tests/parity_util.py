@@ -32,8 +32,9 @@ def one_sweep_error(orc, g, x0, x_gpu, alpha, sweep, *, storage=0, max_enum=10, 
         return err, 0
     ties = ties[:max_enum]
     best = err
+    nforce = g.m + g.n * (2 if kw.get("h") is not None else 1)
     for signs in itertools.product((1, -1), repeat=len(ties)):
-        force = np.zeros(g.m + g.n, dtype=np.int8)
+        force = np.zeros(nforce, dtype=np.int8)
         force[ties] = signs
         xf, _ = orc.sweep(g, x0, alpha, sweep, storage=storage, force=force, **kw)
         best = min(best, float(circ_rad(xf, x_gpu).max()))

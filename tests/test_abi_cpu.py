@@ -89,3 +89,66 @@ def test_partition_validator_agrees_with_oracle(cosm, orc):
     bad2 = col.copy()
     bad2[3] = C
     assert cosm.validate_partition(inst.n, inst.src, inst.dst, C, bad2) == cosm.ERR_PARTITION
+
+
+def test_qubo_to_ising_matches_bruteforce(cosm, orc):
+    # 4 f(x) = H(s) + offset for every x in {0,1}^n, x = (1 + s) / 2
+    import itertools
+    rng = np.random.default_rng(7)
+    for trial in range(5):
+        n = 7
+        nnz = 25
+        qi = rng.integers(0, n, nnz)
+        qj = rng.integers(0, n, nnz)
+        qv = rng.integers(-4, 5, nnz)
+        src, dst, w, h, off = cosm.qubo_to_ising(n, qi, qj, qv)
+        assert (src < dst).all() and (w != 0).all()
+        Q = np.zeros((n, n), dtype=np.int64)
+        np.add.at(Q, (qi, qj), qv)
+        for bits in itertools.product([0, 1], repeat=n):
+            x = np.array(bits)
+            s = (2 * x - 1).astype(np.int8)
+            f = int(x @ Q @ x)
+            assert 4 * f == orc.energy_h(n, src, dst, w, h, s) + off
+
+
+def test_qubo_to_ising_rejects_bad_input(cosm):
+    with pytest.raises(cosm.CosmError) as e:
+        cosm.qubo_to_ising(3, [0], [3], [1])
+    assert e.value.code == cosm.ERR_INVALID_ARG
+    with pytest.raises(cosm.CosmError) as e:
+        cosm.qubo_to_ising(3, [0, 1], [1, 0], [100, 100])
+    assert e.value.code == cosm.ERR_TOO_LARGE
+
+
+def test_single_instance_features_rejected_by_batch_and_static(cosm):
+    # checked on the host before any device work
+    inst = instances.torus2d(8, 8, 1)
+    h = np.ones(inst.n, dtype=np.int32)
+    with pytest.raises(cosm.CosmError) as e:
+        cosm.Batch([inst], track_period=10)
+    assert e.value.code == cosm.ERR_INVALID_ARG
+    with pytest.raises(cosm.CosmError) as e:
+        cosm.Batch([inst], flags=cosm.OPT_BISECTOR)
+    assert e.value.code == cosm.ERR_INVALID_ARG
+    import ctypes as C
+    desc, keep = cosm._desc(inst.n, inst.src, inst.dst, inst.w, h=h)
+    b = C.c_void_p()
+    p = cosm.default_params()
+    rc = cosm.lib().cosm_batch_create(1, C.byref(desc), C.byref(p), 1, C.byref(b))
+    assert rc == cosm.ERR_INVALID_ARG
+    cuts = np.zeros(4, np.int64)
+    bps = np.zeros(4, np.int32)
+    rc = cosm.lib().cosm_solve_static(C.byref(desc), C.byref(p), 10, 4, 1, cosm._p(cuts), cosm._p(bps), None)
+    assert rc == cosm.ERR_INVALID_ARG
+
+
+def test_field_and_tracking_parameters_validated(cosm):
+    inst = instances.torus2d(8, 8, 1)
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver.from_instance(inst, track_period=-1)
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(inst.n, inst.src, inst.dst, inst.w, h=np.full(inst.n, 40000, np.int32))
+    with pytest.raises(cosm.CosmError):
+        cosm.Solver(inst.n, inst.src, inst.dst, inst.w, h=np.ones(inst.n, np.int32),
+                    flags=cosm.OPT_BISECTOR)
