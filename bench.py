@@ -61,6 +61,17 @@ WORKLOADS = {
                  "ablation of Table VII on a G70-like graph (G(n, m) with n = 10000, m = 9999, unit "
                  "weights, greedy colouring): Cosm, without SCS, without DWT, neither; 512 trials x "
                  "2e4 sweeps each"),
+    "fields2d": (lambda: instances.frustrated_loop_planted((100, 100), 0.6, 11), 1024, 2_000,
+                 dict(alpha0_deg=25.0, dwt_ratio=1.0, dwt_period=3, flags=4),
+                 "local fields (eq. (1)): frustrated-loop planted 100x100 torus (loop density 0.6) "
+                 "with unit fields h = tau (along the planted state) on a random 10% of the "
+                 "vertices, drawn twist direction, 1024 replicas, 2e3 sweeps; success = planted "
+                 "ground energy"),
+    "readout": (lambda: instances.torus2d(100, 200, 0), 1024, 100_000,
+                dict(alpha0_deg=14.0, dwt_ratio=0.5, dwt_period=3),
+                "readouts on the default torus workload: 100 bisectors at the last sweep "
+                "against the optimal bisector plus mid-anneal tracking every 1000 sweeps, on the "
+                "same trajectories (same seeds)"),
     "torus16": (lambda: instances.torus2d(16, 16, 0), 64, 1000,
                 dict(alpha0_deg=14.0, dwt_ratio=0.5, dwt_period=3),
                 "2D +-1 torus 16x16 (N=256), 64 replicas, 1000 sweeps"),
@@ -211,16 +222,17 @@ def success_stats(cuts, target, t_step, R):
     return out
 
 
-def measure_single(cosm, inst, col, C, prm, storage, R, S, steps, warmup, seed, local, stream, flush):
+def measure_single(cosm, inst, col, C, prm, storage, R, S, steps, warmup, seed, local, stream, flush,
+                   h=None, keep=False):
     """Times `steps` full trials of R replicas (one cosm_run each) with CUDA
     events on the launching stream, L2 flushed between steps."""
     import torch
-    solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, **prm)
+    solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, h=h, **prm)
     for _ in range(warmup):
         solver.run(S, R, seed, stream)
         solver.sync()
     sampler = ClockSampler(local)
-    times, cuts = [], []
+    times, cuts, energies = [], [], []
     torch.cuda.synchronize()
     sampler.start()
     for k in range(steps):
@@ -235,11 +247,17 @@ def measure_single(cosm, inst, col, C, prm, storage, R, S, steps, warmup, seed, 
         solver.sync()
         times.append(e0.elapsed_time(e1) / 1000.0)
         cuts.append(solver.replica_cuts()[0])
+        energies.append(solver.replica_energies())
     torch.cuda.synchronize()
     clocks = sampler.stop()
     layout = solver.layout()
-    solver.close()
-    return {"t_step": sum(times) / len(times), "cuts": cuts, "clocks": clocks, "layout": layout}
+    out = {"t_step": sum(times) / len(times), "cuts": cuts, "energies": energies, "clocks": clocks,
+           "layout": layout}
+    if keep:
+        out["solver"] = solver
+    else:
+        solver.close()
+    return out
 
 
 def run_ours(args):
@@ -517,6 +535,141 @@ def run_batch(args):
 
 # ---------------------------------------------------------------------- ablation
 
+def _base_line(metric, value, unit, args, t_step, desc, inst, R, S, **extra):
+    line = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded instance generator)",
+            "config": {"workload": args.workload, "description": desc, "n": inst.n, "edges": inst.m,
+                       "replicas_per_gpu": R, "sweeps_per_trial": S,
+                       "l2": "flushed between timed steps (256 MB write)"}}
+    line.update(extra)
+    return line
+
+
+def run_fields(args):
+    """Local fields (eq. (1)) on a planted lattice: throughput and the rate
+    of reaching the planted ground energy."""
+    import torch
+
+    import paper_2605_30355_gb300 as cosm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return None
+    builder, R, S, prm, desc = WORKLOADS[args.workload]
+    R = args.replicas or R
+    S = args.sweeps or S
+    inst = builder()
+    h = instances.aligned_fields(inst, 1, 0.1)
+    ground = inst.meta["ground_energy"] - int(np.abs(h).sum())
+    stream = torch.cuda.Stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    col, C = _colour(inst, args.workload)
+    m = measure_single(cosm, inst, col, C, prm, cosm.F32, R, S, args.steps, args.warmup, 1, local,
+                       stream, flush, h=h)
+    en = np.concatenate(m["energies"])
+    ps = float((en <= ground).mean())
+    r = _r99(ps)
+    updates = (inst.m + inst.n) * S * R  # edge and field updates
+    line = _base_line("edge+field replica updates/s (planted 2D lattice with local fields)",
+                      updates / m["t_step"], "updates/s", args, m["t_step"], desc, inst, R, S,
+                      gpu_launches=2 * args.steps, clocks=m["clocks"],
+                      layout=m["layout"],
+                      success={"ground_energy": int(ground), "trials": int(en.size),
+                               "best_energy": int(en.min()), "mean_energy": float(en.mean()),
+                               "P_s": ps, "R99": r if math.isfinite(r) else None,
+                               "t_trial_s": m["t_step"] / R,
+                               "TTT_s": m["t_step"] / R * r if math.isfinite(r) else None})
+    print(json.dumps(line))
+    return line
+
+
+def run_readout(args):
+    """Readout quality and cost on the same trajectories: the final readout
+    with 100 equally spaced bisectors, against the optimal bisector plus
+    mid-anneal tracking every 1000 sweeps (tracking does not change the
+    dynamics, so replica r follows the same path in both runs)."""
+    import torch
+
+    import paper_2605_30355_gb300 as cosm
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    if rank != 0:
+        return None
+    builder, R, S, prm, desc = WORKLOADS[args.workload]
+    R = args.replicas or R
+    S = args.sweeps or S
+    inst = builder()
+    stream = torch.cuda.Stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    T = min(1000, S)
+    plain = measure_single(cosm, inst, None, 0, prm, cosm.F32, R, S, args.steps, args.warmup, 1, local,
+                           stream, flush)
+    rich = measure_single(cosm, inst, None, 0, dict(prm, flags=cosm.OPT_BISECTOR, track_period=T),
+                          cosm.F32, R, S, args.steps, args.warmup, 1, local, stream, flush, keep=True)
+    # the optimal-bisector readout alone: readouts of the final state
+    s = rich.pop("solver")
+    times = []
+    for k in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.readout(stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1000.0)
+    s.close()
+    p0 = cosm.Solver.from_instance(inst, **prm)
+    p0.run(10, R, 1)
+    t_p = []
+    for k in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        p0.readout(stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_p.append(e0.elapsed_time(e1) / 1000.0)
+    p0.close()
+    a = np.concatenate(plain["cuts"])
+    b = np.concatenate(rich["cuts"])
+    updates = inst.m * S * R
+    # a short anneal, where the phases have not settled into two antipodal
+    # groups when the schedule ends
+    S2 = 1000
+    short = {}
+    for name, extra in (("bisectors_100", {}), ("optimal", dict(flags=cosm.OPT_BISECTOR)),
+                        ("optimal_and_tracking", dict(flags=cosm.OPT_BISECTOR, track_period=100))):
+        sv = cosm.Solver.from_instance(inst, **dict(prm, **extra))
+        sv.run(S2, R, 7)
+        c = sv.replica_cuts()[0]
+        sv.close()
+        short[name] = {"mean_cut": float(c.mean()), "best_cut": int(c.max())}
+    tgt = _targets().get("torus20k") if inst.n == 20000 else None
+    line = _base_line("edge-replica updates/s with the optimal bisector and tracking every 1000 sweeps",
+                      updates / rich["t_step"], "updates/s", args, rich["t_step"], desc, inst, R, S,
+                      gpu_launches=3 * args.steps, clocks=rich["clocks"],
+                      readout={"bisectors_100": {"updates_per_s": updates / plain["t_step"],
+                                                 "mean_cut": float(a.mean()), "best_cut": int(a.max())},
+                               "optimal_and_tracking": {"updates_per_s": updates / rich["t_step"],
+                                                        "mean_cut": float(b.mean()), "best_cut": int(b.max())},
+                               "replicas_improved": float((b > a).mean()),
+                               "replicas_worse": float((b < a).mean()),
+                               "readout_ms": {"bisectors_100": 1000 * min(t_p),
+                                              "optimal": 1000 * min(times)},
+                               "track_period": T,
+                               "short_anneal": dict(short, sweeps=S2, track_period=100)})
+    if tgt is not None:
+        line["readout"]["success"] = {
+            "bisectors_100": success_stats(plain["cuts"], tgt["cut"], plain["t_step"], R)["levels"],
+            "optimal_and_tracking": success_stats(rich["cuts"], tgt["cut"], rich["t_step"], R)["levels"]}
+    print(json.dumps(line))
+    return line
+
+
 def run_ablation(args):
     """Table VII's four variants on the same graph, replicas and seeds."""
     import torch
@@ -642,21 +795,40 @@ def run_serve(args):
 
 # ---------------------------------------------------------------------- oracle
 
+def _oracle_extras(args, inst, prm):
+    """Local fields, flags and tracking of the workload, for the oracle."""
+    h = instances.aligned_fields(inst, 1, 0.1) if args.workload == "fields2d" else None
+    flags = int(prm.get("flags", 0))
+    track = 0
+    if args.workload == "readout":
+        flags |= 8  # the optimal bisector
+        track = 1000
+    return h, flags, track
+
+
 def _oracle_sample(args, inst, col, C, prm):
     import oracle
     oracle.build()
     if col is None:
         col, C = oracle.color_instance(inst)
     g = oracle.ColouredGraph(inst.n, inst.src, inst.dst, inst.w, col, C)
+    h, flags, track = _oracle_extras(args, inst, prm)
+    per_sweep = inst.m + (inst.n if h is not None else 0)
     cores = os.cpu_count() or 1
     reps = cores
-    sweeps = max(10, int(args.cpu_updates / (inst.m * reps)))
+    sweeps = max(10, int(args.cpu_updates / (per_sweep * reps)))
     t0 = time.perf_counter()
-    cuts, _, _, used = oracle.trials(g, sweeps, reps, alpha0=prm["alpha0_deg"] / 360.0,
-                                     dwt_period=prm["dwt_period"], dwt_ratio=prm["dwt_ratio"],
-                                     seed=1, threads=cores)
+    if h is None and not flags and not track:
+        cuts, _, _, used = oracle.trials(g, sweeps, reps, alpha0=prm["alpha0_deg"] / 360.0,
+                                         dwt_period=prm["dwt_period"], dwt_ratio=prm["dwt_ratio"],
+                                         seed=1, threads=cores)
+    else:
+        _, _, _, _ = oracle.trials_ex(g, sweeps, reps, alpha0=prm["alpha0_deg"] / 360.0,
+                                      dwt_period=prm["dwt_period"], dwt_ratio=prm["dwt_ratio"], seed=1,
+                                      threads=cores, h=h, flags=flags, track=min(track, sweeps))
+        used = min(cores, reps)
     dt = time.perf_counter() - t0
-    return inst.m * sweeps * reps / dt, used, f"{reps} replicas x {sweeps} sweeps of the same instance", dt
+    return per_sweep * sweeps * reps / dt, used, f"{reps} replicas x {sweeps} sweeps of the same instance", dt
 
 
 def cpu_baseline(args, inst, col, C, prm):
@@ -688,7 +860,10 @@ def run_reference(args):
         vals.append(v)
         times.append(dt)
     v = sum(vals) / len(vals)
-    line = {"impl": "reference", "metric": "edge-replica updates/s (20k-spin 2D +-1 glass, plain FP32 Cosm)",
+    metric = {"fields2d": "edge+field replica updates/s (planted 2D lattice with local fields)",
+              "readout": "edge-replica updates/s with the optimal bisector and tracking every 1000 sweeps"
+              }.get(args.workload, "edge-replica updates/s (20k-spin 2D +-1 glass, plain FP32 Cosm)")
+    line = {"impl": "reference", "metric": metric,
             "value": v, "unit": "updates/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * sum(times) / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -728,6 +903,10 @@ def main(argv=None):
         run_serve(args)
     elif args.workload == "ablation":
         run_ablation(args)
+    elif args.workload == "fields2d":
+        run_fields(args)
+    elif args.workload == "readout":
+        run_readout(args)
     else:
         run_ours(args)
 

@@ -326,6 +326,20 @@ def frustrated_loop_planted(dims, rho: float, seed: int, R: int = 0) -> Instance
     return inst
 
 
+def aligned_fields(inst: Instance, strength: int, fraction: float = 1.0, seed: int = 0) -> np.ndarray:
+    """Local fields h_i = strength * tau_i on a random `fraction` of the
+    vertices (all of them by default), pointing along a planted instance's
+    hidden state tau; the other fields are 0. Every field term is then
+    lowest at s = tau as well, so tau stays a ground state, with energy
+    ground_energy - strength * (number of fields) (eq. (1))."""
+    tau = np.asarray(inst.meta["tau"], dtype=np.int64)
+    h = int(strength) * tau
+    if fraction < 1.0:
+        u = (Stream(seed, tag=11).u64(inst.n) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+        h = np.where(u < fraction, h, 0)
+    return h.astype(np.int32)
+
+
 def ragged_batch(count: int, seed: int, n_lo: int = 800, n_hi: int = 20000):
     """A ragged batch of instances: N log-uniform in [n_lo, n_hi]; half 2D +-1
     tori with even sides near N, half G(n, m) graphs with m = round(d*N/2),

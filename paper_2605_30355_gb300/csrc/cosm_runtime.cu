@@ -350,31 +350,45 @@ int cosm::choose_layout(cosm_handle *h, int replicas)
         if (forceK && K != forceK) continue;
         const size_t smem = sweep_smem_bytes(p.storage, K, h->g.n, P, mode);
         if (smem > 227 * 1024) continue;
-        int T = forceT ? forceT : std::min(1024, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
-        if (!forceT && T > 512) T = 512;
-        if (mode == MODE_LATTICE2D_ && !forceT) {
-            T = std::min(512, std::max(64, (h->Q + 31) / 32 * 32));
-            // a multiple of the block-row width fixes each thread's column
-            if (h->Wd <= T && (T / h->Wd) * h->Wd >= T / 2) T = (T / h->Wd) * h->Wd;
+        // thread counts to try: edge-list kernels half a colour class's edges
+        // (at most 512); lattice kernels the 2x2 blocks of a sublattice, up
+        // to 512 or, for tiles of at most 4 replicas, 1024 threads
+        int cand[2] = {0, 0};
+        if (forceT) {
+            cand[0] = forceT;
+        } else if (mode == MODE_LATTICE2D_) {
+            for (int c = 0; c < (K <= 4 ? 2 : 1); ++c) {
+                int T = std::min(c ? 1024 : 512, std::max(64, (h->Q + 31) / 32 * 32));
+                // a multiple of the block-row width fixes each thread's column
+                if (h->Wd <= T && (T / h->Wd) * h->Wd >= T / 2) T = (T / h->Wd) * h->Wd;
+                cand[c] = T;
+            }
+            if (cand[1] == cand[0]) cand[1] = 0;
+        } else {
+            cand[0] = std::min(512, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
         }
-        int occ = sweep_occupancy(p.storage, K, mode, T, smem);
-        while (occ == 0 && T > 64 && !forceT) {
-            T /= 2;
-            occ = sweep_occupancy(p.storage, K, mode, T, smem);
-        }
-        if (occ == 0) continue;
-        const long tiles = (replicas + K - 1) / K;
-        // resident replicas per SM, capped by what the run can fill; on a tie
-        // a larger tile amortises per-edge work when the run fills every CTA
-        // slot, a smaller one spreads a small run over more SMs
-        const long resident = std::min<long>((long)occ * K, std::max<long>(1, tiles * K / h->num_sms));
-        const bool full = tiles >= (long)occ * h->num_sms;
-        const long score = resident * 1000 + (full ? K : -K);
-        if (score > bestScore) {
-            bestScore = score;
-            bestK = K;
-            bestT = T;
-            bestOcc = occ;
+        for (int c = 0; c < 2 && cand[c]; ++c) {
+            int T = cand[c];
+            int occ = sweep_occupancy(p.storage, K, mode, T, smem);
+            while (occ == 0 && T > 64 && !forceT) {
+                T /= 2;
+                occ = sweep_occupancy(p.storage, K, mode, T, smem);
+            }
+            if (occ == 0) continue;
+            const long tiles = (replicas + K - 1) / K;
+            // resident replicas per SM, capped by what the run can fill; on a
+            // tie a larger tile amortises per-edge work when the run fills
+            // every CTA slot, a smaller one spreads a small run over more
+            // SMs; then more resident threads hide more latency
+            const long resident = std::min<long>((long)occ * K, std::max<long>(1, tiles * K / h->num_sms));
+            const bool full = tiles >= (long)occ * h->num_sms;
+            const long score = resident * 100000 + (full ? K : -K) * 4096 + (long)occ * T;
+            if (score > bestScore) {
+                bestScore = score;
+                bestK = K;
+                bestT = T;
+                bestOcc = occ;
+            }
         }
     }
     if (!bestK) return fail(COSM_ERR_TOO_LARGE, "no replica tile fits in shared memory");
