@@ -71,7 +71,7 @@ struct InstView {
     int64_t *trace;       // [replicas][n_trace] readout energies
     uint32_t *bits;       // [replicas][words] spins of the kept readout (slot order)
     int32_t words;        // (n + 31) / 32
-    int32_t pad_;
+    int32_t paired;       // binary32 lattice tiles: packed f32x2 passes (else scalar)
 };
 
 // Single-instance launch: the instance plus the CTAs' segment lists.

@@ -730,6 +730,189 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
     }
 }
 
+// ---------------------------------------------------------------- paired binary32
+// Two replicas' binary32 phases in one 64-bit register pair, updated with the
+// packed f32x2 instructions of sm_100 and later: one issue slot carries two
+// binary32 additions, each rounded exactly as the scalar instruction, so the
+// paired passes give bit-identical phases to the scalar ones above.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 p_add(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 p_sub(f32x2 a, f32x2 b)
+{
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 p_fma(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 p_splat(float a)
+{
+    const uint32_t u = __float_as_uint(a);
+    return ((f32x2)u << 32) | u;
+}
+__device__ __forceinline__ float p_lo(f32x2 v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float p_hi(f32x2 v) { return __uint_as_float((uint32_t)(v >> 32)); }
+constexpr f32x2 kMagic2 = 0x4B4000004B400000ull;  // 1.5 * 2^23 in both lanes
+constexpr f32x2 kSign2 = 0x8000000080000000ull;
+constexpr f32x2 kTie2 = 0x0000000100000001ull;    // 2^-149 in both lanes
+__device__ __forceinline__ f32x2 p_wrap(f32x2 v) { return p_sub(v, p_sub(p_add(v, kMagic2), kMagic2)); }
+
+// Pair update of eq. (6) as pair_fast, for two replicas: the step on x1 is
+// +aw iff m = d - rint(d) >= tz, i.e. iff m - tz has a clear sign bit, so the
+// step is aw with its sign bit xor-ed with that of m - tz. This needs
+// m - tz != -0: no phase is ever -0 (the initial draws and set states are
+// +0 at zero, and a round-to-nearest sum or difference that is exactly zero
+// is +0), so d = x1 - x2 is never -0, and d - rint(d) and m - tz of equal
+// operands are +0.
+template <bool kTie>
+__device__ __forceinline__ void pair_x2(f32x2 &x1, f32x2 &x2, f32x2 aw2, f32x2 tz2)
+{
+    const f32x2 d = p_sub(x1, x2);
+    f32x2 m = p_sub(d, p_sub(p_add(d, kMagic2), kMagic2));
+    if (kTie) m = p_sub(m, tz2);
+    const f32x2 st = aw2 ^ (m & kSign2);
+    x1 = p_add(x1, st);
+    x2 = p_sub(x2, st);
+}
+
+template <int K>
+__device__ __forceinline__ void ldp(const float *p, f32x2 (&x)[K / 2])
+{
+    if constexpr (K == 2) {
+        x[0] = *reinterpret_cast<const f32x2 *>(p);
+    } else {
+        static_assert(K == 4, "K");
+        const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(p);
+        x[0] = v.x;
+        x[1] = v.y;
+    }
+}
+template <int K>
+__device__ __forceinline__ void stp(float *p, const f32x2 (&x)[K / 2])
+{
+    if constexpr (K == 2) {
+        *reinterpret_cast<f32x2 *>(p) = x[0];
+    } else {
+        *reinterpret_cast<ulonglong2 *>(p) = make_ulonglong2(x[0], x[1]);
+    }
+}
+
+// The dual window twist of dwt_nowrap for two replicas: y = 2x + c,
+// u = y - rint(y); inside iff (u >= 0 ? u < W2 : u < W2 - 1); an inside lane
+// moves by its replica's step, an outside one adds +0 (exact).
+__device__ __forceinline__ void dwt_x2(f32x2 &x, f32x2 thc2, float W2, f32x2 st2)
+{
+    const f32x2 y = p_fma(0x4000000040000000ull, x, thc2);  // 2x + c
+    const f32x2 u = p_sub(y, p_sub(p_add(y, kMagic2), kMagic2));
+    const float u0 = p_lo(u), u1 = p_hi(u);
+    const bool in0 = (u0 >= 0.0f) ? (u0 < W2) : (u0 < W2 - 1.0f);
+    const bool in1 = (u1 >= 0.0f) ? (u1 < W2) : (u1 < W2 - 1.0f);
+    const f32x2 mask = (in0 ? 0xFFFFFFFFull : 0ull) | (in1 ? 0xFFFFFFFF00000000ull : 0ull);
+    x = p_add(x, st2 & mask);
+}
+
+template <int K>
+__device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wnib, float alpha, int Q)
+{
+    const f32x2 a2 = p_splat(alpha), n2 = a2 ^ kSign2;
+#pragma unroll 2
+    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+        const uint32_t wb = __ldg(wnib + f);
+        f32x2 xa[K / 2], xb[K / 2], xc[K / 2], xd[K / 2];
+        ldp<K>(xs + (size_t)f * K, xa);
+        ldp<K>(xs + (size_t)(Q + f) * K, xb);
+        ldp<K>(xs + (size_t)(2 * Q + f) * K, xc);
+        ldp<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
+        const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
+#pragma unroll
+        for (int h = 0; h < K / 2; ++h) {
+            pair_x2<false>(xa[h], xb[h], w0, 0ull);
+            pair_x2<false>(xc[h], xd[h], w1, 0ull);
+            pair_x2<false>(xa[h], xc[h], w2, 0ull);
+            pair_x2<false>(xb[h], xd[h], w3, 0ull);
+        }
+        stp<K>(xs + (size_t)f * K, xa);
+        stp<K>(xs + (size_t)(Q + f) * K, xb);
+        stp<K>(xs + (size_t)(2 * Q + f) * K, xc);
+        stp<K>(xs + (size_t)(3 * Q + f) * K, xd);
+    }
+}
+
+template <int K, bool kFixedColumn>
+__device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
+                                                  int m0, int dm, bool dwt, const float *thc, float W2,
+                                                  const float *stp_)
+{
+    const f32x2 a2 = p_splat(alpha), n2 = a2 ^ kSign2;
+    f32x2 th2[K / 2], st2[K / 2];
+#pragma unroll
+    for (int h = 0; h < K / 2; ++h) {
+        th2[h] = dwt ? (((f32x2)__float_as_uint(thc[2 * h + 1]) << 32) | __float_as_uint(thc[2 * h])) : 0ull;
+        st2[h] = dwt ? (((f32x2)__float_as_uint(stp_[2 * h + 1]) << 32) | __float_as_uint(stp_[2 * h])) : 0ull;
+    }
+    int m = m0;  // column of block f within its row
+    const bool cw0 = (m0 == Wd - 1);
+    const int goff0 = cw0 ? 1 - Wd : 1;
+    const f32x2 tzc0 = cw0 ? kTie2 : 0ull;
+#pragma unroll 2
+    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+        int goff = goff0;
+        f32x2 tzc = tzc0;
+        if (!kFixedColumn) {
+            const bool cw = (m == Wd - 1);  // next column wraps to column 0
+            goff = cw ? 1 - Wd : 1;
+            tzc = cw ? kTie2 : 0ull;
+            m += dm;
+            if (m >= Wd) m -= Wd;
+        }
+        const bool rw = (f >= Q - Wd);      // next row wraps to row 0
+        const int hoff = rw ? Wd - Q : Wd;
+        const int g = f + goff, hh = f + hoff, gh = g + hoff;
+        const f32x2 tzr = rw ? kTie2 : 0ull;
+        const uint32_t wb = __ldg(wnib + Q + f);
+        f32x2 xd[K / 2], xc[K / 2], xb[K / 2], xa[K / 2];
+        ldp<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        ldp<K>(xs + (size_t)(2 * Q + g) * K, xc);
+        ldp<K>(xs + (size_t)(Q + hh) * K, xb);
+        ldp<K>(xs + (size_t)gh * K, xa);
+        const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
+        const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
+#pragma unroll
+        for (int h = 0; h < K / 2; ++h) {
+            // colour 2: D-C, B-A; colour 3: D-B, C-A
+            pair_x2<true>(xd[h], xc[h], w0, tzc);
+            pair_x2<true>(xb[h], xa[h], w1, tzc);
+            pair_x2<true>(xd[h], xb[h], w2, tzr);
+            pair_x2<true>(xc[h], xa[h], w3, tzr);
+            if (dwt) {
+                dwt_x2(xd[h], th2[h], W2, st2[h]);
+                dwt_x2(xc[h], th2[h], W2, st2[h]);
+                dwt_x2(xb[h], th2[h], W2, st2[h]);
+                dwt_x2(xa[h], th2[h], W2, st2[h]);
+            }
+            xa[h] = p_wrap(xa[h]);
+            xb[h] = p_wrap(xb[h]);
+            xc[h] = p_wrap(xc[h]);
+            xd[h] = p_wrap(xd[h]);
+        }
+        stp<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        stp<K>(xs + (size_t)(2 * Q + g) * K, xc);
+        stp<K>(xs + (size_t)(Q + hh) * K, xb);
+        stp<K>(xs + (size_t)gh * K, xa);
+    }
+}
+
 // ---------------------------------------------------------------- fixed point sweep
 // Eq. (6) on the 2^-16-turn grid: with phases held as q << 16, d = x_i - x_j
 // read as int32 is the minimum angular difference (times 2^32) and the
@@ -1046,14 +1229,28 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
         }
         if (kLattice) {
             // colours 0, 1 in the 2x2 blocks; colours 2, 3 (+ DWT) in the
-            // shifted blocks
-            block_pass_even<Store, K>(t.xs, v.wnib, at.x, v.Q);
-            __syncthreads();
-            if (dm == 0)
-                block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
-            else
-                block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
-            __syncthreads();
+            // shifted blocks; binary32 tiles of an even width in f32x2 pairs
+            constexpr bool kPaired = sizeof(Store) == 4 && (K == 2 || K == 4);
+            if (kPaired && v.paired) {
+                if constexpr (kPaired) {
+                    float *xf = reinterpret_cast<float *>(t.xs);
+                    block_pass_even_x2<K>(xf, v.wnib, at.x, v.Q);
+                    __syncthreads();
+                    if (dm == 0)
+                        block_pass_odd_x2<K, true>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                    else
+                        block_pass_odd_x2<K, false>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                    __syncthreads();
+                }
+            } else {
+                block_pass_even<Store, K>(t.xs, v.wnib, at.x, v.Q);
+                __syncthreads();
+                if (dm == 0)
+                    block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                else
+                    block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                __syncthreads();
+            }
         } else {
             if (kMode == MODE_GENERAL) {
                 // sequential conflict-free search: colours in order (eq. (11))

@@ -448,6 +448,8 @@ InstView cosm::inst_view(cosm_handle *h)
     v.energy = h->d_energy.p;
     v.bisB = h->d_bisB.p;
     v.words = (h->g.n + 31) / 32;
+    // the scalar binary32 lattice passes stay available as a cross-check
+    v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : 1;
     return v;
 }
 
@@ -797,7 +799,7 @@ extern "C" int cosm_set_state(cosm_handle *h, const double *phases, int32_t repl
     for (int32_t r = 0; r < replicas; ++r) {
         const size_t base = (size_t)(r / h->K) * (size_t)h->tile_stride;
         for (int32_t v = 0; v < h->g.n; ++v) {
-            double x = in[(size_t)r * h->g.n + v];
+            double x = in[(size_t)r * h->g.n + v] + 0.0;  // -0 becomes +0
             if (!(x >= 0.0 && x < 1.0)) return fail(COSM_ERR_INVALID_ARG, "phases must be in [0, 1)");
             const double g = x >= 0.5 ? x - 1.0 : x;
             const size_t idx = base + (size_t)h->slot_of[(size_t)v] * h->K + (size_t)(r % h->K);

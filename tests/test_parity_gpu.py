@@ -325,3 +325,22 @@ def test_full_size_workload_sampled(cosm, orc):
     for r in (3, 700):
         err, _ = one_sweep_error(orc, g, x[r], x1[r], alpha, 61, seed=21, replica=r, **kw)
         assert err <= TOL_F32
+
+
+@pytest.mark.parametrize("K,flags", [(2, 0), (4, 0), (2, 4)])
+def test_paired_f32_lattice_equals_scalar(cosm, orc, K, flags):
+    # the f32x2 passes round every lane as the scalar binary32 passes do
+    inst = instances.torus2d(24, 32, 5)
+    os.environ["COSM_K"] = str(K)
+    try:
+        s = cosm.Solver.from_instance(inst, flags=flags, dwt_ratio=1.0)
+        assert s.layout()["lattice"] == 2
+        s.run(400, 3 * K, 21)
+        x_pair, c_pair = s.get_state(), s.replica_cuts()[0]
+        os.environ["COSM_SCALAR_F32"] = "1"
+        s.run(400, 3 * K, 21)
+        assert np.array_equal(s.get_state(), x_pair)
+        assert np.array_equal(s.replica_cuts()[0], c_pair)
+    finally:
+        os.environ.pop("COSM_K", None)
+        os.environ.pop("COSM_SCALAR_F32", None)
