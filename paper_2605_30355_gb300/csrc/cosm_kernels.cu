@@ -216,8 +216,18 @@ __host__ __device__ constexpr size_t smem_bytes(int n, int P, bool accum)
 }
 
 // ---------------------------------------------------------------- pair update
-// Eq. (6) with J = -w, on the minimum angular difference (eq. (4)):
-//   d = x_i - x_j; m = d - rint(d) in [-1/2, 1/2]; s = +1 if m >= 0 else -1
+// Biased sign of eq. (4) on the minimum angular difference of d: +1 iff
+// frac(d) < 1/2, i.e. iff floor(2d) is even. An FMA rounded toward -inf
+// into the binade of 1.5 * 2^23 (ulp 1) gives 1.5 * 2^23 + floor(c d)
+// exactly for |c d| < 2^22, and its last bit is the parity of floor(c d):
+// one instruction for the whole decision, exact at the ties d = k / 2 too.
+// c = -2 evaluates the sign of -d (the other orientation of the pair).
+__device__ __forceinline__ uint32_t floor_parity(float c, float d)
+{
+    return __float_as_uint(__fmaf_rd(c, d, 12582912.0f)) & 1u;
+}
+
+// Eq. (6) with J = -w: d = x_i - x_j; s = sgn_b(d);
 //   x_i <- wrap(x_i + alpha w s); x_j <- wrap(x_j - alpha w s)
 template <int K>
 __device__ __forceinline__ void pair_update(float (&xi)[K], float (&xj)[K], float aw)
@@ -225,8 +235,7 @@ __device__ __forceinline__ void pair_update(float (&xi)[K], float (&xj)[K], floa
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         const float d = __fadd_rn(xi[r], -xj[r]);
-        const float m = __fadd_rn(d, -rint_fast(d));
-        const float st = (m >= 0.0f) ? aw : -aw;
+        const float st = floor_parity(2.0f, d) ? -aw : aw;
         xi[r] = wrap_c(__fadd_rn(xi[r], st));
         xj[r] = wrap_c(__fadd_rn(xj[r], -st));
     }
@@ -553,25 +562,22 @@ __device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int
 
 // Pair update inside a 2x2 block. x1, x2 are the block's slots; eq. (6)
 // takes x_i as the endpoint with the smaller original id, which is x1
-// except at a torus wrap. With d = x1 - x2 and m = d - rint(d) its minimum
-// angular difference (valid for any |d| < 2^22, so phases may stay
-// unwrapped inside a sweep), the biased sign of eq. (4) gives
-//     x_i = x1:  the step on x1 is positive iff m >= 0
-//     x_i = x2:  the step on x1 is positive iff m > 0   (= -sgn_b(-m))
-// so one comparison threshold tz (0, or the least positive binary32 2^-149
-// for a wrap edge) covers both orientations; they agree with the oracle
-// except at the measure-zero tie m = +1/2. aw = alpha w (w = +-1). Phases
-// are wrapped once per sweep, at the end of the odd pass: in between a
-// phase moves by a few steps, so |g| < 1 and binary32 keeps an ulp of at
-// most 2^-24 turn.
+// except at a torus wrap. With d = x1 - x2 (any |d| < 2^21, so phases may
+// stay unwrapped inside a sweep):
+//     x_i = x1:  the step on x1 is +alpha w iff floor(2d) is even
+//     x_i = x2:  the step on x1 is -alpha w iff floor(-2d) is even
+// so a wrap edge passes c = -2 and aw = -alpha w, an ordinary one c = 2 and
+// aw = alpha w, and both follow the oracle's biased sign exactly, ties
+// included. Phases are wrapped once per sweep, at the end of the odd pass:
+// in between a phase moves by a few steps, so |g| < 1 and binary32 keeps an
+// ulp of at most 2^-24 turn.
 template <int K>
-__device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float aw, float tz)
+__device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float aw, float c)
 {
 #pragma unroll
     for (int r = 0; r < K; ++r) {
         const float d = __fadd_rn(x1[r], -x2[r]);
-        const bool p = __fadd_rn(d, -rint_fast(d)) >= tz;
-        const float st = p ? aw : -aw;
+        const float st = floor_parity(c, d) ? -aw : aw;
         x1[r] = __fadd_rn(x1[r], st);
         x2[r] = __fadd_rn(x2[r], -st);
     }
@@ -592,9 +598,9 @@ __device__ __forceinline__ void round_f16(float (&x)[K])
 }
 
 template <typename Store, int K>
-__device__ __forceinline__ void pair_block(float (&x1)[K], float (&x2)[K], float aw, float tz)
+__device__ __forceinline__ void pair_block(float (&x1)[K], float (&x2)[K], float aw, float c)
 {
-    pair_fast<K>(x1, x2, aw, tz);
+    pair_fast<K>(x1, x2, aw, c);
     if constexpr (sizeof(Store) == 2) {
 #pragma unroll
         for (int r = 0; r < K; ++r) {
@@ -635,7 +641,6 @@ __device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, floa
 // loads a block, applies both colours in registers and stores it: every
 // vertex meets one edge of each colour inside its block. Edge indices are
 // implicit; weights are +-1 bits.
-constexpr float kTieUp = 0x1p-149f;  // least positive binary32
 
 __device__ __forceinline__ float signed_alpha(uint32_t wb, uint32_t bit, float alpha)
 {
@@ -654,10 +659,10 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
         ldk<K>(xs + (size_t)(2 * Q + f) * K, xc);
         ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
         // colour 0: A-B, C-D; colour 1: A-C, B-D (first slot = smaller id)
-        pair_block<Store, K>(xa, xb, signed_alpha(wb, 1u, alpha), 0.0f);
-        pair_block<Store, K>(xc, xd, signed_alpha(wb, 2u, alpha), 0.0f);
-        pair_block<Store, K>(xa, xc, signed_alpha(wb, 4u, alpha), 0.0f);
-        pair_block<Store, K>(xb, xd, signed_alpha(wb, 8u, alpha), 0.0f);
+        pair_block<Store, K>(xa, xb, signed_alpha(wb, 1u, alpha), 2.0f);
+        pair_block<Store, K>(xc, xd, signed_alpha(wb, 2u, alpha), 2.0f);
+        pair_block<Store, K>(xa, xc, signed_alpha(wb, 4u, alpha), 2.0f);
+        pair_block<Store, K>(xb, xd, signed_alpha(wb, 8u, alpha), 2.0f);
         // binary32 phases stay unwrapped until the odd pass of this sweep
         stk<K>(xs + (size_t)f * K, xa);
         stk<K>(xs + (size_t)(Q + f) * K, xb);
@@ -679,23 +684,22 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
     int m = m0;  // column of block f within its row
     const bool cw0 = (m0 == Wd - 1);
     const int goff0 = cw0 ? 1 - Wd : 1;
-    const float tzc0 = cw0 ? kTieUp : 0.0f;
 #pragma unroll 2
     for (int f = threadIdx.x; f < Q; f += blockDim.x) {
         int goff = goff0;
-        float tzc = tzc0;
+        bool cw = cw0;
         if (!kFixedColumn) {
-            const bool cw = (m == Wd - 1);  // next column wraps to column 0
+            cw = (m == Wd - 1);  // next column wraps to column 0
             goff = cw ? 1 - Wd : 1;
-            tzc = cw ? kTieUp : 0.0f;
             m += dm;
             if (m >= Wd) m -= Wd;
         }
         const bool rw = (f >= Q - Wd);      // next row wraps to row 0
         const int hoff = rw ? Wd - Q : Wd;
         const int g = f + goff, h = f + hoff, gh = g + hoff;
-        const float tzr = rw ? kTieUp : 0.0f;
-        const uint32_t wb = __ldg(wnib + Q + f);
+        // wrap edges: the other orientation (c = -2, negated step)
+        const float tzc = cw ? -2.0f : 2.0f, tzr = rw ? -2.0f : 2.0f;
+        const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u) ^ (rw ? 12u : 0u);
         float xd[K], xc[K], xb[K], xa[K];
         ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
         ldk<K>(xs + (size_t)(2 * Q + g) * K, xc);
@@ -762,25 +766,36 @@ __device__ __forceinline__ f32x2 p_splat(float a)
 }
 __device__ __forceinline__ float p_lo(f32x2 v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float p_hi(f32x2 v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ f32x2 p_fma_rd(f32x2 a, f32x2 b, f32x2 c)
+{
+    f32x2 d;
+    asm("fma.rm.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
 constexpr f32x2 kMagic2 = 0x4B4000004B400000ull;  // 1.5 * 2^23 in both lanes
 constexpr f32x2 kSign2 = 0x8000000080000000ull;
-constexpr f32x2 kTie2 = 0x0000000100000001ull;    // 2^-149 in both lanes
+constexpr f32x2 kTwo2 = 0x4000000040000000ull;    // 2 in both lanes
+constexpr f32x2 kMinusTwo2 = 0xC0000000C0000000ull;
 __device__ __forceinline__ f32x2 p_wrap(f32x2 v) { return p_sub(v, p_sub(p_add(v, kMagic2), kMagic2)); }
 
-// Pair update of eq. (6) as pair_fast, for two replicas: the step on x1 is
-// +aw iff m = d - rint(d) >= tz, i.e. iff m - tz has a clear sign bit, so the
-// step is aw with its sign bit xor-ed with that of m - tz. This needs
-// m - tz != -0: no phase is ever -0 (the initial draws and set states are
-// +0 at zero, and a round-to-nearest sum or difference that is exactly zero
-// is +0), so d = x1 - x2 is never -0, and d - rint(d) and m - tz of equal
-// operands are +0.
-template <bool kTie>
-__device__ __forceinline__ void pair_x2(f32x2 &x1, f32x2 &x2, f32x2 aw2, f32x2 tz2)
+// aw with its sign flipped where t is odd: aw + t 2^31 mod 2^32 (an integer
+// multiply-add, issued to the FMA pipe rather than the logic unit).
+__device__ __forceinline__ uint32_t flip_if_odd(uint32_t aw, uint32_t t)
+{
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, 0x80000000, %2;" : "=r"(r) : "r"(t), "r"(aw));
+    return r;
+}
+
+// Pair update of eq. (6) as pair_fast, for two replicas: t = 1.5 * 2^23 +
+// floor(c d) per lane (one fma rounded toward -inf), and the step on x1 is
+// aw, negated where floor(c d) is odd.
+__device__ __forceinline__ void pair_x2(f32x2 &x1, f32x2 &x2, f32x2 aw2, f32x2 c2)
 {
     const f32x2 d = p_sub(x1, x2);
-    f32x2 m = p_sub(d, p_sub(p_add(d, kMagic2), kMagic2));
-    if (kTie) m = p_sub(m, tz2);
-    const f32x2 st = aw2 ^ (m & kSign2);
+    const f32x2 t = p_fma_rd(c2, d, kMagic2);
+    const f32x2 st = ((f32x2)flip_if_odd((uint32_t)(aw2 >> 32), (uint32_t)(t >> 32)) << 32) |
+                     flip_if_odd((uint32_t)aw2, (uint32_t)t);
     x1 = p_add(x1, st);
     x2 = p_sub(x2, st);
 }
@@ -837,10 +852,10 @@ __device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wni
         const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
 #pragma unroll
         for (int h = 0; h < K / 2; ++h) {
-            pair_x2<false>(xa[h], xb[h], w0, 0ull);
-            pair_x2<false>(xc[h], xd[h], w1, 0ull);
-            pair_x2<false>(xa[h], xc[h], w2, 0ull);
-            pair_x2<false>(xb[h], xd[h], w3, 0ull);
+            pair_x2(xa[h], xb[h], w0, kTwo2);
+            pair_x2(xc[h], xd[h], w1, kTwo2);
+            pair_x2(xa[h], xc[h], w2, kTwo2);
+            pair_x2(xb[h], xd[h], w3, kTwo2);
         }
         stp<K>(xs + (size_t)f * K, xa);
         stp<K>(xs + (size_t)(Q + f) * K, xb);
@@ -864,23 +879,22 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
     int m = m0;  // column of block f within its row
     const bool cw0 = (m0 == Wd - 1);
     const int goff0 = cw0 ? 1 - Wd : 1;
-    const f32x2 tzc0 = cw0 ? kTie2 : 0ull;
 #pragma unroll 2
     for (int f = threadIdx.x; f < Q; f += blockDim.x) {
         int goff = goff0;
-        f32x2 tzc = tzc0;
+        bool cw = cw0;
         if (!kFixedColumn) {
-            const bool cw = (m == Wd - 1);  // next column wraps to column 0
+            cw = (m == Wd - 1);  // next column wraps to column 0
             goff = cw ? 1 - Wd : 1;
-            tzc = cw ? kTie2 : 0ull;
             m += dm;
             if (m >= Wd) m -= Wd;
         }
         const bool rw = (f >= Q - Wd);      // next row wraps to row 0
         const int hoff = rw ? Wd - Q : Wd;
         const int g = f + goff, hh = f + hoff, gh = g + hoff;
-        const f32x2 tzr = rw ? kTie2 : 0ull;
-        const uint32_t wb = __ldg(wnib + Q + f);
+        // wrap edges: the other orientation (c = -2, negated step)
+        const f32x2 tzc = cw ? kMinusTwo2 : kTwo2, tzr = rw ? kMinusTwo2 : kTwo2;
+        const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u) ^ (rw ? 12u : 0u);
         f32x2 xd[K / 2], xc[K / 2], xb[K / 2], xa[K / 2];
         ldp<K>(xs + (size_t)(3 * Q + f) * K, xd);
         ldp<K>(xs + (size_t)(2 * Q + g) * K, xc);
@@ -891,10 +905,10 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
 #pragma unroll
         for (int h = 0; h < K / 2; ++h) {
             // colour 2: D-C, B-A; colour 3: D-B, C-A
-            pair_x2<true>(xd[h], xc[h], w0, tzc);
-            pair_x2<true>(xb[h], xa[h], w1, tzc);
-            pair_x2<true>(xd[h], xb[h], w2, tzr);
-            pair_x2<true>(xc[h], xa[h], w3, tzr);
+            pair_x2(xd[h], xc[h], w0, tzc);
+            pair_x2(xb[h], xa[h], w1, tzc);
+            pair_x2(xd[h], xb[h], w2, tzr);
+            pair_x2(xc[h], xa[h], w3, tzr);
             if (dwt) {
                 dwt_x2(xd[h], th2[h], W2, st2[h]);
                 dwt_x2(xc[h], th2[h], W2, st2[h]);
@@ -1066,7 +1080,7 @@ __device__ __forceinline__ void field_pass(const InstView &a, Store *xs, float a
         ldk<K>(xs + (size_t)u * K, x);
 #pragma unroll
         for (int r = 0; r < K; ++r) {
-            const float st = (__fadd_rn(x[r], -rint_fast(x[r])) >= 0.0f) ? aw : -aw;
+            const float st = floor_parity(2.0f, x[r]) ? -aw : aw;
             x[r] = wrap_c(__fadd_rn(x[r], st));
         }
         stk<K>(xs + (size_t)u * K, x);
@@ -1278,8 +1292,7 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
 #pragma unroll
                         for (int r = 0; r < K; ++r) {
                             const float d = __fadd_rn(xi[r], -xj[r]);
-                            const float mm = __fadd_rn(d, -rint_fast(d));
-                            const float st = (mm >= 0.0f) ? aw : -aw;
+                            const float st = floor_parity(2.0f, d) ? -aw : aw;
                             t.acc[(size_t)i * K + r] += st;
                             t.acc[(size_t)j * K + r] -= st;
                         }
@@ -1294,7 +1307,7 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
 #pragma unroll
                     for (int r = 0; r < K; ++r) {
                         float dx = t.acc[(size_t)u * K + r];
-                        if (hvu) dx = __fadd_rn(dx, (__fadd_rn(x[r], -rint_fast(x[r])) >= 0.0f) ? aw : -aw);
+                        if (hvu) dx = __fadd_rn(dx, floor_parity(2.0f, x[r]) ? -aw : aw);
                         x[r] = wrap_c(__fadd_rn(x[r], dx));
                     }
                     stk<K>(t.xs + (size_t)u * K, x);

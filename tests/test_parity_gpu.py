@@ -344,3 +344,30 @@ def test_paired_f32_lattice_equals_scalar(cosm, orc, K, flags):
     finally:
         os.environ.pop("COSM_K", None)
         os.environ.pop("COSM_SCALAR_F32", None)
+
+
+@pytest.mark.parametrize("storage,dims,scalar", [(0, True, False), (0, True, True), (0, False, False),
+                                                 (1, True, False), (1, False, False)])
+def test_exact_ties_follow_the_biased_sign(cosm, orc, storage, dims, scalar):
+    # phases on a 1/16-turn grid make many pairs coincide (d = 0) or sit
+    # exactly opposite (d = 1/2); with a step of 1/256 every operation is
+    # exact in binary32, binary16 and FP64, so the sweep must match the
+    # oracle bit for bit, ties included (both orientations of wrap edges)
+    inst = instances.torus2d(16, 16, 3)
+    s, g = _solver(cosm, orc, inst, storage=storage, use_dims=dims)
+    R = 4
+    rng = np.random.default_rng(5)
+    x0 = rng.integers(0, 16, (R, inst.n)) / 16.0
+    if scalar:
+        os.environ["COSM_SCALAR_F32"] = "1"
+    try:
+        s.set_state(x0, seed=3)
+        s.step(1, 1.0 / 256)
+        x1 = s.get_state()
+    finally:
+        os.environ.pop("COSM_SCALAR_F32", None)
+    for r in range(R):
+        xo, ties = orc.sweep(g, x0[r], 1.0 / 256, 1, seed=3, replica=r, storage=storage,
+                             tie_eps=1e-12, **_params_kw(s))
+        assert len(ties) > 0
+        assert np.array_equal(x1[r], xo), r
