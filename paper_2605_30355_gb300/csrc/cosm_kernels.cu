@@ -207,12 +207,12 @@ __host__ __device__ constexpr size_t phase_bytes(int n)
 
 // Shared layout: phases | NO_SCS accumulators (FP32, n*K) | readout
 // difference arrays (int32, K*(P+1)) | per-replica words: DWT offsets,
-// twist steps, readout flags and bisector positions (4K words).
+// twist steps, readout flags, bisector positions, second DWT offsets (5K).
 template <typename Store, int K>
 __host__ __device__ constexpr size_t smem_bytes(int n, int P, bool accum)
 {
     return phase_bytes<Store, K>(n) + (accum ? round16((size_t)n * K * 4) : 0) +
-           round16((size_t)K * (P + 1) * 4) + round16((size_t)K * 16);
+           round16((size_t)K * (P + 1) * 4) + round16((size_t)K * 20);
 }
 
 // ---------------------------------------------------------------- pair update
@@ -244,17 +244,22 @@ __device__ __forceinline__ void pair_update(float (&xi)[K], float (&xj)[K], floa
 // ---------------------------------------------------------------- DWT
 // Dual window twist (Section II-D): windows [th - W/2, th + W/2) and their
 // antipode; x is inside iff ((x - th + W/2) mod 1/2) < W. With y = 2x + c,
-// c = 2 (W/2 - th) precomputed per replica, the test is frac(y) < 2W.
+// c = 2 (W/2 - th) precomputed per replica, the test is frac(y) < 2W, i.e.
+// floor(y) != floor(y - 2W): two adds rounded toward -inf into the binade
+// of 1.5 * 2^23 give both floors, and they differ exactly for the phases
+// inside (c2 = c - 2W is precomputed too).
+__device__ __forceinline__ bool in_windows(float x, float c1, float c2)
+{
+    const float y1 = fmaf(2.0f, x, c1), y2 = fmaf(2.0f, x, c2);
+    return __float_as_uint(__fadd_rd(y1, 12582912.0f)) != __float_as_uint(__fadd_rd(y2, 12582912.0f));
+}
+
 template <int K>
-__device__ __forceinline__ void dwt_apply(float (&x)[K], const float *thc, float W2, const float (&st)[K])
+__device__ __forceinline__ void dwt_apply(float (&x)[K], const float *thc, const float *thc2, const float (&st)[K])
 {
 #pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const float y = fmaf(2.0f, x[r], thc[r]);
-        const float u = __fadd_rn(y, -rint_fast(y));
-        const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
-        if (in) x[r] = wrap_c(__fadd_rn(x[r], st[r]));
-    }
+    for (int r = 0; r < K; ++r)
+        if (in_windows(x[r], thc[r], thc2[r])) x[r] = wrap_c(__fadd_rn(x[r], st[r]));
 }
 
 // ---------------------------------------------------------------- segments
@@ -266,6 +271,7 @@ struct Tile {
     float *acc;    // [n][K] NO_SCS accumulators (mode 1 only)
     int *D;        // [K][P+1] readout difference arrays
     float *thc;    // [K] DWT offsets 2 (W/2 - theta)
+    float *thc2;   // [K] the same minus 2W
     float *stp;    // [K] twist step of each replica (sign drawn or +1)
     int *imp;      // [K] readout: the replica's kept readout changed
     uint32_t *Bs;  // [K] readout: bisector position of the replica
@@ -287,6 +293,7 @@ __device__ __forceinline__ Tile<Store, K> carve(unsigned char *smem, int n, int 
     t.stp = t.thc + K;
     t.imp = reinterpret_cast<int *>(t.thc + 2 * K);
     t.Bs = reinterpret_cast<uint32_t *>(t.thc + 3 * K);
+    t.thc2 = t.thc + 4 * K;
     return t;
 }
 
@@ -620,15 +627,11 @@ __device__ __forceinline__ void wrap_all(float (&x)[K])
 }
 
 template <int K>
-__device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, float W2, const float (&st)[K])
+__device__ __forceinline__ void dwt_nowrap(float (&x)[K], const float *thc, const float *thc2, const float (&st)[K])
 {
 #pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const float y = fmaf(2.0f, x[r], thc[r]);
-        const float u = __fadd_rn(y, -rint_fast(y));
-        const bool in = (u >= 0.0f) ? (u < W2) : (u < W2 - 1.0f);
-        if (in) x[r] = __fadd_rn(x[r], st[r]);
-    }
+    for (int r = 0; r < K; ++r)
+        if (in_windows(x[r], thc[r], thc2[r])) x[r] = __fadd_rn(x[r], st[r]);
 }
 
 // 2D torus in the sublattice layout: groups A = (even r, even c), B = (even,
@@ -675,7 +678,7 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
 // thread visits sits in the same column and the column wrap is fixed.
 template <typename Store, int K, bool kFixedColumn>
 __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
-                                               int m0, int dm, bool dwt, const float *thc, float W2,
+                                               int m0, int dm, bool dwt, const float *thc, const float *thc2,
                                                const float *stp)
 {
     float st[K];  // the twist step of each replica
@@ -715,15 +718,15 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
             // the DWT follows the last colour of the sweep; every vertex is in
             // exactly one shifted block
             if constexpr (sizeof(Store) == 4) {
-                dwt_nowrap<K>(xd, thc, W2, st);
-                dwt_nowrap<K>(xc, thc, W2, st);
-                dwt_nowrap<K>(xb, thc, W2, st);
-                dwt_nowrap<K>(xa, thc, W2, st);
+                dwt_nowrap<K>(xd, thc, thc2, st);
+                dwt_nowrap<K>(xc, thc, thc2, st);
+                dwt_nowrap<K>(xb, thc, thc2, st);
+                dwt_nowrap<K>(xa, thc, thc2, st);
             } else {
-                dwt_apply<K>(xd, thc, W2, st);
-                dwt_apply<K>(xc, thc, W2, st);
-                dwt_apply<K>(xb, thc, W2, st);
-                dwt_apply<K>(xa, thc, W2, st);
+                dwt_apply<K>(xd, thc, thc2, st);
+                dwt_apply<K>(xc, thc, thc2, st);
+                dwt_apply<K>(xb, thc, thc2, st);
+                dwt_apply<K>(xa, thc, thc2, st);
             }
         }
         wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
@@ -822,18 +825,29 @@ __device__ __forceinline__ void stp(float *p, const f32x2 (&x)[K / 2])
     }
 }
 
-// The dual window twist of dwt_nowrap for two replicas: y = 2x + c,
-// u = y - rint(y); inside iff (u >= 0 ? u < W2 : u < W2 - 1); an inside lane
-// moves by its replica's step, an outside one adds +0 (exact).
-__device__ __forceinline__ void dwt_x2(f32x2 &x, f32x2 thc2, float W2, f32x2 st2)
+// The dual window twist of dwt_nowrap for two replicas: the floors of
+// y1 = 2x + c and y2 = 2x + c - 2W per lane (fma, then an add rounded toward
+// -inf into the binade of 1.5 * 2^23); their difference (1 inside, 0
+// outside) scales the lane's step, and an outside lane adds +0 (exact).
+__device__ __forceinline__ f32x2 p_add_rd(f32x2 a, f32x2 b)
 {
-    const f32x2 y = p_fma(0x4000000040000000ull, x, thc2);  // 2x + c
-    const f32x2 u = p_sub(y, p_sub(p_add(y, kMagic2), kMagic2));
-    const float u0 = p_lo(u), u1 = p_hi(u);
-    const bool in0 = (u0 >= 0.0f) ? (u0 < W2) : (u0 < W2 - 1.0f);
-    const bool in1 = (u1 >= 0.0f) ? (u1 < W2) : (u1 < W2 - 1.0f);
-    const f32x2 mask = (in0 ? 0xFFFFFFFFull : 0ull) | (in1 ? 0xFFFFFFFF00000000ull : 0ull);
-    x = p_add(x, st2 & mask);
+    f32x2 d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+__device__ __forceinline__ uint32_t times_diff(uint32_t st, uint32_t k1, uint32_t k2)
+{
+    return (k1 - k2) * st;
+}
+
+__device__ __forceinline__ void dwt_x2(f32x2 &x, f32x2 c1, f32x2 c2, f32x2 st2)
+{
+    const f32x2 k1 = p_add_rd(p_fma(kTwo2, x, c1), kMagic2);
+    const f32x2 k2 = p_add_rd(p_fma(kTwo2, x, c2), kMagic2);
+    const f32x2 add = ((f32x2)times_diff((uint32_t)(st2 >> 32), (uint32_t)(k1 >> 32), (uint32_t)(k2 >> 32)) << 32) |
+                      times_diff((uint32_t)st2, (uint32_t)k1, (uint32_t)k2);
+    x = p_add(x, add);
 }
 
 template <int K>
@@ -866,14 +880,15 @@ __device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wni
 
 template <int K, bool kFixedColumn>
 __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
-                                                  int m0, int dm, bool dwt, const float *thc, float W2,
+                                                  int m0, int dm, bool dwt, const float *thc, const float *thc2,
                                                   const float *stp_)
 {
     const f32x2 a2 = p_splat(alpha), n2 = a2 ^ kSign2;
-    f32x2 th2[K / 2], st2[K / 2];
+    f32x2 th2[K / 2], tk2[K / 2], st2[K / 2];
 #pragma unroll
     for (int h = 0; h < K / 2; ++h) {
         th2[h] = dwt ? (((f32x2)__float_as_uint(thc[2 * h + 1]) << 32) | __float_as_uint(thc[2 * h])) : 0ull;
+        tk2[h] = dwt ? (((f32x2)__float_as_uint(thc2[2 * h + 1]) << 32) | __float_as_uint(thc2[2 * h])) : 0ull;
         st2[h] = dwt ? (((f32x2)__float_as_uint(stp_[2 * h + 1]) << 32) | __float_as_uint(stp_[2 * h])) : 0ull;
     }
     int m = m0;  // column of block f within its row
@@ -910,10 +925,10 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
             pair_x2(xd[h], xb[h], w2, tzr);
             pair_x2(xc[h], xa[h], w3, tzr);
             if (dwt) {
-                dwt_x2(xd[h], th2[h], W2, st2[h]);
-                dwt_x2(xc[h], th2[h], W2, st2[h]);
-                dwt_x2(xb[h], th2[h], W2, st2[h]);
-                dwt_x2(xa[h], th2[h], W2, st2[h]);
+                dwt_x2(xd[h], th2[h], tk2[h], st2[h]);
+                dwt_x2(xc[h], th2[h], tk2[h], st2[h]);
+                dwt_x2(xb[h], th2[h], tk2[h], st2[h]);
+                dwt_x2(xa[h], th2[h], tk2[h], st2[h]);
             }
             xa[h] = p_wrap(xa[h]);
             xb[h] = p_wrap(xb[h]);
@@ -1238,7 +1253,9 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
         const bool dwt = dwt_on && phase == 0;
         if (dwt && tid < K) {
             bool neg = false;
-            t.thc[tid] = 2.0f * (hw - dwt_theta(v.seed, rep0 + tid, s, &neg));
+            const float c = 2.0f * (hw - dwt_theta(v.seed, rep0 + tid, s, &neg));
+            t.thc[tid] = c;
+            t.thc2[tid] = c - W2;
             t.stp[tid] = (randdir && neg) ? -at.y : at.y;
         }
         if (kLattice) {
@@ -1251,18 +1268,18 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                     block_pass_even_x2<K>(xf, v.wnib, at.x, v.Q);
                     __syncthreads();
                     if (dm == 0)
-                        block_pass_odd_x2<K, true>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                        block_pass_odd_x2<K, true>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
                     else
-                        block_pass_odd_x2<K, false>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                        block_pass_odd_x2<K, false>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
                     __syncthreads();
                 }
             } else {
                 block_pass_even<Store, K>(t.xs, v.wnib, at.x, v.Q);
                 __syncthreads();
                 if (dm == 0)
-                    block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                    block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
                 else
-                    block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, W2, t.stp);
+                    block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
                 __syncthreads();
             }
         } else {
@@ -1322,7 +1339,7 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 for (int u = tid; u < n; u += nt) {
                     float x[K];
                     ldk<K>(t.xs + (size_t)u * K, x);
-                    dwt_apply<K>(x, t.thc, W2, st);
+                    dwt_apply<K>(x, t.thc, t.thc2, st);
                     stk<K>(t.xs + (size_t)u * K, x);
                 }
                 __syncthreads();
