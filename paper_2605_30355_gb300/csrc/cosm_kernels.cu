@@ -533,6 +533,13 @@ __device__ void seg_end(const InstView &a, const Segment &sg, const Tile<Store, 
 // several edge-record loads in flight.
 constexpr int kBatch = 4;
 
+// An int8 weight as a float without the conversion unit: the bits of
+// 1.5 * 2^23 + w, minus 1.5 * 2^23 (exact for |w| < 2^22).
+__device__ __forceinline__ float weight_f(int8_t w)
+{
+    return __fadd_rn(__int_as_float(0x4B400000 + (int)w), -12582912.0f);
+}
+
 template <typename Store, int K>
 __device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int c, float alpha)
 {
@@ -545,7 +552,7 @@ __device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int
         for (int u = 0; u < kBatch; ++u) {
             const int e = e0 + u * nt;
             rec[u] = e < e1 ? __ldg(a.ij + e) : 0u;
-            aw[u] = e < e1 ? alpha * (float)__ldg(a.w + e) : 0.0f;
+            aw[u] = e < e1 ? alpha * weight_f(__ldg(a.w + e)) : 0.0f;
         }
         float xi[kBatch][K], xj[kBatch][K];
 #pragma unroll
