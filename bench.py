@@ -346,6 +346,10 @@ def run_ours(args):
 
     # ---- roofline of the sweep kernel: shared memory and FP32 issue
     roof = roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks)
+    traffic = DRAM_TRAFFIC.get((args.workload, args.storage, R, S))
+    if traffic is not None:
+        roof["traffic"] = traffic
+        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one full-size launch"
 
     line = {
         "metric": "edge-replica updates/s (20k-spin 2D +-1 glass, plain FP32 Cosm)",
@@ -378,6 +382,12 @@ def run_ours(args):
         dist.destroy_process_group()
     return line
 
+
+# DRAM bytes (read + write) of one full-size launch of the headline sweep
+# kernel, from the one-pass ncu capture summarised in
+# profiles/launches_torus20k_bench.md; keyed by (workload, storage,
+# replicas, sweeps). Only the exact configuration captured gets a number.
+DRAM_TRAFFIC = {("torus20k", "f32", 1024, 100_000): 8.86e6 + 76.77e6}
 
 # Algorithmic FP32 operations of one edge-replica update (eq. (6) on the
 # minimum angular difference): difference, rounding to the nearest turn,
