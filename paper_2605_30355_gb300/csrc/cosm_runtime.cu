@@ -195,6 +195,106 @@ static int setup_lattice2d(cosm_handle *h)
     return COSM_OK;
 }
 
+// Order of one colour class's edges for the edge-list kernel. A warp takes
+// 32 consecutive edges; with two binary32 replicas per slot (8 bytes) a
+// half-warp's 16 loads of source phases, and its 16 loads of destination
+// phases, are each conflict-free in shared memory when their slots are
+// distinct modulo 16. Edges are grouped accordingly: the class is read as a
+// bipartite multigraph between source residues and destination residues
+// (slot mod 16), properly edge-coloured with its maximum degree of colours
+// by Konig's alternating-path method, and each colour class (at most one
+// edge per residue on either side) becomes a run of consecutive edges,
+// largest first, in source-residue order. Edges of one colour share no
+// vertex, so their order changes no result; it only changes which phases a
+// half-warp touches together.
+static void balance_banks(int64_t *e, int64_t cnt, const std::vector<int32_t> &ss,
+                          const std::vector<int32_t> &ds)
+{
+    constexpr int R = 16;
+    if (cnt < 32 || cnt > ((int64_t)1 << 20)) return;
+    std::vector<int32_t> A((size_t)cnt), B((size_t)cnt);
+    int deg[2 * R] = {0};
+    for (int64_t k = 0; k < cnt; ++k) {
+        A[(size_t)k] = ss[(size_t)e[k]] & (R - 1);
+        B[(size_t)k] = R + (ds[(size_t)e[k]] & (R - 1));
+        ++deg[A[(size_t)k]];
+        ++deg[B[(size_t)k]];
+    }
+    int D = 0;
+    for (int v = 0; v < 2 * R; ++v) D = std::max(D, deg[v]);
+    const int Wd = (D + 63) / 64;
+    std::vector<int32_t> at((size_t)2 * R * D, -1);  // at[v D + c]: edge of colour c at residue v
+    std::vector<uint64_t> freeb((size_t)2 * R * Wd, ~0ull);
+    std::vector<int32_t> color((size_t)cnt, -1);
+    auto mark = [&](int v, int c, bool used) {
+        uint64_t &w = freeb[(size_t)v * Wd + c / 64];
+        if (used) w &= ~(1ull << (c % 64));
+        else w |= 1ull << (c % 64);
+    };
+    auto first_free = [&](int v, int u) {  // first colour free at v (and at u when u >= 0)
+        for (int w = 0; w < Wd; ++w) {
+            uint64_t f = freeb[(size_t)v * Wd + w];
+            if (u >= 0) f &= freeb[(size_t)u * Wd + w];
+            if (w == Wd - 1 && D % 64) f &= (1ull << (D % 64)) - 1;
+            if (f) return w * 64 + __builtin_ctzll(f);
+        }
+        return -1;
+    };
+    auto put = [&](int32_t k, int c) {
+        color[(size_t)k] = c;
+        at[(size_t)A[(size_t)k] * D + c] = k;
+        at[(size_t)B[(size_t)k] * D + c] = k;
+        mark(A[(size_t)k], c, true);
+        mark(B[(size_t)k], c, true);
+    };
+    auto take = [&](int32_t k) {
+        const int c = color[(size_t)k];
+        at[(size_t)A[(size_t)k] * D + c] = -1;
+        at[(size_t)B[(size_t)k] * D + c] = -1;
+        mark(A[(size_t)k], c, false);
+        mark(B[(size_t)k], c, false);
+    };
+    std::vector<int32_t> path;
+    for (int32_t k = 0; k < (int32_t)cnt; ++k) {
+        const int a = A[(size_t)k], b = B[(size_t)k];
+        int c = first_free(a, b);
+        if (c < 0) {
+            // colour al free at a, be free at b; swap al/be along the
+            // alternating path that starts at b with its al-edge (it never
+            // reaches a), after which al is free at both ends
+            const int al = first_free(a, -1), be = first_free(b, -1);
+            path.clear();
+            int v = b, cur = al;
+            for (;;) {
+                const int32_t k2 = at[(size_t)v * D + cur];
+                if (k2 < 0) break;
+                path.push_back(k2);
+                v = (B[(size_t)k2] == v) ? A[(size_t)k2] : B[(size_t)k2];
+                cur = (cur == al) ? be : al;
+            }
+            std::vector<int> old(path.size());
+            for (size_t i = 0; i < path.size(); ++i) {
+                old[i] = color[(size_t)path[i]];
+                take(path[i]);
+            }
+            for (size_t i = 0; i < path.size(); ++i) put(path[i], old[i] == al ? be : al);
+            c = al;
+        }
+        put(k, c);
+    }
+    std::vector<std::vector<int32_t>> groups((size_t)D);
+    for (int32_t k = 0; k < (int32_t)cnt; ++k) groups[(size_t)color[(size_t)k]].push_back(k);
+    std::stable_sort(groups.begin(), groups.end(),
+                     [](const std::vector<int32_t> &x, const std::vector<int32_t> &y) { return x.size() > y.size(); });
+    std::vector<int64_t> out;
+    out.reserve((size_t)cnt);
+    for (auto &g : groups) {
+        std::sort(g.begin(), g.end(), [&](int32_t x, int32_t y) { return A[(size_t)x] < A[(size_t)y]; });
+        for (int32_t k : g) out.push_back(e[k]);
+    }
+    std::copy(out.begin(), out.end(), e);
+}
+
 extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm_handle **out)
 {
     if (!gd || !out) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
@@ -272,6 +372,20 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
         if (g.color[(size_t)a] != g.color[(size_t)b]) return g.color[(size_t)a] < g.color[(size_t)b];
         return h->slot_of[(size_t)g.src[(size_t)a]] < h->slot_of[(size_t)g.src[(size_t)b]];
     });
+    {
+        std::vector<int32_t> ss((size_t)g.m), ds((size_t)g.m);
+        for (int64_t e = 0; e < g.m; ++e) {
+            ss[(size_t)e] = h->slot_of[(size_t)g.src[(size_t)e]];
+            ds[(size_t)e] = h->slot_of[(size_t)g.dst[(size_t)e]];
+        }
+        int64_t a = 0;
+        while (a < g.m) {
+            int64_t z = a;
+            while (z < g.m && g.color[(size_t)order[(size_t)z]] == g.color[(size_t)order[(size_t)a]]) ++z;
+            if (!std::getenv("COSM_SRC_ORDER")) balance_banks(order.data() + a, z - a, ss, ds);
+            a = z;
+        }
+    }
     std::vector<uint32_t> ij((size_t)g.m);
     std::vector<int8_t> wv((size_t)g.m);
     std::memset(h->off, 0, sizeof(h->off));

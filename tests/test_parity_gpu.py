@@ -371,3 +371,22 @@ def test_exact_ties_follow_the_biased_sign(cosm, orc, storage, dims, scalar):
                              tie_eps=1e-12, **_params_kw(s))
         assert len(ties) > 0
         assert np.array_equal(x1[r], xo), r
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2])
+def test_edge_order_within_colours_changes_nothing(cosm, orc, storage):
+    # the bank-spreading order of each colour class against the plain
+    # source-slot order: a colour is a matching, so trials are identical
+    inst = instances.sparse_gnm(3000, 9000, 4)
+    col, C = orc.color_greedy(inst.n, inst.src, inst.dst)
+    kw = dict(color=col, n_colors=C, storage=storage, dwt_ratio=1.0)
+    a = cosm.Solver(inst.n, inst.src, inst.dst, inst.w, **kw)
+    a.run(200, 6, 9)
+    os.environ["COSM_SRC_ORDER"] = "1"
+    try:
+        b = cosm.Solver(inst.n, inst.src, inst.dst, inst.w, **kw)
+    finally:
+        os.environ.pop("COSM_SRC_ORDER", None)
+    b.run(200, 6, 9)
+    assert np.array_equal(a.get_state(), b.get_state())
+    assert np.array_equal(a.replica_cuts()[0], b.replica_cuts()[0])
