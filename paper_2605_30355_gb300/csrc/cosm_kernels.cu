@@ -528,10 +528,14 @@ __device__ void seg_end(const InstView &a, const Segment &sg, const Tile<Store, 
 
 // ---------------------------------------------------------------- sub-sweeps
 // General graphs: colour c's edge records [off[c], off[c+1]) map to threads;
-// each thread takes kBatch edges at a time (edges of one colour share no
+// each thread takes a batch of edges at a time (edges of one colour share no
 // vertex, so all loads of a batch may precede its stores), which keeps
-// several edge-record loads in flight.
-constexpr int kBatch = 4;
+// several edge-record loads in flight: 8 for tiles of 2 or 4 replicas (a
+// large tile per SM, registers to spare), 4 for single-replica tiles (many
+// small CTAs per SM, where registers bound occupancy) and for 8-replica
+// tiles (whose per-edge state would not fit in registers).
+template <int K>
+__host__ __device__ constexpr int edge_batch() { return (K == 2 || K == 4) ? 8 : 4; }
 
 // An int8 weight as a float without the conversion unit: the bits of
 // 1.5 * 2^23 + w, minus 1.5 * 2^23 (exact for |w| < 2^22).
@@ -545,6 +549,7 @@ __device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int e1 = __ldg(a.off + c + 1);
+    constexpr int kBatch = edge_batch<K>();
     for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += kBatch * nt) {
         uint32_t rec[kBatch];
         float aw[kBatch];
@@ -980,6 +985,7 @@ __device__ __forceinline__ void general_colour_q(const InstView &a, uint16_t *xs
 {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int e1 = __ldg(a.off + c + 1);
+    constexpr int kBatch = edge_batch<K>();
     for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += kBatch * nt) {
         uint32_t rec[kBatch], ap[kBatch];
 #pragma unroll
