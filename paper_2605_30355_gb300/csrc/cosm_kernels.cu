@@ -579,6 +579,81 @@ __device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int
     }
 }
 
+// The colours of one sweep with the edge records of each thread's next
+// batch loaded while the current batch is processed, across colour
+// boundaries and into the next sweep too (records do not depend on the
+// phases), so their L2 latency overlaps the shared-memory work. pf carries
+// the prefetched batch between sweeps; pf.e0 names its first edge (-1: none).
+template <int B>
+struct EdgePrefetch {
+    uint32_t rec[B];
+    int32_t w[B];
+    int e0;
+};
+
+template <int B>
+__device__ __forceinline__ void fetch_edges(const InstView &a, int e0, int e1, uint32_t (&rec)[B],
+                                            int32_t (&w)[B])
+{
+    const int nt = blockDim.x;
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int e = e0 + u * nt;
+        rec[u] = e < e1 ? __ldg(a.ij + e) : 0u;
+        w[u] = e < e1 ? (int32_t)__ldg(a.w + e) : 0;
+    }
+}
+
+template <typename Store, int K, int B>
+__device__ __forceinline__ void general_colours_pf(const InstView &a, Store *xs, float alpha, EdgePrefetch<B> &pf)
+{
+    const int tid = threadIdx.x, nt = blockDim.x, step = B * nt;
+    for (int c = 0; c < a.C; ++c) {
+        const int e1 = __ldg(a.off + c + 1);
+        for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += step) {
+            uint32_t rec[B];
+            int32_t wv[B];
+            if (pf.e0 == e0) {
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    rec[u] = pf.rec[u];
+                    wv[u] = pf.w[u];
+                }
+            } else {
+                fetch_edges<B>(a, e0, e1, rec, wv);
+            }
+            // the next batch: further in this colour, else the first batch
+            // of the next colour (of colour 0 for the next sweep)
+            int n0 = e0 + step, n1 = e1;
+            if (n0 >= e1) {
+                const int nc = (c + 1 < a.C) ? c + 1 : 0;
+                n0 = __ldg(a.off + nc) + tid;
+                n1 = __ldg(a.off + nc + 1);
+            }
+            fetch_edges<B>(a, n0, n1, pf.rec, pf.w);
+            pf.e0 = n0;
+            float xi[B][K], xj[B][K];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                if (e0 + u * nt < e1) {
+                    ldk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
+                    ldk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < B; ++u) pair_update<K>(xi[u], xj[u], alpha * weight_f((int8_t)wv[u]));
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                if (e0 + u * nt < e1) {
+                    stk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
+                    stk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // Pair update inside a 2x2 block. x1, x2 are the block's slots; eq. (6)
 // takes x_i as the endpoint with the smaller original id, which is x1
 // except at a torus wrap. With d = x1 - x2 (any |d| < 2^21, so phases may
@@ -1261,6 +1336,8 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
     if (!seg_begin<Store, K>(v, sg, t, s_skip, ready, err, wait_limit_ns)) return;
     const uint32_t rep0 = (uint32_t)sg.tile * K;
     int phase = dwt_on ? (int)(sg.s_begin % v.dwt_period) : 1;
+    EdgePrefetch<4> pf;
+    pf.e0 = -1;
     for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
         const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));
         const bool dwt = dwt_on && phase == 0;
@@ -1297,10 +1374,16 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
             }
         } else {
             if (kMode == MODE_GENERAL) {
-                // sequential conflict-free search: colours in order (eq. (11))
-                for (int c = 0; c < v.C; ++c) {
-                    general_colour<Store, K>(v, t.xs, c, at.x);
-                    __syncthreads();
+                // sequential conflict-free search: colours in order (eq. (11));
+                // tiles of 2 or 4 replicas prefetch their next edge batch,
+                // single- and 8-replica tiles keep registers for occupancy
+                if constexpr (K == 2 || K == 4) {
+                    general_colours_pf<Store, K, 4>(v, t.xs, at.x, pf);
+                } else {
+                    for (int c = 0; c < v.C; ++c) {
+                        general_colour<Store, K>(v, t.xs, c, at.x);
+                        __syncthreads();
+                    }
                 }
                 if (v.hv) {
                     field_pass<Store, K>(v, t.xs, at.x);
