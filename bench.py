@@ -113,6 +113,32 @@ def max_over_ranks(x: float, device: str = "cpu") -> float:
     return float(t.item())
 
 
+def global_best(cut: int, spins, device: str = "cpu"):
+    """The one exchange of a sharded run, after the timed region: the best
+    cut over all ranks (ties -> the lowest rank), its owner, and the owner's
+    spins broadcast to every rank. Returns (cut, owner, spins)."""
+    import torch
+    import torch.distributed as dist
+    s = torch.as_tensor(np.asarray(spins, dtype=np.int8)).to(device)
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return int(cut), 0, s.cpu().numpy()
+    rank = dist.get_rank()
+    # one int64 max-reduce of (cut, -rank) packed as cut * 2^20 + (2^20 - 1 - rank)
+    key = torch.tensor([int(cut) * (1 << 20) + ((1 << 20) - 1 - rank)], dtype=torch.int64, device=device)
+    dist.all_reduce(key, op=dist.ReduceOp.MAX)
+    k = int(key.item())
+    best, owner = k >> 20, (1 << 20) - 1 - (k & ((1 << 20) - 1))
+    dist.broadcast(s, src=owner)
+    return best, owner, s.cpu().numpy()
+
+
+def spins_cut(inst, spins) -> int:
+    """Cut of a spin vector (sum of w over edges whose ends differ), a host
+    check of the exchanged spins."""
+    sp = np.asarray(spins)
+    return int(np.asarray(inst.w, dtype=np.int64)[sp[inst.src] != sp[inst.dst]].sum())
+
+
 def whole_job_rate(units_per_rank: float, world: int, t_max: float) -> float:
     """Whole-job throughput: every rank processed units_per_rank units; the
     job took the slowest rank's time."""
@@ -328,6 +354,13 @@ def run_ours(args):
         batched = measure_batch(cosm, args, rank, ws, local, stream, flush, steps=2, warmup=1,
                                 e2e=False)
 
+    # ---- the best state over all ranks (untimed): one max-reduce, one broadcast
+    solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, **prm)
+    solver.run(min(S, 1000), min(R, 256), seed + 7, stream)
+    b_cut, _, _, b_spins = solver.best()
+    solver.close()
+    g_cut, g_owner, g_spins = global_best(b_cut, b_spins, "cuda" if ws > 1 else "cpu")
+
     if rank != 0:
         if ws > 1:
             dist.destroy_process_group()
@@ -363,6 +396,9 @@ def run_ours(args):
                    "replicas_per_cta": layout["K"], "threads_per_cta": layout["threads"],
                    "ctas": layout["grid"], "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas sharded over {ws} GPU(s), no collective on the data path"},
+        "global_best": {"cut": g_cut, "owner_rank": g_owner, "spins_cut": spins_cut(inst, g_spins),
+                        "run": "after the timed region: min(S, 1000) sweeps x min(R, 256) replicas per "
+                               "rank, an int64 max-reduce of (cut, rank), a broadcast of the owner's spins"},
         "e2e": None if e2e_t is None else {
             "value": whole_job_rate(updates, ws, e2e_t), "unit": "updates/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "api": "cosm_solve (host buffers)"},

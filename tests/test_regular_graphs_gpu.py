@@ -43,7 +43,7 @@ def test_one_sweep_regular(cosm, orc, n, d, storage):
     x0 = np.stack([orc.init_phases(inst.n, 11, r) for r in range(R)])
     if storage == 1:
         x0 = f16_exact_turns(x0)
-    for sweep in (3, 700):
+    for sweep in (1, 10, 100, 1000):
         s.set_state(x0, seed=11)
         alpha = float(np.float32(orc.alpha(sweep, 1000, A14)))
         s.step(sweep, alpha)
