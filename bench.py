@@ -301,7 +301,7 @@ def run_ours(args):
         R = args.replicas
     if args.sweeps:
         S = args.sweeps
-    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage]
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16, "bf16": cosm.BF16}[args.storage]
     inst = builder()
     col, C = _colour(inst, args.workload)
     seed = rank_seed(1, rank)  # every rank runs its own independent replicas
@@ -335,7 +335,7 @@ def run_ours(args):
     # ---- the other phase-storage forms and the ragged batch ("batched")
     forms = {}
     if args.forms and args.workload == "torus20k" and not args.replicas and not args.sweeps:
-        for name, st in (("f16", cosm.F16), ("q16", cosm.Q16)):
+        for name, st in (("f16", cosm.F16), ("q16", cosm.Q16), ("bf16", cosm.BF16)):
             if st == storage:
                 continue
             f = measure_single(cosm, inst, col, C, prm, st, R, S, max(2, args.steps // 2), 1, seed,
@@ -389,7 +389,8 @@ def run_ours(args):
         "value": value, "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max * 1000.0, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point"}[storage],
+        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point",
+                  cosm.BF16: "bf16-storage/f32-compute"}[storage],
         "data": "synthetic (seeded instance generator; no Gset files)",
         "config": {"workload": args.workload, "description": desc, "n": inst.n, "edges": inst.m,
                    "replicas_per_gpu": R, "sweeps_per_trial": S, "colors": layout["colors"],
@@ -475,7 +476,7 @@ def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e
     _, _, S, prm, desc = WORKLOADS["batch512"]
     if args.workload == "batch512" and args.sweeps:
         S = args.sweeps
-    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage] \
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16, "bf16": cosm.BF16}[args.storage] \
         if args.workload == "batch512" else cosm.F32
     insts, reps = instances.ragged_batch(512, seed=0)
     seeds = np.arange(len(insts), dtype=np.uint64) + np.uint64(rank_seed(1, rank))
@@ -789,7 +790,7 @@ def run_serve(args):
     if rank != 0:
         return None
     _, R, S, prm, desc = WORKLOADS[args.workload]
-    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16}[args.storage]
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16, "bf16": cosm.BF16}[args.storage]
     pool = serve_pool()
     rate, window, max_trials = 50.0, args.serve_seconds, 4
     arr = instances.Stream(77, tag=10)
@@ -824,7 +825,8 @@ def run_serve(args):
         "metric": "serving: requests/s and time-to-target p50/p99 (planted instances)",
         "value": len(res) / t_total, "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1,
         "ms_per_step": t_total * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point"}[storage],
+        "dtype": {cosm.F32: "f32", cosm.F16: "f16-storage/f32-compute", cosm.Q16: "u16-fixed-point",
+                  cosm.BF16: "bf16-storage/f32-compute"}[storage],
         "data": "synthetic (seeded frustrated-loop planted instances)",
         "config": {"workload": "serve", "description": desc, "pool": [(i.n, i.m, len(i.dims)) for i in pool],
                    "requests": len(res), "arrival_rate": rate, "window_s": window,
@@ -929,7 +931,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="torus20k")
-    ap.add_argument("--storage", choices=["f32", "f16", "q16"], default="f32")
+    ap.add_argument("--storage", choices=["f32", "f16", "q16", "bf16"], default="f32")
     ap.add_argument("--replicas", type=int, default=0)
     ap.add_argument("--sweeps", type=int, default=0)
     ap.add_argument("--e2e-steps", type=int, default=1, help="0 skips the end-to-end leg")

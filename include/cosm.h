@@ -53,6 +53,8 @@ extern "C" {
 #define COSM_F16 1 /* binary16 phases (half the shared memory), FP32 arithmetic */
 #define COSM_Q16 2 /* fixed point: phases on the 2^-16-turn grid as u16,
                     * steps rounded to the grid, exact integer arithmetic   */
+#define COSM_BF16 3 /* bfloat16 phases (8 significant bits; quantum 2^-9 turn
+                     * near 1/2), FP32 arithmetic                           */
 
 /* ---- variant flags ------------------------------------------------------ */
 #define COSM_NO_DWT 1 /* no dual window twist (ablation, Table VII)         */
@@ -106,7 +108,7 @@ typedef struct cosm_graph_desc {
  *  dwt_period   sweeps between DWT events (3 or 6); 0 disables the DWT
  *  window_deg   width of each of the two DWT windows, (0, 180] (paper: 90)
  *  n_bisectors  bisectors over a semicircle at readout, 1..256 (paper: 100)
- *  storage      COSM_F32, COSM_F16 or COSM_Q16
+ *  storage      COSM_F32, COSM_F16, COSM_Q16 or COSM_BF16
  *  flags        COSM_NO_DWT | COSM_NO_SCS | COSM_DWT_RANDOM_DIR |
  *               COSM_OPT_BISECTOR
  *  track_period 0: one readout after the last sweep. T > 0: mid-anneal best

@@ -33,6 +33,7 @@ OPT_BISECTOR = 8
 STORE_F64 = 0
 STORE_F16 = 1
 STORE_Q16 = 2
+STORE_BF16 = 3
 
 
 def build(force: bool = False) -> str:
@@ -62,6 +63,7 @@ def lib():
                 "orc_wrap": (f64, [f64]),
                 "orc_sgn_b": (C.c_int, [f64, f64]),
                 "orc_round_binary16": (f64, [f64]),
+                "orc_round_bfloat16": (f64, [f64]),
                 "orc_in_window_q": (C.c_int, [f64, f64, f64]),
                 "orc_sweep": (i64, [i32, i32, P, P, P, P, P, f64, i64, i32, f64, f64, u64, i64,
                                     i32, i32, P, f64, P, i64]),
@@ -145,6 +147,10 @@ def sgn_b(xi: float, xj: float) -> int:
 
 def round_binary16(y: float) -> float:
     return lib().orc_round_binary16(y)
+
+
+def round_bfloat16(y: float) -> float:
+    return lib().orc_round_bfloat16(y)
 
 
 def in_window(x: float, th: float, W: float) -> int:

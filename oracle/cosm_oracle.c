@@ -144,6 +144,20 @@ double orc_round_binary16(double y)
     return nearbyint(y / q) * q; /* default rounding mode: to nearest, ties to even */
 }
 
+/* bfloat16 round-to-nearest-even of a value with |y| <= 1/2: 8 significant
+ * bits (7 fraction bits), the exponent range of binary32 (no subnormal
+ * quanta arise at these magnitudes above 2^-126). */
+double orc_round_bfloat16(double y)
+{
+    if (y == 0.0) return y;
+    int E;
+    frexp(y, &E);             /* |y| = f 2^E, f in [1/2, 1): binade exponent E-1 */
+    int e = E - 1;
+    if (e < -126) e = -126;
+    double q = ldexp(1.0, e - 7);
+    return nearbyint(y / q) * q;
+}
+
 /* Fixed-point phases (storage 2): phases live on the grid of 2^-16 turn
  * and every step is rounded to that grid, a step a becoming
  * floor(a 2^16 + 1/2) 2^-16; sums and differences of grid values are then
@@ -152,13 +166,15 @@ static double orc_q16_step(double a) { return floor(a * 65536.0 + 0.5) / 65536.0
 
 /* Storage rounding: 0 = none (FP64), 1 = binary16 of the phase's
  * representative in [-1/2, 1/2), 2 = fixed point (values already on the
- * grid). The result is returned in [0,1). */
+ * grid), 3 = bfloat16 of the representative. The result is returned in
+ * [0,1). */
 static double orc_store(double x, int32_t storage)
 {
-    if (storage != 1) return x;
+    if (storage != 1 && storage != 3) return x;
     double g = (x >= 0.5) ? x - 1.0 : x;
-    g = orc_round_binary16(g);
-    return (g < 0.0) ? g + 1.0 : g;
+    g = (storage == 1) ? orc_round_binary16(g) : orc_round_bfloat16(g);
+    g = (g < 0.0) ? g + 1.0 : g;
+    return g >= 1.0 ? 0.0 : g;
 }
 
 /* Dual-window membership (Section II-D, Alg. 1): two windows of width W

@@ -34,6 +34,7 @@ ERR_NOMEM = -8
 F32 = 0
 F16 = 1
 Q16 = 2
+BF16 = 3
 NO_DWT = 1
 NO_SCS = 2
 DWT_RANDOM_DIR = 4

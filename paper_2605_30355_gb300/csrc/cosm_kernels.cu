@@ -12,6 +12,7 @@
 // (g = x for x < 1/2, g = x - 1 otherwise). Every wrap is then
 // g - rint(g), which is exact in binary32; rint uses the 1.5 * 2^23 addend
 // (valid for |g| < 2^22), so the hot loop is plain FP32 adds.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <limits.h>
@@ -100,49 +101,81 @@ __device__ __forceinline__ void stk(float *p, const float (&x)[K])
         *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
     }
 }
+// Two 16-bit floats (binary16 or bfloat16) packed in a 32-bit word, to and
+// from two binary32 values (round to nearest even on the way in).
+template <typename H>
 __device__ __forceinline__ float2 h2_to_f2(uint32_t u)
 {
-    __half2 h;
-    memcpy(&h, &u, 4);
-    return __half22float2(h);
+    if constexpr (std::is_same<H, __half>::value) {
+        __half2 h;
+        memcpy(&h, &u, 4);
+        return __half22float2(h);
+    } else {
+        __nv_bfloat162 h;
+        memcpy(&h, &u, 4);
+        return __bfloat1622float2(h);
+    }
 }
+template <typename H>
 __device__ __forceinline__ uint32_t f2_to_h2(float a, float b)
 {
-    const __half2 h = __floats2half2_rn(a, b);
     uint32_t u;
-    memcpy(&u, &h, 4);
+    if constexpr (std::is_same<H, __half>::value) {
+        const __half2 h = __floats2half2_rn(a, b);
+        memcpy(&u, &h, 4);
+    } else {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+        memcpy(&u, &h, 4);
+    }
     return u;
 }
-template <int K>
-__device__ __forceinline__ void ldk(const __half *p, float (&x)[K])
+template <typename H, int K>
+__device__ __forceinline__ void ldk16(const H *p, float (&x)[K])
 {
     if constexpr (K == 2) {
-        const float2 f = h2_to_f2(*reinterpret_cast<const uint32_t *>(p));
+        const float2 f = h2_to_f2<H>(*reinterpret_cast<const uint32_t *>(p));
         x[0] = f.x; x[1] = f.y;
     } else if constexpr (K == 4) {
         const uint2 u = *reinterpret_cast<const uint2 *>(p);
-        float2 f = h2_to_f2(u.x); x[0] = f.x; x[1] = f.y;
-        f = h2_to_f2(u.y); x[2] = f.x; x[3] = f.y;
+        float2 f = h2_to_f2<H>(u.x); x[0] = f.x; x[1] = f.y;
+        f = h2_to_f2<H>(u.y); x[2] = f.x; x[3] = f.y;
     } else {
         static_assert(K == 8, "K");
         const uint4 u = *reinterpret_cast<const uint4 *>(p);
-        float2 f = h2_to_f2(u.x); x[0] = f.x; x[1] = f.y;
-        f = h2_to_f2(u.y); x[2] = f.x; x[3] = f.y;
-        f = h2_to_f2(u.z); x[4] = f.x; x[5] = f.y;
-        f = h2_to_f2(u.w); x[6] = f.x; x[7] = f.y;
+        float2 f = h2_to_f2<H>(u.x); x[0] = f.x; x[1] = f.y;
+        f = h2_to_f2<H>(u.y); x[2] = f.x; x[3] = f.y;
+        f = h2_to_f2<H>(u.z); x[4] = f.x; x[5] = f.y;
+        f = h2_to_f2<H>(u.w); x[6] = f.x; x[7] = f.y;
+    }
+}
+template <typename H, int K>
+__device__ __forceinline__ void stk16(H *p, const float (&x)[K])
+{
+    if constexpr (K == 2) {
+        *reinterpret_cast<uint32_t *>(p) = f2_to_h2<H>(x[0], x[1]);
+    } else if constexpr (K == 4) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(f2_to_h2<H>(x[0], x[1]), f2_to_h2<H>(x[2], x[3]));
+    } else {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(f2_to_h2<H>(x[0], x[1]), f2_to_h2<H>(x[2], x[3]),
+                                                   f2_to_h2<H>(x[4], x[5]), f2_to_h2<H>(x[6], x[7]));
     }
 }
 template <int K>
-__device__ __forceinline__ void stk(__half *p, const float (&x)[K])
+__device__ __forceinline__ void ldk(const __half *p, float (&x)[K]) { ldk16<__half, K>(p, x); }
+template <int K>
+__device__ __forceinline__ void stk(__half *p, const float (&x)[K]) { stk16<__half, K>(p, x); }
+template <int K>
+__device__ __forceinline__ void ldk(const __nv_bfloat16 *p, float (&x)[K]) { ldk16<__nv_bfloat16, K>(p, x); }
+template <int K>
+__device__ __forceinline__ void stk(__nv_bfloat16 *p, const float (&x)[K]) { stk16<__nv_bfloat16, K>(p, x); }
+
+// A binary32 value in a storage type (round to nearest even).
+template <typename Store>
+__device__ __forceinline__ Store to_store(float v)
 {
-    if constexpr (K == 2) {
-        *reinterpret_cast<uint32_t *>(p) = f2_to_h2(x[0], x[1]);
-    } else if constexpr (K == 4) {
-        *reinterpret_cast<uint2 *>(p) = make_uint2(f2_to_h2(x[0], x[1]), f2_to_h2(x[2], x[3]));
-    } else {
-        *reinterpret_cast<uint4 *>(p) = make_uint4(f2_to_h2(x[0], x[1]), f2_to_h2(x[2], x[3]),
-                                                   f2_to_h2(x[4], x[5]), f2_to_h2(x[6], x[7]));
-    }
+    if constexpr (std::is_same<Store, __half>::value) return __float2half_rn(v);
+    else if constexpr (std::is_same<Store, __nv_bfloat16>::value) return __float2bfloat16_rn(v);
+    else return v;
 }
 
 // COSM_Q16 phases: integers on the 2^-16-turn grid stored as u16. In
@@ -187,7 +220,7 @@ __device__ __forceinline__ void stq(uint16_t *p, const uint32_t (&x)[K])
 template <typename Store, int K>
 __device__ __forceinline__ void ld_q32(const Store *p, uint32_t (&q)[K])
 {
-    if constexpr (sizeof(Store) == 2 && !std::is_same<Store, __half>::value) {
+    if constexpr (std::is_same<Store, uint16_t>::value) {
         ldq<K>(p, q);
     } else {
         float x[K];
@@ -337,7 +370,7 @@ __device__ bool seg_begin(const InstView &v, const Segment &sg, const Tile<Store
             const uint32_t word = (ov & 2) ? hi : lo;
             if constexpr (std::is_same<Store, uint16_t>::value) t.xs[k] = (uint16_t)(word >> 16);
             else if constexpr (sizeof(Store) == 4) t.xs[k] = u24_centered(word);
-            else t.xs[k] = __float2half_rn(u24_centered(word));
+            else t.xs[k] = to_store<Store>(u24_centered(word));
         }
         // mid-anneal tracking keeps the lowest-energy readout of the trial
         if (v.track > 0 && v.energy && tid < K && rep0 + tid < (uint32_t)v.replicas)
@@ -677,15 +710,15 @@ __device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float 
     }
 }
 
-// Binary16 storage: every phase write is a binary16 store of the wrapped
-// value, also between the colours of a block, so each update there is
-// wrapped and rounded through binary16 at once.
-template <int K>
-__device__ __forceinline__ void round_f16(float (&x)[K])
+// 16-bit float storage (binary16, bfloat16): every phase write is a store of
+// the wrapped value in the storage type, also between the colours of a
+// block, so each update there is wrapped and rounded through it at once.
+template <typename H, int K>
+__device__ __forceinline__ void round_16(float (&x)[K])
 {
 #pragma unroll
     for (int r = 0; r < K; r += 2) {
-        const float2 f = __half22float2(__floats2half2_rn(x[r], x[r + 1]));
+        const float2 f = h2_to_f2<H>(f2_to_h2<H>(x[r], x[r + 1]));
         x[r] = f.x;
         x[r + 1] = f.y;
     }
@@ -701,8 +734,8 @@ __device__ __forceinline__ void pair_block(float (&x1)[K], float (&x2)[K], float
             x1[r] = wrap_c(x1[r]);
             x2[r] = wrap_c(x2[r]);
         }
-        round_f16<K>(x1);
-        round_f16<K>(x2);
+        round_16<Store, K>(x1);
+        round_16<Store, K>(x2);
     }
 }
 
@@ -1511,6 +1544,7 @@ __device__ __forceinline__ uint32_t stored_q(const void *state, int storage, siz
 {
     if (storage == 0) return phase_q(reinterpret_cast<const float *>(state)[idx]);
     if (storage == 1) return phase_q(__half2float(reinterpret_cast<const __half *>(state)[idx]));
+    if (storage == 3) return phase_q(__bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(state)[idx]));
     return (uint32_t)reinterpret_cast<const uint16_t *>(state)[idx] << 16;
 }
 
@@ -1770,6 +1804,10 @@ static int occ_one(int threads, size_t smem)
             if ((K) == 2) COSM_DISPATCH_M(__half, 2, MODE, CALL);   \
             if ((K) == 4) COSM_DISPATCH_M(__half, 4, MODE, CALL);   \
             if ((K) == 8) COSM_DISPATCH_M(__half, 8, MODE, CALL);   \
+        } else if ((STORAGE) == 3) {                                \
+            if ((K) == 2) COSM_DISPATCH_M(__nv_bfloat16, 2, MODE, CALL); \
+            if ((K) == 4) COSM_DISPATCH_M(__nv_bfloat16, 4, MODE, CALL); \
+            if ((K) == 8) COSM_DISPATCH_M(__nv_bfloat16, 8, MODE, CALL); \
         } else {                                                    \
             if ((K) == 2) COSM_DISPATCH_M(uint16_t, 2, MODE, CALL); \
             if ((K) == 4) COSM_DISPATCH_M(uint16_t, 4, MODE, CALL); \

@@ -1,5 +1,6 @@
 // Host runtime behind the C ABI of include/cosm.h: handles, device layout,
 // the work schedule of replica tiles over resident CTAs, and launches.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -54,8 +55,8 @@ static int check_params(const cosm_params *p)
         return fail(COSM_ERR_INVALID_ARG, "window_deg must be in (0, 180]");
     if (p->n_bisectors < 1 || p->n_bisectors > kMaxBisectors)
         return fail(COSM_ERR_INVALID_ARG, "n_bisectors must be in [1, 256]");
-    if (p->storage != COSM_F32 && p->storage != COSM_F16 && p->storage != COSM_Q16)
-        return fail(COSM_ERR_INVALID_ARG, "storage must be COSM_F32, COSM_F16 or COSM_Q16");
+    if (p->storage != COSM_F32 && p->storage != COSM_F16 && p->storage != COSM_Q16 && p->storage != COSM_BF16)
+        return fail(COSM_ERR_INVALID_ARG, "storage must be COSM_F32, COSM_F16, COSM_Q16 or COSM_BF16");
     if (p->flags & ~(COSM_NO_DWT | COSM_NO_SCS | COSM_DWT_RANDOM_DIR | COSM_OPT_BISECTOR))
         return fail(COSM_ERR_INVALID_ARG, "unknown flags");
     if (p->track_period < 0) return fail(COSM_ERR_INVALID_ARG, "track_period must be >= 0");
@@ -877,6 +878,10 @@ extern "C" int cosm_get_state(cosm_handle *h, double *phases)
                 float f;
                 std::memcpy(&f, raw.data() + idx * 4, 4);
                 g = f;
+            } else if (h->prm.storage == COSM_BF16) {
+                __nv_bfloat16 bv;
+                std::memcpy(&bv, raw.data() + idx * 2, 2);
+                g = (double)__bfloat162float(bv);
             } else if (h->prm.storage == COSM_F16) {
                 __half hv;
                 std::memcpy(&hv, raw.data() + idx * 2, 2);
@@ -920,6 +925,9 @@ extern "C" int cosm_set_state(cosm_handle *h, const double *phases, int32_t repl
             if (esz == 4) {
                 const float f = (float)g;
                 std::memcpy(raw.data() + idx * 4, &f, 4);
+            } else if (h->prm.storage == COSM_BF16) {
+                const __nv_bfloat16 bv = __float2bfloat16_rn((float)g);
+                std::memcpy(raw.data() + idx * 2, &bv, 2);
             } else if (h->prm.storage == COSM_F16) {
                 const __half hv = __float2half_rn((float)g);
                 std::memcpy(raw.data() + idx * 2, &hv, 2);

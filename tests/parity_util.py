@@ -16,6 +16,10 @@ import numpy as np
 TIE_EPS = 2.0 ** -20
 TOL_F32 = 1e-5
 TOL_F16 = 2e-3
+# bfloat16 storage cannot meet 2e-3 rad (its quantum is 2^-9 turn = 1.2e-2 rad
+# near 1/2); against the oracle's bfloat16-storage mode the bound is one
+# quantum (a binary32-vs-FP64 difference can move a rounding by one step)
+TOL_BF16 = 2 * math.pi * 2 ** -9 * 1.05
 
 
 def circ_rad(a, b):
@@ -39,6 +43,15 @@ def one_sweep_error(orc, g, x0, x_gpu, alpha, sweep, *, storage=0, max_enum=10, 
         xf, _ = orc.sweep(g, x0, alpha, sweep, storage=storage, force=force, **kw)
         best = min(best, float(circ_rad(xf, x_gpu).max()))
     return best, len(ties)
+
+
+def bf16_exact_turns(x):
+    """Round turns to bfloat16 in the representation [-1/2, 1/2), back to [0,1)."""
+    import torch
+    x = np.asarray(x, dtype=np.float64)
+    g = np.where(x >= 0.5, x - 1.0, x)
+    g = torch.tensor(g).to(torch.bfloat16).to(torch.float64).numpy()
+    return np.mod(np.where(g < 0, g + 1.0, g), 1.0)
 
 
 def f16_exact_turns(x):

@@ -310,6 +310,33 @@ def test_f16_storage_keeps_phases_representable(orc):
     assert _circ(x, xf).max() < 8 * 2 ** -12
 
 
+def test_bfloat16_rounding_matches_library(orc):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(4)
+    ys = np.concatenate([rng.uniform(-0.5, 0.5, 5000), rng.uniform(-1e-4, 1e-4, 2000),
+                         np.array([0.5, -0.5, 2 ** -25, 3 * 2 ** -26, 0.25 + 2 ** -10])])
+    ref = torch.tensor(ys, dtype=torch.float64).to(torch.bfloat16).to(torch.float64).numpy()
+    for y, r in zip(ys, ref):
+        assert orc.round_bfloat16(float(y)) == float(r)
+
+
+def test_bf16_storage_keeps_phases_representable(orc):
+    torch = pytest.importorskip("torch")
+    inst = instances.random_regular(300, 3, 4)
+    g = orc.coloured(inst)
+    x0 = np.array([orc.round_bfloat16(v - 1.0) + 1.0 if v >= 0.5 else orc.round_bfloat16(v)
+                   for v in orc.init_phases(inst.n, 2, 0)]) % 1.0
+    x, _ = orc.sweep(g, x0, 0.031, 3, seed=2, dwt_ratio=1.0, storage=orc.STORE_BF16)
+    gcen = np.where(x >= 0.5, x - 1.0, x)
+    back = torch.tensor(gcen).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(back, gcen)
+    # most phases stay within a few bfloat16 quanta of the FP64 sweep; a
+    # rounding can flip a sign decision near a tie and move a phase by a
+    # whole step, so this is a distribution bound
+    xf, _ = orc.sweep(g, x0, 0.031, 3, seed=2, dwt_ratio=1.0)
+    assert (_circ(x, xf) > 8 * 2 ** -9).mean() < 0.02
+
+
 # ------------------------------------------------------------------ conflict trap
 
 def test_circular_conflict_trap_gd_freezes_scs_escapes(orc):

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import instances
-from parity_util import TOL_F16, TOL_F32, circ_rad, f16_exact_turns, one_sweep_error
+from parity_util import TOL_BF16, TOL_F16, TOL_F32, bf16_exact_turns, circ_rad, f16_exact_turns, one_sweep_error
 
 pytestmark = pytest.mark.gpu
 
@@ -71,6 +71,39 @@ def test_initial_phases_f16_rounded(cosm, orc):
     x = s.get_state()
     for r in range(6):
         assert np.array_equal(x[r], f16_exact_turns(orc.init_phases(inst.n, 77, r)))
+
+
+def test_initial_phases_bf16_rounded(cosm, orc):
+    inst = instances.torus2d(16, 16, 0)
+    s, g = _solver(cosm, orc, inst, storage=3, alpha0_deg=0.0)
+    s.run(1, 6, seed=77)
+    x = s.get_state()
+    for r in range(6):
+        assert np.array_equal(x[r], bf16_exact_turns(orc.init_phases(inst.n, 77, r)))
+
+
+@pytest.mark.parametrize("dims", [True, False])
+@pytest.mark.parametrize("sweep", [2, 3, 500])
+def test_one_sweep_bf16_storage(cosm, orc, dims, sweep):
+    # bfloat16 storage: bounded by one bfloat16 quantum against the oracle's
+    # bfloat16-storage mode; against pure FP64 only reported (a distribution
+    # bound, as for binary16)
+    inst = instances.torus2d(16, 16, 1)
+    s, g = _solver(cosm, orc, inst, storage=3, use_dims=dims)
+    R = 8
+    x0 = np.stack([bf16_exact_turns(orc.init_phases(inst.n, 3, r)) for r in range(R)])
+    s.set_state(x0, seed=3)
+    alpha = float(np.float32(orc.alpha(sweep, 1000, A14)))
+    s.step(sweep, alpha)
+    x1 = s.get_state()
+    far = []
+    for r in range(R):
+        err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=3, replica=r,
+                                 storage=orc.STORE_BF16, **_params_kw(s))
+        assert err <= TOL_BF16, (r, err)
+        xf, _ = orc.sweep(g, x0[r], alpha, sweep, seed=3, replica=r, **_params_kw(s))
+        far.append(float((circ_rad(xf, x1[r]) > 8 * 2 * np.pi * 2 ** -9).mean()))
+    assert np.mean(far) < 0.05
 
 
 @pytest.mark.parametrize("name,make,dims", CASES, ids=[c[0] for c in CASES])
@@ -182,7 +215,7 @@ def test_readout_bit_exact_on_replayed_state(cosm, orc, name, make, dims):
     assert orc.cut(inst.src, inst.dst, inst.w, spins) == cut
 
 
-@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("storage", [0, 1, 3])
 def test_full_trial_cuts_bit_exact_on_final_state(cosm, orc, storage):
     inst = instances.torus2d(16, 16, 0)
     s, g = _solver(cosm, orc, inst, storage=storage)
@@ -390,3 +423,20 @@ def test_edge_order_within_colours_changes_nothing(cosm, orc, storage):
     b.run(200, 6, 9)
     assert np.array_equal(a.get_state(), b.get_state())
     assert np.array_equal(a.replica_cuts()[0], b.replica_cuts()[0])
+
+
+def test_quality_at_ten_thousand_spins(cosm, orc):
+    # the unfrustrated gauge-planted 100 x 100 torus reaches its known
+    # optimum; the +-J 100 x 100 glass reaches a ground-energy density near
+    # the paper's -1.40 for its toroidal glasses (Section III-A)
+    inst = instances.gauge_planted(instances.torus2d(100, 100, 5), 6)
+    s = cosm.Solver.from_instance(inst, alpha0_deg=25.0, dwt_ratio=1.0)
+    s.run(10000, 256, 3)
+    cut, energy, rep, spins = s.best()
+    assert (cut, energy) == (inst.meta["opt_cut"], inst.meta["ground_energy"])
+    glass = instances.torus2d(100, 100, 0)
+    s = cosm.Solver.from_instance(glass)
+    s.run(20000, 1024, 4)
+    cut, energy, rep, spins = s.best()
+    assert energy / glass.n < -1.395
+    assert orc.energy(glass.src, glass.dst, glass.w, spins) == energy
