@@ -970,18 +970,43 @@ __device__ __forceinline__ void dwt_x2(f32x2 &x, f32x2 c1, f32x2 c2, f32x2 st2)
     x = p_add(x, add);
 }
 
+// Shared-memory loads and stores of a slot's K/2 replica pairs at a 32-bit
+// shared address (per-thread addresses advance by adds; no 64-bit index math).
+template <int K>
+__device__ __forceinline__ void lds_p(uint32_t a, f32x2 (&x)[K / 2])
+{
+    if constexpr (K == 2) {
+        asm volatile("ld.shared.b64 %0, [%1];" : "=l"(x[0]) : "r"(a) : "memory");
+    } else {
+        static_assert(K == 4, "K");
+        asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(x[0]), "=l"(x[1]) : "r"(a) : "memory");
+    }
+}
+template <int K>
+__device__ __forceinline__ void sts_p(uint32_t a, const f32x2 (&x)[K / 2])
+{
+    if constexpr (K == 2) {
+        asm volatile("st.shared.b64 [%0], %1;" ::"r"(a), "l"(x[0]) : "memory");
+    } else {
+        asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(x[0]), "l"(x[1]) : "memory");
+    }
+}
+
 template <int K>
 __device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wnib, float alpha, int Q)
 {
+    constexpr uint32_t E = K * 4;  // bytes per slot
     const f32x2 a2 = p_splat(alpha), n2 = a2 ^ kSign2;
+    const uint32_t qb = (uint32_t)Q * E, qb2 = 2 * qb, qb3 = 3 * qb, step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + threadIdx.x * E;
 #pragma unroll 2
-    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
         const uint32_t wb = __ldg(wnib + f);
         f32x2 xa[K / 2], xb[K / 2], xc[K / 2], xd[K / 2];
-        ldp<K>(xs + (size_t)f * K, xa);
-        ldp<K>(xs + (size_t)(Q + f) * K, xb);
-        ldp<K>(xs + (size_t)(2 * Q + f) * K, xc);
-        ldp<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        lds_p<K>(ad, xa);
+        lds_p<K>(ad + qb, xb);
+        lds_p<K>(ad + qb2, xc);
+        lds_p<K>(ad + qb3, xd);
         const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
         const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
 #pragma unroll
@@ -991,10 +1016,10 @@ __device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wni
             pair_x2(xa[h], xc[h], w2, kTwo2);
             pair_x2(xb[h], xd[h], w3, kTwo2);
         }
-        stp<K>(xs + (size_t)f * K, xa);
-        stp<K>(xs + (size_t)(Q + f) * K, xb);
-        stp<K>(xs + (size_t)(2 * Q + f) * K, xc);
-        stp<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        sts_p<K>(ad, xa);
+        sts_p<K>(ad + qb, xb);
+        sts_p<K>(ad + qb2, xc);
+        sts_p<K>(ad + qb3, xd);
     }
 }
 
@@ -1003,6 +1028,7 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
                                                   int m0, int dm, bool dwt, const float *thc, const float *thc2,
                                                   const float *stp_)
 {
+    constexpr uint32_t E = K * 4;  // bytes per slot
     const f32x2 a2 = p_splat(alpha), n2 = a2 ^ kSign2;
     f32x2 th2[K / 2], tk2[K / 2], st2[K / 2];
 #pragma unroll
@@ -1011,30 +1037,37 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
         tk2[h] = dwt ? (((f32x2)__float_as_uint(thc2[2 * h + 1]) << 32) | __float_as_uint(thc2[2 * h])) : 0ull;
         st2[h] = dwt ? (((f32x2)__float_as_uint(stp_[2 * h + 1]) << 32) | __float_as_uint(stp_[2 * h])) : 0ull;
     }
+    // byte offsets from D[f] (sublattice D at 3Q) to C[g], B[h], A[gh] with
+    // g = f + goff (next column) and h = f + hoff (next row)
+    const uint32_t qb = (uint32_t)Q * E;
+    const uint32_t wdb = (uint32_t)Wd * E;
+    const uint32_t rowwrap = (uint32_t)(Wd - Q) * E;  // hoff at the last row, mod 2^32
+    const uint32_t step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + 3 * qb + threadIdx.x * E;
     int m = m0;  // column of block f within its row
     const bool cw0 = (m0 == Wd - 1);
-    const int goff0 = cw0 ? 1 - Wd : 1;
+    const uint32_t goffb0 = cw0 ? (uint32_t)(1 - Wd) * E : E;
 #pragma unroll 2
-    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
-        int goff = goff0;
+    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
+        uint32_t goffb = goffb0;
         bool cw = cw0;
         if (!kFixedColumn) {
             cw = (m == Wd - 1);  // next column wraps to column 0
-            goff = cw ? 1 - Wd : 1;
+            goffb = cw ? (uint32_t)(1 - Wd) * E : E;
             m += dm;
             if (m >= Wd) m -= Wd;
         }
         const bool rw = (f >= Q - Wd);      // next row wraps to row 0
-        const int hoff = rw ? Wd - Q : Wd;
-        const int g = f + goff, hh = f + hoff, gh = g + hoff;
+        const uint32_t hoffb = rw ? rowwrap : wdb;
+        const uint32_t aC = ad - qb + goffb, aB = ad - 2 * qb + hoffb, aA = ad - 3 * qb + goffb + hoffb;
         // wrap edges: the other orientation (c = -2, negated step)
         const f32x2 tzc = cw ? kMinusTwo2 : kTwo2, tzr = rw ? kMinusTwo2 : kTwo2;
         const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u) ^ (rw ? 12u : 0u);
         f32x2 xd[K / 2], xc[K / 2], xb[K / 2], xa[K / 2];
-        ldp<K>(xs + (size_t)(3 * Q + f) * K, xd);
-        ldp<K>(xs + (size_t)(2 * Q + g) * K, xc);
-        ldp<K>(xs + (size_t)(Q + hh) * K, xb);
-        ldp<K>(xs + (size_t)gh * K, xa);
+        lds_p<K>(ad, xd);
+        lds_p<K>(aC, xc);
+        lds_p<K>(aB, xb);
+        lds_p<K>(aA, xa);
         const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
         const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
 #pragma unroll
@@ -1055,10 +1088,10 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
             xc[h] = p_wrap(xc[h]);
             xd[h] = p_wrap(xd[h]);
         }
-        stp<K>(xs + (size_t)(3 * Q + f) * K, xd);
-        stp<K>(xs + (size_t)(2 * Q + g) * K, xc);
-        stp<K>(xs + (size_t)(Q + hh) * K, xb);
-        stp<K>(xs + (size_t)gh * K, xa);
+        sts_p<K>(ad, xd);
+        sts_p<K>(aC, xc);
+        sts_p<K>(aB, xb);
+        sts_p<K>(aA, xa);
     }
 }
 
