@@ -1160,24 +1160,66 @@ __device__ __forceinline__ uint32_t signed_q(uint32_t wb, uint32_t bit, uint32_t
     return (wb & bit) ? 0u - ap : ap;
 }
 
+// Fixed-point phases at a 32-bit shared address (two u16 phases per word).
+template <int K>
+__device__ __forceinline__ void lds_q(uint32_t a, uint32_t (&x)[K])
+{
+    if constexpr (K == 2) {
+        uint32_t w;
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w) : "r"(a) : "memory");
+        x[0] = w << 16; x[1] = w & 0xFFFF0000u;
+    } else if constexpr (K == 4) {
+        uint32_t w0, w1;
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(a) : "memory");
+        x[0] = w0 << 16; x[1] = w0 & 0xFFFF0000u;
+        x[2] = w1 << 16; x[3] = w1 & 0xFFFF0000u;
+    } else {
+        static_assert(K == 8, "K");
+        uint32_t w[4];
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(a) : "memory");
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            x[2 * i] = w[i] << 16;
+            x[2 * i + 1] = w[i] & 0xFFFF0000u;
+        }
+    }
+}
+template <int K>
+__device__ __forceinline__ void sts_q(uint32_t a, const uint32_t (&x)[K])
+{
+    if constexpr (K == 2) {
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(pack_q(x[0], x[1])) : "memory");
+    } else if constexpr (K == 4) {
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(pack_q(x[0], x[1])),
+                     "r"(pack_q(x[2], x[3])) : "memory");
+    } else {
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(pack_q(x[0], x[1])),
+                     "r"(pack_q(x[2], x[3])), "r"(pack_q(x[4], x[5])), "r"(pack_q(x[6], x[7])) : "memory");
+    }
+}
+
 template <int K>
 __device__ __forceinline__ void block_pass_even_q(uint16_t *xs, const uint8_t *wnib, uint32_t ap, int Q)
 {
-    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+    constexpr uint32_t E = K * 2;  // bytes per slot
+    const uint32_t qb = (uint32_t)Q * E, qb2 = 2 * qb, qb3 = 3 * qb, step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + threadIdx.x * E;
+    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
         const uint32_t wb = __ldg(wnib + f);
         uint32_t xa[K], xb[K], xc[K], xd[K];
-        ldq<K>(xs + (size_t)f * K, xa);
-        ldq<K>(xs + (size_t)(Q + f) * K, xb);
-        ldq<K>(xs + (size_t)(2 * Q + f) * K, xc);
-        ldq<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        lds_q<K>(ad, xa);
+        lds_q<K>(ad + qb, xb);
+        lds_q<K>(ad + qb2, xc);
+        lds_q<K>(ad + qb3, xd);
         pair_q<K>(xa, xb, signed_q(wb, 1u, ap));
         pair_q<K>(xc, xd, signed_q(wb, 2u, ap));
         pair_q<K>(xa, xc, signed_q(wb, 4u, ap));
         pair_q<K>(xb, xd, signed_q(wb, 8u, ap));
-        stq<K>(xs + (size_t)f * K, xa);
-        stq<K>(xs + (size_t)(Q + f) * K, xb);
-        stq<K>(xs + (size_t)(2 * Q + f) * K, xc);
-        stq<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        sts_q<K>(ad, xa);
+        sts_q<K>(ad + qb, xb);
+        sts_q<K>(ad + qb2, xc);
+        sts_q<K>(ad + qb3, xd);
     }
 }
 
@@ -1191,28 +1233,40 @@ __device__ __forceinline__ void pair_q_oriented(uint32_t (&x1)[K], uint32_t (&x2
     else pair_q<K>(x1, x2, ap);
 }
 
-template <int K>
+template <int K, bool kFixedColumn>
 __device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wnib, uint32_t ap, int Q, int Wd,
                                                  int m0, int dm, bool dwt, const uint32_t *c, uint32_t qw,
                                                  const uint32_t *sqs)
 {
+    constexpr uint32_t E = K * 2;  // bytes per slot
     uint32_t sq[K];  // the twist step of each replica
 #pragma unroll
     for (int r = 0; r < K; ++r) sq[r] = dwt ? sqs[r] : 0u;
+    // byte offsets from D[f] to C[g], B[h], A[gh] (g: next column, h: next row)
+    const uint32_t qb = (uint32_t)Q * E, wdb = (uint32_t)Wd * E, rowwrap = (uint32_t)(Wd - Q) * E;
+    const uint32_t step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + 3 * qb + threadIdx.x * E;
     int m = m0;
-    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
-        const bool cw = (m == Wd - 1);
-        m += dm;
-        if (m >= Wd) m -= Wd;
+    const bool cw0 = (m0 == Wd - 1);
+    const uint32_t goffb0 = cw0 ? (uint32_t)(1 - Wd) * E : E;
+    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
+        uint32_t goffb = goffb0;
+        bool cw = cw0;
+        if (!kFixedColumn) {
+            cw = (m == Wd - 1);
+            goffb = cw ? (uint32_t)(1 - Wd) * E : E;
+            m += dm;
+            if (m >= Wd) m -= Wd;
+        }
         const bool rw = (f >= Q - Wd);
-        const int hoff = rw ? Wd - Q : Wd;
-        const int g = f + (cw ? 1 - Wd : 1), h = f + hoff, gh = g + hoff;
+        const uint32_t hoffb = rw ? rowwrap : wdb;
+        const uint32_t aC = ad - qb + goffb, aB = ad - 2 * qb + hoffb, aA = ad - 3 * qb + goffb + hoffb;
         const uint32_t wb = __ldg(wnib + Q + f);
         uint32_t xd[K], xc[K], xb[K], xa[K];
-        ldq<K>(xs + (size_t)(3 * Q + f) * K, xd);
-        ldq<K>(xs + (size_t)(2 * Q + g) * K, xc);
-        ldq<K>(xs + (size_t)(Q + h) * K, xb);
-        ldq<K>(xs + (size_t)gh * K, xa);
+        lds_q<K>(ad, xd);
+        lds_q<K>(aC, xc);
+        lds_q<K>(aB, xb);
+        lds_q<K>(aA, xa);
         pair_q_oriented<K>(xd, xc, signed_q(wb, 1u, ap), cw);
         pair_q_oriented<K>(xb, xa, signed_q(wb, 2u, ap), cw);
         pair_q_oriented<K>(xd, xb, signed_q(wb, 4u, ap), rw);
@@ -1223,10 +1277,10 @@ __device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wn
             dwt_q<K>(xb, c, qw, sq);
             dwt_q<K>(xa, c, qw, sq);
         }
-        stq<K>(xs + (size_t)(3 * Q + f) * K, xd);
-        stq<K>(xs + (size_t)(2 * Q + g) * K, xc);
-        stq<K>(xs + (size_t)(Q + h) * K, xb);
-        stq<K>(xs + (size_t)gh * K, xa);
+        sts_q<K>(ad, xd);
+        sts_q<K>(aC, xc);
+        sts_q<K>(aB, xb);
+        sts_q<K>(aA, xa);
     }
 }
 
@@ -1311,7 +1365,10 @@ __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment
         if (kMode == MODE_LATTICE2D) {
             block_pass_even_q<K>(t.xs, v.wnib, aq << 16, v.Q);
             __syncthreads();
-            block_pass_odd_q<K>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
+            if (dm == 0)
+                block_pass_odd_q<K, true>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
+            else
+                block_pass_odd_q<K, false>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
             __syncthreads();
         } else {
             if (kMode == MODE_GENERAL) {
