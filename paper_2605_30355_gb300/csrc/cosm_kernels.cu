@@ -770,27 +770,88 @@ __device__ __forceinline__ float signed_alpha(uint32_t wb, uint32_t bit, float a
     return (wb & bit) ? -alpha : alpha;
 }
 
+// 1, 2 or 4 words at a 32-bit shared address.
+template <int NW>
+__device__ __forceinline__ void ld_words(uint32_t a, uint32_t (&w)[NW])
+{
+    if constexpr (NW == 1) {
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w[0]) : "r"(a) : "memory");
+    } else if constexpr (NW == 2) {
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w[0]), "=r"(w[1]) : "r"(a) : "memory");
+    } else {
+        static_assert(NW == 4, "NW");
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(a) : "memory");
+    }
+}
+template <int NW>
+__device__ __forceinline__ void st_words(uint32_t a, const uint32_t (&w)[NW])
+{
+    if constexpr (NW == 1) {
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(w[0]) : "memory");
+    } else if constexpr (NW == 2) {
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(w[0]), "r"(w[1]) : "memory");
+    } else {
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(w[0]), "r"(w[1]), "r"(w[2]),
+                     "r"(w[3]) : "memory");
+    }
+}
+// A slot's K phases in the storage type at a 32-bit shared address, as
+// binary32 (ldk / stk by address).
+template <typename Store, int K>
+__device__ __forceinline__ void lds_k(uint32_t a, float (&x)[K])
+{
+    constexpr int NW = (int)(sizeof(Store) * K / 4);
+    uint32_t w[NW];
+    ld_words<NW>(a, w);
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        if constexpr (sizeof(Store) == 4) {
+            x[i] = __uint_as_float(w[i]);
+        } else {
+            const float2 f = h2_to_f2<Store>(w[i]);
+            x[2 * i] = f.x;
+            x[2 * i + 1] = f.y;
+        }
+    }
+}
+template <typename Store, int K>
+__device__ __forceinline__ void sts_k(uint32_t a, const float (&x)[K])
+{
+    constexpr int NW = (int)(sizeof(Store) * K / 4);
+    uint32_t w[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) {
+        if constexpr (sizeof(Store) == 4) w[i] = __float_as_uint(x[i]);
+        else w[i] = f2_to_h2<Store>(x[2 * i], x[2 * i + 1]);
+    }
+    st_words<NW>(a, w);
+}
+
 template <typename Store, int K>
 __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, float alpha, int Q)
 {
+    constexpr uint32_t E = sizeof(Store) * K;  // bytes per slot
+    const uint32_t qb = (uint32_t)Q * E, qb2 = 2 * qb, qb3 = 3 * qb, step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + threadIdx.x * E;
 #pragma unroll 2
-    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
+    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
         const uint32_t wb = __ldg(wnib + f);
         float xa[K], xb[K], xc[K], xd[K];
-        ldk<K>(xs + (size_t)f * K, xa);
-        ldk<K>(xs + (size_t)(Q + f) * K, xb);
-        ldk<K>(xs + (size_t)(2 * Q + f) * K, xc);
-        ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        lds_k<Store, K>(ad, xa);
+        lds_k<Store, K>(ad + qb, xb);
+        lds_k<Store, K>(ad + qb2, xc);
+        lds_k<Store, K>(ad + qb3, xd);
         // colour 0: A-B, C-D; colour 1: A-C, B-D (first slot = smaller id)
         pair_block<Store, K>(xa, xb, signed_alpha(wb, 1u, alpha), 2.0f);
         pair_block<Store, K>(xc, xd, signed_alpha(wb, 2u, alpha), 2.0f);
         pair_block<Store, K>(xa, xc, signed_alpha(wb, 4u, alpha), 2.0f);
         pair_block<Store, K>(xb, xd, signed_alpha(wb, 8u, alpha), 2.0f);
         // binary32 phases stay unwrapped until the odd pass of this sweep
-        stk<K>(xs + (size_t)f * K, xa);
-        stk<K>(xs + (size_t)(Q + f) * K, xb);
-        stk<K>(xs + (size_t)(2 * Q + f) * K, xc);
-        stk<K>(xs + (size_t)(3 * Q + f) * K, xd);
+        sts_k<Store, K>(ad, xa);
+        sts_k<Store, K>(ad + qb, xb);
+        sts_k<Store, K>(ad + qb2, xc);
+        sts_k<Store, K>(ad + qb3, xd);
     }
 }
 
@@ -804,30 +865,35 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
     float st[K];  // the twist step of each replica
 #pragma unroll
     for (int r = 0; r < K; ++r) st[r] = dwt ? stp[r] : 0.0f;
+    // byte offsets from D[f] to C[g], B[h], A[gh] (g: next column, h: next row)
+    constexpr uint32_t E = sizeof(Store) * K;  // bytes per slot
+    const uint32_t qb = (uint32_t)Q * E, wdb = (uint32_t)Wd * E, rowwrap = (uint32_t)(Wd - Q) * E;
+    const uint32_t step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + 3 * qb + threadIdx.x * E;
     int m = m0;  // column of block f within its row
     const bool cw0 = (m0 == Wd - 1);
-    const int goff0 = cw0 ? 1 - Wd : 1;
+    const uint32_t goffb0 = cw0 ? (uint32_t)(1 - Wd) * E : E;
 #pragma unroll 2
-    for (int f = threadIdx.x; f < Q; f += blockDim.x) {
-        int goff = goff0;
+    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
+        uint32_t goffb = goffb0;
         bool cw = cw0;
         if (!kFixedColumn) {
             cw = (m == Wd - 1);  // next column wraps to column 0
-            goff = cw ? 1 - Wd : 1;
+            goffb = cw ? (uint32_t)(1 - Wd) * E : E;
             m += dm;
             if (m >= Wd) m -= Wd;
         }
         const bool rw = (f >= Q - Wd);      // next row wraps to row 0
-        const int hoff = rw ? Wd - Q : Wd;
-        const int g = f + goff, h = f + hoff, gh = g + hoff;
+        const uint32_t hoffb = rw ? rowwrap : wdb;
+        const uint32_t aC = ad - qb + goffb, aB = ad - 2 * qb + hoffb, aA = ad - 3 * qb + goffb + hoffb;
         // wrap edges: the other orientation (c = -2, negated step)
         const float tzc = cw ? -2.0f : 2.0f, tzr = rw ? -2.0f : 2.0f;
         const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u) ^ (rw ? 12u : 0u);
         float xd[K], xc[K], xb[K], xa[K];
-        ldk<K>(xs + (size_t)(3 * Q + f) * K, xd);
-        ldk<K>(xs + (size_t)(2 * Q + g) * K, xc);
-        ldk<K>(xs + (size_t)(Q + h) * K, xb);
-        ldk<K>(xs + (size_t)gh * K, xa);
+        lds_k<Store, K>(ad, xd);
+        lds_k<Store, K>(aC, xc);
+        lds_k<Store, K>(aB, xb);
+        lds_k<Store, K>(aA, xa);
         // colour 2: D-C, B-A (horizontal from odd columns)
         pair_block<Store, K>(xd, xc, signed_alpha(wb, 1u, alpha), tzc);
         pair_block<Store, K>(xb, xa, signed_alpha(wb, 2u, alpha), tzc);
@@ -850,10 +916,10 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
             }
         }
         wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
-        stk<K>(xs + (size_t)(3 * Q + f) * K, xd);
-        stk<K>(xs + (size_t)(2 * Q + g) * K, xc);
-        stk<K>(xs + (size_t)(Q + h) * K, xb);
-        stk<K>(xs + (size_t)gh * K, xa);
+        sts_k<Store, K>(ad, xd);
+        sts_k<Store, K>(aC, xc);
+        sts_k<Store, K>(aB, xb);
+        sts_k<Store, K>(aA, xa);
     }
 }
 
