@@ -72,6 +72,7 @@ struct InstView {
     uint32_t *bits;       // [replicas][words] spins of the kept readout (slot order)
     int32_t words;        // (n + 31) / 32
     int32_t paired;       // binary32 lattice tiles: packed f32x2 passes (else scalar)
+    int32_t wrap_p;       // binary32 lattice phases: wrapped on sweeps s with s % wrap_p == 0
 };
 
 // Single-instance launch: the instance plus the CTAs' segment lists.
@@ -102,6 +103,12 @@ struct BatchArgs {
 };
 
 enum KernelMode { MODE_GENERAL_ = 0, MODE_ACCUM_ = 1, MODE_LATTICE2D_ = 2 };
+
+// Sweeps between wraps of binary32 lattice phases (InstView::wrap_p): the
+// largest P <= 4 for which P sweeps of steps (four +-alpha0 edges per vertex
+// and sweep, plus the twist step on the DWT sweeps among them) keep a phase
+// wrapped to [-1/2, 1/2] inside |g| < 1; 1 for other modes and storages.
+int32_t lattice_wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, int flags, int mode, int storage);
 
 struct LaunchCfg {
     int mode;      // KernelMode

@@ -695,9 +695,10 @@ __device__ __forceinline__ void general_colours_pf(const InstView &a, Store *xs,
 //     x_i = x2:  the step on x1 is -alpha w iff floor(-2d) is even
 // so a wrap edge passes c = -2 and aw = -alpha w, an ordinary one c = 2 and
 // aw = alpha w, and both follow the oracle's biased sign exactly, ties
-// included. Phases are wrapped once per sweep, at the end of the odd pass:
-// in between a phase moves by a few steps, so |g| < 1 and binary32 keeps an
-// ulp of at most 2^-24 turn.
+// included. Binary32 phases are wrapped to [-1/2, 1/2] at the end of the odd
+// pass of every wrap_p-th sweep (every sweep for 16-bit storage): the host
+// picks wrap_p so that the steps taken in between keep |g| < 1, where
+// binary32 keeps an ulp of at most 2^-24 turn.
 template <int K>
 __device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float aw, float c)
 {
@@ -847,7 +848,7 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
         pair_block<Store, K>(xc, xd, signed_alpha(wb, 2u, alpha), 2.0f);
         pair_block<Store, K>(xa, xc, signed_alpha(wb, 4u, alpha), 2.0f);
         pair_block<Store, K>(xb, xd, signed_alpha(wb, 8u, alpha), 2.0f);
-        // binary32 phases stay unwrapped until the odd pass of this sweep
+        // binary32 phases stay unwrapped until the next wrapping odd pass
         sts_k<Store, K>(ad, xa);
         sts_k<Store, K>(ad + qb, xb);
         sts_k<Store, K>(ad + qb2, xc);
@@ -857,7 +858,7 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
 
 // kFixedColumn: the thread count is a multiple of Wd, so every block a
 // thread visits sits in the same column and the column wrap is fixed.
-template <typename Store, int K, bool kFixedColumn>
+template <typename Store, int K, bool kFixedColumn, bool kWrap>
 __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
                                                int m0, int dm, bool dwt, const float *thc, const float *thc2,
                                                const float *stp)
@@ -915,7 +916,9 @@ __device__ __forceinline__ void block_pass_odd(Store *xs, const uint8_t *wnib, f
                 dwt_apply<K>(xa, thc, thc2, st);
             }
         }
-        wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
+        if constexpr (kWrap || sizeof(Store) == 2) {
+            wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
+        }
         sts_k<Store, K>(ad, xd);
         sts_k<Store, K>(aC, xc);
         sts_k<Store, K>(aB, xb);
@@ -978,7 +981,8 @@ __device__ __forceinline__ uint32_t flip_if_odd(uint32_t aw, uint32_t t)
 
 // Pair update of eq. (6) as pair_fast, for two replicas: t = 1.5 * 2^23 +
 // floor(c d) per lane (one fma rounded toward -inf), and the step on x1 is
-// aw, negated where floor(c d) is odd.
+// aw (the bits of alpha w, shared by both lanes), negated where floor(c d)
+// is odd.
 __device__ __forceinline__ void pair_x2(f32x2 &x1, f32x2 &x2, f32x2 aw2, f32x2 c2)
 {
     const f32x2 d = p_sub(x1, x2);
@@ -1013,8 +1017,9 @@ __device__ __forceinline__ void stp(float *p, const f32x2 (&x)[K / 2])
 
 // The dual window twist of dwt_nowrap for two replicas: the floors of
 // y1 = 2x + c and y2 = 2x + c - 2W per lane (fma, then an add rounded toward
-// -inf into the binade of 1.5 * 2^23); their difference (1 inside, 0
-// outside) scales the lane's step, and an outside lane adds +0 (exact).
+// -inf into the binade of 1.5 * 2^23); their difference, exact in binary32
+// (1 inside, 0 outside), scales the lane's step in one fma: x + st rounded
+// once inside, x + 0 outside.
 __device__ __forceinline__ f32x2 p_add_rd(f32x2 a, f32x2 b)
 {
     f32x2 d;
@@ -1022,18 +1027,11 @@ __device__ __forceinline__ f32x2 p_add_rd(f32x2 a, f32x2 b)
     return d;
 }
 
-__device__ __forceinline__ uint32_t times_diff(uint32_t st, uint32_t k1, uint32_t k2)
-{
-    return (k1 - k2) * st;
-}
-
 __device__ __forceinline__ void dwt_x2(f32x2 &x, f32x2 c1, f32x2 c2, f32x2 st2)
 {
     const f32x2 k1 = p_add_rd(p_fma(kTwo2, x, c1), kMagic2);
     const f32x2 k2 = p_add_rd(p_fma(kTwo2, x, c2), kMagic2);
-    const f32x2 add = ((f32x2)times_diff((uint32_t)(st2 >> 32), (uint32_t)(k1 >> 32), (uint32_t)(k2 >> 32)) << 32) |
-                      times_diff((uint32_t)st2, (uint32_t)k1, (uint32_t)k2);
-    x = p_add(x, add);
+    x = p_fma(p_sub(k1, k2), st2, x);
 }
 
 // Shared-memory loads and stores of a slot's K/2 replica pairs at a 32-bit
@@ -1062,7 +1060,7 @@ template <int K>
 __device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wnib, float alpha, int Q)
 {
     constexpr uint32_t E = K * 4;  // bytes per slot
-    const f32x2 a2 = p_splat(alpha), n2 = a2 ^ kSign2;
+    const uint32_t a1 = __float_as_uint(alpha), n1 = a1 ^ 0x80000000u;
     const uint32_t qb = (uint32_t)Q * E, qb2 = 2 * qb, qb3 = 3 * qb, step = blockDim.x * E;
     uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + threadIdx.x * E;
 #pragma unroll 2
@@ -1073,6 +1071,7 @@ __device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wni
         lds_p<K>(ad + qb, xb);
         lds_p<K>(ad + qb2, xc);
         lds_p<K>(ad + qb3, xd);
+        const f32x2 a2 = ((f32x2)a1 << 32) | a1, n2 = ((f32x2)n1 << 32) | n1;
         const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
         const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
 #pragma unroll
@@ -1089,19 +1088,67 @@ __device__ __forceinline__ void block_pass_even_x2(float *xs, const uint8_t *wni
     }
 }
 
-template <int K, bool kFixedColumn>
+// One shifted block {D[f], C[g], B[h], A[gh]} of the odd pass for two or four
+// replicas; kRowWrap: f sits in the last block row, so h wraps to row 0;
+// kDwt: the twist follows the colours; kWrap: the phases are wrapped to
+// [-1/2, 1/2] before the store.
+template <int K, bool kRowWrap, bool kDwt, bool kWrap>
+__device__ __forceinline__ void odd_block_x2(uint32_t ad, uint32_t oC, uint32_t oB, uint32_t oA, uint32_t wb,
+                                             uint32_t a1, f32x2 tzc, const f32x2 (&th2)[K / 2],
+                                             const f32x2 (&tk2)[K / 2], const f32x2 (&st2)[K / 2])
+{
+    // wrap edges: the other orientation (c = -2, negated step)
+    constexpr f32x2 tzr = kRowWrap ? kMinusTwo2 : kTwo2;
+    const uint32_t n1 = a1 ^ 0x80000000u;
+    f32x2 xd[K / 2], xc[K / 2], xb[K / 2], xa[K / 2];
+    lds_p<K>(ad, xd);
+    lds_p<K>(ad + oC, xc);
+    lds_p<K>(ad + oB, xb);
+    lds_p<K>(ad + oA, xa);
+    const f32x2 a2 = ((f32x2)a1 << 32) | a1, n2 = ((f32x2)n1 << 32) | n1;
+    const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
+    const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
+#pragma unroll
+    for (int h = 0; h < K / 2; ++h) {
+        // colour 2: D-C, B-A; colour 3: D-B, C-A
+        pair_x2(xd[h], xc[h], w0, tzc);
+        pair_x2(xb[h], xa[h], w1, tzc);
+        pair_x2(xd[h], xb[h], w2, tzr);
+        pair_x2(xc[h], xa[h], w3, tzr);
+        if constexpr (kDwt) {
+            dwt_x2(xd[h], th2[h], tk2[h], st2[h]);
+            dwt_x2(xc[h], th2[h], tk2[h], st2[h]);
+            dwt_x2(xb[h], th2[h], tk2[h], st2[h]);
+            dwt_x2(xa[h], th2[h], tk2[h], st2[h]);
+        }
+        if constexpr (kWrap) {
+            xa[h] = p_wrap(xa[h]);
+            xb[h] = p_wrap(xb[h]);
+            xc[h] = p_wrap(xc[h]);
+            xd[h] = p_wrap(xd[h]);
+        }
+    }
+    sts_p<K>(ad, xd);
+    sts_p<K>(ad + oC, xc);
+    sts_p<K>(ad + oB, xb);
+    sts_p<K>(ad + oA, xa);
+}
+
+// The odd pass: blocks above the last block row first (fixed offsets to the
+// next row), then the last row, whose next row wraps to row 0.
+template <int K, bool kFixedColumn, bool kDwt, bool kWrap>
 __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
-                                                  int m0, int dm, bool dwt, const float *thc, const float *thc2,
+                                                  int m0, int dm, const float *thc, const float *thc2,
                                                   const float *stp_)
 {
     constexpr uint32_t E = K * 4;  // bytes per slot
-    const f32x2 a2 = p_splat(alpha), n2 = a2 ^ kSign2;
+    const uint32_t a1 = __float_as_uint(alpha);
     f32x2 th2[K / 2], tk2[K / 2], st2[K / 2];
 #pragma unroll
     for (int h = 0; h < K / 2; ++h) {
-        th2[h] = dwt ? (((f32x2)__float_as_uint(thc[2 * h + 1]) << 32) | __float_as_uint(thc[2 * h])) : 0ull;
-        tk2[h] = dwt ? (((f32x2)__float_as_uint(thc2[2 * h + 1]) << 32) | __float_as_uint(thc2[2 * h])) : 0ull;
-        st2[h] = dwt ? (((f32x2)__float_as_uint(stp_[2 * h + 1]) << 32) | __float_as_uint(stp_[2 * h])) : 0ull;
+        th2[h] = kDwt ? (((f32x2)__float_as_uint(thc[2 * h + 1]) << 32) | __float_as_uint(thc[2 * h])) : 0ull;
+        tk2[h] = kDwt ? (((f32x2)__float_as_uint(thc2[2 * h + 1]) << 32) | __float_as_uint(thc2[2 * h])) : 0ull;
+        st2[h] = kDwt ? (((f32x2)__float_as_uint(stp_[2 * h + 1]) << 32) | __float_as_uint(stp_[2 * h])) : 0ull;
     }
     // byte offsets from D[f] (sublattice D at 3Q) to C[g], B[h], A[gh] with
     // g = f + goff (next column) and h = f + hoff (next row)
@@ -1111,53 +1158,46 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
     const uint32_t step = blockDim.x * E;
     uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + 3 * qb + threadIdx.x * E;
     int m = m0;  // column of block f within its row
-    const bool cw0 = (m0 == Wd - 1);
-    const uint32_t goffb0 = cw0 ? (uint32_t)(1 - Wd) * E : E;
+    bool cw = (m0 == Wd - 1);  // next column wraps to column 0
+    uint32_t goffb = cw ? (uint32_t)(1 - Wd) * E : E;
+    const int qlast = Q - Wd;  // first block of the last row
+    int f = threadIdx.x;
 #pragma unroll 2
-    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
-        uint32_t goffb = goffb0;
-        bool cw = cw0;
+    for (; f < qlast; f += blockDim.x, ad += step) {
         if (!kFixedColumn) {
-            cw = (m == Wd - 1);  // next column wraps to column 0
+            cw = (m == Wd - 1);
             goffb = cw ? (uint32_t)(1 - Wd) * E : E;
             m += dm;
             if (m >= Wd) m -= Wd;
         }
-        const bool rw = (f >= Q - Wd);      // next row wraps to row 0
-        const uint32_t hoffb = rw ? rowwrap : wdb;
-        const uint32_t aC = ad - qb + goffb, aB = ad - 2 * qb + hoffb, aA = ad - 3 * qb + goffb + hoffb;
-        // wrap edges: the other orientation (c = -2, negated step)
-        const f32x2 tzc = cw ? kMinusTwo2 : kTwo2, tzr = rw ? kMinusTwo2 : kTwo2;
-        const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u) ^ (rw ? 12u : 0u);
-        f32x2 xd[K / 2], xc[K / 2], xb[K / 2], xa[K / 2];
-        lds_p<K>(ad, xd);
-        lds_p<K>(aC, xc);
-        lds_p<K>(aB, xb);
-        lds_p<K>(aA, xa);
-        const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
-        const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
-#pragma unroll
-        for (int h = 0; h < K / 2; ++h) {
-            // colour 2: D-C, B-A; colour 3: D-B, C-A
-            pair_x2(xd[h], xc[h], w0, tzc);
-            pair_x2(xb[h], xa[h], w1, tzc);
-            pair_x2(xd[h], xb[h], w2, tzr);
-            pair_x2(xc[h], xa[h], w3, tzr);
-            if (dwt) {
-                dwt_x2(xd[h], th2[h], tk2[h], st2[h]);
-                dwt_x2(xc[h], th2[h], tk2[h], st2[h]);
-                dwt_x2(xb[h], th2[h], tk2[h], st2[h]);
-                dwt_x2(xa[h], th2[h], tk2[h], st2[h]);
-            }
-            xa[h] = p_wrap(xa[h]);
-            xb[h] = p_wrap(xb[h]);
-            xc[h] = p_wrap(xc[h]);
-            xd[h] = p_wrap(xd[h]);
+        const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u);
+        odd_block_x2<K, false, kDwt, kWrap>(ad, goffb - qb, wdb - 2 * qb, goffb + wdb - 3 * qb, wb, a1,
+                                            cw ? kMinusTwo2 : kTwo2, th2, tk2, st2);
+    }
+    for (; f < Q; f += blockDim.x, ad += step) {
+        if (!kFixedColumn) {
+            cw = (m == Wd - 1);
+            goffb = cw ? (uint32_t)(1 - Wd) * E : E;
+            m += dm;
+            if (m >= Wd) m -= Wd;
         }
-        sts_p<K>(ad, xd);
-        sts_p<K>(aC, xc);
-        sts_p<K>(aB, xb);
-        sts_p<K>(aA, xa);
+        const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u) ^ 12u;
+        odd_block_x2<K, true, kDwt, kWrap>(ad, goffb - qb, rowwrap - 2 * qb, goffb + rowwrap - 3 * qb, wb, a1,
+                                           cw ? kMinusTwo2 : kTwo2, th2, tk2, st2);
+    }
+}
+
+template <int K, bool kFixedColumn>
+__device__ __forceinline__ void block_pass_odd_x2_sel(float *xs, const uint8_t *wnib, float alpha, int Q, int Wd,
+                                                      int m0, int dm, bool dwt, bool wrap, const float *thc,
+                                                      const float *thc2, const float *stp_)
+{
+    if (dwt) {
+        if (wrap) block_pass_odd_x2<K, kFixedColumn, true, true>(xs, wnib, alpha, Q, Wd, m0, dm, thc, thc2, stp_);
+        else block_pass_odd_x2<K, kFixedColumn, true, false>(xs, wnib, alpha, Q, Wd, m0, dm, thc, thc2, stp_);
+    } else {
+        if (wrap) block_pass_odd_x2<K, kFixedColumn, false, true>(xs, wnib, alpha, Q, Wd, m0, dm, thc, thc2, stp_);
+        else block_pass_odd_x2<K, kFixedColumn, false, false>(xs, wnib, alpha, Q, Wd, m0, dm, thc, thc2, stp_);
     }
 }
 
@@ -1530,6 +1570,9 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
     for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
         const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));
         const bool dwt = dwt_on && phase == 0;
+        // binary32 lattice phases are wrapped on every wrap_p-th sweep of the
+        // trial (16-bit storage: every sweep)
+        const bool wrap = sizeof(Store) == 2 || v.wrap_p <= 1 || (s % v.wrap_p) == 0;
         if (dwt && tid < K) {
             bool neg = false;
             const float c = 2.0f * (hw - dwt_theta(v.seed, rep0 + tid, s, &neg));
@@ -1547,18 +1590,31 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                     block_pass_even_x2<K>(xf, v.wnib, at.x, v.Q);
                     __syncthreads();
                     if (dm == 0)
-                        block_pass_odd_x2<K, true>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
+                        block_pass_odd_x2_sel<K, true>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, wrap, t.thc, t.thc2,
+                                                       t.stp);
                     else
-                        block_pass_odd_x2<K, false>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
+                        block_pass_odd_x2_sel<K, false>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, wrap, t.thc, t.thc2,
+                                                        t.stp);
                     __syncthreads();
                 }
             } else {
                 block_pass_even<Store, K>(t.xs, v.wnib, at.x, v.Q);
                 __syncthreads();
-                if (dm == 0)
-                    block_pass_odd<Store, K, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
-                else
-                    block_pass_odd<Store, K, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2, t.stp);
+                if (wrap) {
+                    if (dm == 0)
+                        block_pass_odd<Store, K, true, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc, t.thc2,
+                                                             t.stp);
+                    else
+                        block_pass_odd<Store, K, false, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc,
+                                                              t.thc2, t.stp);
+                } else if constexpr (sizeof(Store) == 4) {
+                    if (dm == 0)
+                        block_pass_odd<Store, K, true, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc,
+                                                              t.thc2, t.stp);
+                    else
+                        block_pass_odd<Store, K, false, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, t.thc,
+                                                               t.thc2, t.stp);
+                }
                 __syncthreads();
             }
         } else {

@@ -532,6 +532,21 @@ int cosm::ensure_run_buffers(cosm_handle *h, int replicas)
     return COSM_OK;
 }
 
+int32_t cosm::lattice_wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, int flags, int mode,
+                                  int storage)
+{
+    if (mode != MODE_LATTICE2D_ || storage != COSM_F32) return 1;
+    const double a0 = std::fabs(alpha0_deg) / 360.0;
+    const bool dwt = !(flags & COSM_NO_DWT) && dwt_period > 0;
+    int32_t best = 1;
+    for (int P = 2; P <= 4; ++P) {
+        const double twists = dwt ? std::ceil((double)P / dwt_period) : 0.0;
+        if (0.5 + 4.0 * P * a0 + twists * std::fabs(dwt_ratio) * a0 >= 0.999) break;
+        best = P;
+    }
+    return best;
+}
+
 InstView cosm::inst_view(cosm_handle *h)
 {
     InstView v;
@@ -565,6 +580,8 @@ InstView cosm::inst_view(cosm_handle *h)
     v.words = (h->g.n + 31) / 32;
     // the scalar binary32 lattice passes stay available as a cross-check
     v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : 1;
+    v.wrap_p = lattice_wrap_period(h->prm.alpha0_deg, h->prm.dwt_ratio, h->prm.dwt_period, h->prm.flags, h->mode,
+                                   h->prm.storage);
     return v;
 }
 
@@ -852,9 +869,11 @@ extern "C" int cosm_get_replica_cuts(cosm_handle *h, int64_t *cuts, int32_t *bes
 }
 
 // Stored value (FP32 or FP16, representative in [-1/2, 1/2]) -> turn in [0, 1).
+// Turn in [0, 1) of a stored representative (binary32 lattice phases may sit
+// anywhere in (-1, 1) between wraps).
 static inline double to_turn(double g)
 {
-    double x = g < 0.0 ? g + 1.0 : g;
+    const double x = g - std::floor(g);
     return x >= 1.0 ? 0.0 : x;
 }
 

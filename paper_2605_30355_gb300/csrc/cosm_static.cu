@@ -193,6 +193,7 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
     v.seed = seed;
     v.replicas = replicas;
     v.dwt_period = (p->flags & COSM_NO_DWT) ? 0 : p->dwt_period;
+    v.wrap_p = lattice_wrap_period(p->alpha0_deg, p->dwt_ratio, p->dwt_period, p->flags, mode, p->storage);
     v.window = (float)(p->window_deg / 360.0);
     v.flags = p->flags;
     v.P = p->n_bisectors;
