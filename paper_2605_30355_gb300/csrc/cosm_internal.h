@@ -71,7 +71,7 @@ struct InstView {
     int64_t *trace;       // [replicas][n_trace] readout energies
     uint32_t *bits;       // [replicas][words] spins of the kept readout (slot order)
     int32_t words;        // (n + 31) / 32
-    int32_t paired;       // binary32 lattice tiles: packed f32x2 passes (else scalar)
+    int32_t paired;       // binary32 lattice tiles: packed f32x2 passes (0 scalar, 1 single blocks, 2 block pairs in the even pass)
     int32_t wrap_p;       // binary32 lattice phases: wrapped on sweeps s with s % wrap_p == 0
 };
 

@@ -1201,6 +1201,66 @@ __device__ __forceinline__ void block_pass_odd_x2_sel(float *xs, const uint8_t *
     }
 }
 
+// Block pairs in the even pass (two replicas per tile, an even number of
+// block columns): a thread takes the blocks f = 2u and f + 1 of one block row
+// together, so the slots of both sit side by side in each sublattice and move
+// in 16-byte shared accesses, with one weight load, one address update and
+// one loop step per two blocks. (In the odd pass the C and A slots of such a
+// pair straddle a 16-byte boundary; their 8-byte accesses at a 16-byte
+// stride conflict in the shared-memory banks, so the odd pass keeps one
+// block per thread.)
+__device__ __forceinline__ void lds_q2(uint32_t a, f32x2 &x0, f32x2 &x1)
+{
+    asm volatile("ld.shared.v2.b64 {%0, %1}, [%2];" : "=l"(x0), "=l"(x1) : "r"(a) : "memory");
+}
+__device__ __forceinline__ void sts_q2(uint32_t a, f32x2 x0, f32x2 x1)
+{
+    asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(x0), "l"(x1) : "memory");
+}
+__device__ __forceinline__ f32x2 lds_q1(uint32_t a)
+{
+    f32x2 x;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(x) : "r"(a) : "memory");
+    return x;
+}
+__device__ __forceinline__ void sts_q1(uint32_t a, f32x2 x)
+{
+    asm volatile("st.shared.b64 [%0], %1;" ::"r"(a), "l"(x) : "memory");
+}
+
+__device__ __forceinline__ void block_pass_even_x2p(float *xs, const uint8_t *wnib, float alpha, int Q)
+{
+    constexpr uint32_t E = 8;  // bytes per slot (two binary32 replicas)
+    const uint32_t a1 = __float_as_uint(alpha), n1 = a1 ^ 0x80000000u;
+    const f32x2 a2 = ((f32x2)a1 << 32) | a1, n2 = ((f32x2)n1 << 32) | n1;
+    const uint32_t qb = (uint32_t)Q * E, qb2 = 2 * qb, qb3 = 3 * qb, step = blockDim.x * 2 * E;
+    const int U = Q >> 1;
+    const unsigned short *wp = reinterpret_cast<const unsigned short *>(wnib);
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + threadIdx.x * 2 * E;
+#pragma unroll 1
+    for (int u = threadIdx.x; u < U; u += blockDim.x, ad += step) {
+        const uint32_t wb = __ldg(wp + u);  // block 2u: bits 0-3, block 2u + 1: bits 8-11
+        f32x2 xa0, xa1, xb0, xb1, xc0, xc1, xd0, xd1;
+        lds_q2(ad, xa0, xa1);
+        lds_q2(ad + qb, xb0, xb1);
+        lds_q2(ad + qb2, xc0, xc1);
+        lds_q2(ad + qb3, xd0, xd1);
+        // colour 0: A-B, C-D; colour 1: A-C, B-D (first slot = smaller id)
+        pair_x2(xa0, xb0, (wb & 0x001u) ? n2 : a2, kTwo2);
+        pair_x2(xa1, xb1, (wb & 0x100u) ? n2 : a2, kTwo2);
+        pair_x2(xc0, xd0, (wb & 0x002u) ? n2 : a2, kTwo2);
+        pair_x2(xc1, xd1, (wb & 0x200u) ? n2 : a2, kTwo2);
+        pair_x2(xa0, xc0, (wb & 0x004u) ? n2 : a2, kTwo2);
+        pair_x2(xa1, xc1, (wb & 0x400u) ? n2 : a2, kTwo2);
+        pair_x2(xb0, xd0, (wb & 0x008u) ? n2 : a2, kTwo2);
+        pair_x2(xb1, xd1, (wb & 0x800u) ? n2 : a2, kTwo2);
+        sts_q2(ad, xa0, xa1);
+        sts_q2(ad + qb, xb0, xb1);
+        sts_q2(ad + qb2, xc0, xc1);
+        sts_q2(ad + qb3, xd0, xd1);
+    }
+}
+
 // ---------------------------------------------------------------- fixed point sweep
 // Eq. (6) on the 2^-16-turn grid: with phases held as q << 16, d = x_i - x_j
 // read as int32 is the minimum angular difference (times 2^32) and the
@@ -1584,7 +1644,20 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
             // colours 0, 1 in the 2x2 blocks; colours 2, 3 (+ DWT) in the
             // shifted blocks; binary32 tiles of an even width in f32x2 pairs
             constexpr bool kPaired = sizeof(Store) == 4 && (K == 2 || K == 4);
-            if (kPaired && v.paired) {
+            if (K == 2 && kPaired && v.paired == 2) {
+                if constexpr (K == 2 && kPaired) {
+                    float *xf = reinterpret_cast<float *>(t.xs);
+                    block_pass_even_x2p(xf, v.wnib, at.x, v.Q);
+                    __syncthreads();
+                    if (dm == 0)
+                        block_pass_odd_x2_sel<K, true>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, wrap, t.thc, t.thc2,
+                                                       t.stp);
+                    else
+                        block_pass_odd_x2_sel<K, false>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, wrap, t.thc, t.thc2,
+                                                        t.stp);
+                    __syncthreads();
+                }
+            } else if (kPaired && v.paired) {
                 if constexpr (kPaired) {
                     float *xf = reinterpret_cast<float *>(t.xs);
                     block_pass_even_x2<K>(xf, v.wnib, at.x, v.Q);

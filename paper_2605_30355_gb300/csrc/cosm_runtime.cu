@@ -459,6 +459,12 @@ int cosm::choose_layout(cosm_handle *h, int replicas)
     const int *Ks = p.storage == COSM_F32 ? Ks_f32 : Ks_f16;
     int forceK = env_int("COSM_K", 0), forceT = env_int("COSM_THREADS", 0);
     int bestK = 0, bestT = 0, bestOcc = 0;
+    // binary32 lattice tiles of two replicas on an even number of block
+    // columns take two adjacent 2x2 blocks per thread in the even pass
+    // (COSM_SCALAR_F32 and COSM_SINGLE_BLOCKS keep the other passes
+    // available as cross-checks)
+    const bool pairs_ok = mode == MODE_LATTICE2D_ && p.storage == COSM_F32 && h->Wd % 2 == 0 &&
+                          !std::getenv("COSM_SCALAR_F32") && !std::getenv("COSM_SINGLE_BLOCKS");
     long bestScore = -1;
     for (int k = 0; k < 3; ++k) {
         const int K = Ks[k];
@@ -509,6 +515,7 @@ int cosm::choose_layout(cosm_handle *h, int replicas)
     if (!bestK) return fail(COSM_ERR_TOO_LARGE, "no replica tile fits in shared memory");
     h->K = bestK;
     h->threads = bestT;
+    h->block_pairs = pairs_ok && bestK == 2;
     h->occupancy = bestOcc;
     h->smem = sweep_smem_bytes(p.storage, bestK, h->g.n, P, mode);
     const size_t esz = p.storage == COSM_F32 ? 4 : 2;
@@ -579,7 +586,7 @@ InstView cosm::inst_view(cosm_handle *h)
     v.bisB = h->d_bisB.p;
     v.words = (h->g.n + 31) / 32;
     // the scalar binary32 lattice passes stay available as a cross-check
-    v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : 1;
+    v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : (h->block_pairs ? 2 : 1);
     v.wrap_p = lattice_wrap_period(h->prm.alpha0_deg, h->prm.dwt_ratio, h->prm.dwt_period, h->prm.flags, h->mode,
                                    h->prm.storage);
     return v;

@@ -379,8 +379,33 @@ def test_paired_f32_lattice_equals_scalar(cosm, orc, K, flags):
         os.environ.pop("COSM_SCALAR_F32", None)
 
 
+@pytest.mark.parametrize("L1,L2,threads", [(24, 32, 0), (20, 36, 64), (6, 4, 0), (10, 28, 96), (8, 30, 0)])
+def test_block_pairs_equal_single_blocks(cosm, orc, L1, L2, threads):
+    # two-replica binary32 tiles take two 2x2 blocks per thread in the even
+    # pass where the block rows have an even width; the phases and cuts equal
+    # those of the one-block passes bit for bit, with the twist, wraps of
+    # rows and columns, fixed and moving columns (forced thread counts), and
+    # an odd width (one-block passes)
+    inst = instances.torus2d(L1, L2, 9)
+    os.environ["COSM_K"] = "2"
+    if threads:
+        os.environ["COSM_THREADS"] = str(threads)
+    try:
+        s = cosm.Solver.from_instance(inst, dwt_ratio=1.0)
+        assert s.layout()["lattice"] == 2
+        s.run(300, 6, 17)
+        x_pair, c_pair = s.get_state(), s.replica_cuts()[0]
+        os.environ["COSM_SINGLE_BLOCKS"] = "1"
+        s.run(300, 6, 17)
+        assert np.array_equal(s.get_state(), x_pair)
+        assert np.array_equal(s.replica_cuts()[0], c_pair)
+    finally:
+        for k in ("COSM_K", "COSM_THREADS", "COSM_SINGLE_BLOCKS"):
+            os.environ.pop(k, None)
+
+
 @pytest.mark.parametrize("storage,dims,scalar", [(0, True, False), (0, True, True), (0, False, False),
-                                                 (1, True, False), (1, False, False)])
+                                                 (1, True, False), (1, False, False), (0, True, "K2")])
 def test_exact_ties_follow_the_biased_sign(cosm, orc, storage, dims, scalar):
     # phases on a 1/16-turn grid make many pairs coincide (d = 0) or sit
     # exactly opposite (d = 1/2); with a step of 1/256 every operation is
@@ -391,7 +416,10 @@ def test_exact_ties_follow_the_biased_sign(cosm, orc, storage, dims, scalar):
     R = 4
     rng = np.random.default_rng(5)
     x0 = rng.integers(0, 16, (R, inst.n)) / 16.0
-    if scalar:
+    if scalar == "K2":
+        # two-replica tiles: the block-pair passes
+        os.environ["COSM_K"] = "2"
+    elif scalar:
         os.environ["COSM_SCALAR_F32"] = "1"
     try:
         s.set_state(x0, seed=3)
@@ -399,6 +427,7 @@ def test_exact_ties_follow_the_biased_sign(cosm, orc, storage, dims, scalar):
         x1 = s.get_state()
     finally:
         os.environ.pop("COSM_SCALAR_F32", None)
+        os.environ.pop("COSM_K", None)
     for r in range(R):
         xo, ties = orc.sweep(g, x0[r], 1.0 / 256, 1, seed=3, replica=r, storage=storage,
                              tie_eps=1e-12, **_params_kw(s))
