@@ -379,7 +379,8 @@ def test_paired_f32_lattice_equals_scalar(cosm, orc, K, flags):
         os.environ.pop("COSM_SCALAR_F32", None)
 
 
-@pytest.mark.parametrize("L1,L2,threads", [(24, 32, 0), (20, 36, 64), (6, 4, 0), (10, 28, 96), (8, 30, 0)])
+@pytest.mark.parametrize("L1,L2,threads", [(24, 32, 64), (20, 36, 64), (16, 16, 32), (24, 32, 0), (6, 4, 0),
+                                           (10, 28, 96), (8, 30, 0)])
 def test_block_pairs_equal_single_blocks(cosm, orc, L1, L2, threads):
     # two-replica binary32 tiles take two 2x2 blocks per thread in the even
     # pass where the block rows have an even width; the phases and cuts equal
