@@ -64,6 +64,7 @@ struct cosm_handle {
     int num_sms = 0;
     bool lattice = false;
     int64_t W = 0;                  // total weight
+    int64_t wbound = 0;             // sum over colours of the largest |w|, plus the largest |h|
     std::vector<int32_t> slot_of;   // original id -> slot
     std::vector<int32_t> orig_of;   // slot -> original id
     int32_t off[cosm::kMaxColors + 1] = {0};

@@ -1261,6 +1261,132 @@ __device__ __forceinline__ void block_pass_even_x2p(float *xs, const uint8_t *wn
     }
 }
 
+// ---------------------------------------------------------------- paired edge lists
+// The edge-list sweep of binary32 tiles in f32x2 lanes: the two lanes of an
+// instruction carry the two replicas of a pair (tiles of 2 or 4 replicas) or
+// two edges of a thread's batch (single-replica tiles); each lane rounds
+// exactly as the scalar pair_update does, so every tile size gives the same
+// phases. Slots are addressed by 32-bit shared offsets; a batch past the end
+// of its colour loads slot 0 harmlessly and skips its stores.
+// kWrapEach: every update is wrapped (instances whose steps per sweep could
+// carry a phase far from [-1/2, 1/2]); otherwise the phases are wrapped by the
+// pass after the colours on every wrap_p-th sweep.
+__device__ __forceinline__ float lds_f(uint32_t a)
+{
+    float x;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x) : "r"(a) : "memory");
+    return x;
+}
+__device__ __forceinline__ void sts_f(uint32_t a, float x)
+{
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(x) : "memory");
+}
+__device__ __forceinline__ f32x2 p_pack(float lo, float hi)
+{
+    return ((f32x2)__float_as_uint(hi) << 32) | __float_as_uint(lo);
+}
+
+template <int K, int B, bool kPrefetch, bool kWrapEach>
+__device__ __forceinline__ void general_colours_x2(const InstView &a, float *xs, float alpha, EdgePrefetch<B> &pf)
+{
+    static_assert(K == 1 || K == 2 || K == 4, "K");
+    static_assert(K > 1 || B % 2 == 0, "B");
+    constexpr uint32_t E = K * 4;  // bytes per slot
+    const int tid = threadIdx.x, nt = blockDim.x, step = B * nt;
+    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
+    for (int c = 0; c < a.C; ++c) {
+        const int e1 = __ldg(a.off + c + 1);
+        for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += step) {
+            uint32_t rec[B];
+            int32_t wv[B];
+            if (kPrefetch && pf.e0 == e0) {
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    rec[u] = pf.rec[u];
+                    wv[u] = pf.w[u];
+                }
+            } else {
+                fetch_edges<B>(a, e0, e1, rec, wv);
+            }
+            if (kPrefetch) {
+                // the next batch: further in this colour, else the first batch
+                // of the next colour (of colour 0 for the next sweep)
+                int n0 = e0 + step, n1 = e1;
+                if (n0 >= e1) {
+                    const int nc = (c + 1 < a.C) ? c + 1 : 0;
+                    n0 = __ldg(a.off + nc) + tid;
+                    n1 = __ldg(a.off + nc + 1);
+                }
+                fetch_edges<B>(a, n0, n1, pf.rec, pf.w);
+                pf.e0 = n0;
+            }
+            uint32_t ai[B], aj[B];
+            float aw[B];
+#pragma unroll
+            for (int u = 0; u < B; ++u) {
+                ai[u] = xb + (rec[u] & 0xFFFFu) * E;
+                aj[u] = xb + (rec[u] >> 16) * E;
+                aw[u] = alpha * weight_f((int8_t)wv[u]);
+            }
+            if constexpr (K == 1) {
+                float xi[B], xj[B];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    xi[u] = lds_f(ai[u]);
+                    xj[u] = lds_f(aj[u]);
+                }
+#pragma unroll
+                for (int q = 0; q < B; q += 2) {
+                    f32x2 x1 = p_pack(xi[q], xi[q + 1]), x2 = p_pack(xj[q], xj[q + 1]);
+                    pair_x2(x1, x2, p_pack(aw[q], aw[q + 1]), kTwo2);
+                    if constexpr (kWrapEach) {
+                        x1 = p_wrap(x1);
+                        x2 = p_wrap(x2);
+                    }
+                    xi[q] = p_lo(x1);
+                    xi[q + 1] = p_hi(x1);
+                    xj[q] = p_lo(x2);
+                    xj[q + 1] = p_hi(x2);
+                }
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    if (e0 + u * nt < e1) {
+                        sts_f(ai[u], xi[u]);
+                        sts_f(aj[u], xj[u]);
+                    }
+                }
+            } else {
+                f32x2 xi[B][K / 2], xj[B][K / 2];
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    lds_p<K>(ai[u], xi[u]);
+                    lds_p<K>(aj[u], xj[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    const f32x2 aw2 = p_pack(aw[u], aw[u]);
+#pragma unroll
+                    for (int h = 0; h < K / 2; ++h) {
+                        pair_x2(xi[u][h], xj[u][h], aw2, kTwo2);
+                        if constexpr (kWrapEach) {
+                            xi[u][h] = p_wrap(xi[u][h]);
+                            xj[u][h] = p_wrap(xj[u][h]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < B; ++u) {
+                    if (e0 + u * nt < e1) {
+                        sts_p<K>(ai[u], xi[u]);
+                        sts_p<K>(aj[u], xj[u]);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- fixed point sweep
 // Eq. (6) on the 2^-16-turn grid: with phases held as q << 16, d = x_i - x_j
 // read as int32 is the minimum angular difference (times 2^32) and the
@@ -1695,7 +1821,16 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 // sequential conflict-free search: colours in order (eq. (11));
                 // tiles of 2 or 4 replicas prefetch their next edge batch,
                 // single- and 8-replica tiles keep registers for occupancy
-                if constexpr (K == 2 || K == 4) {
+                if constexpr (sizeof(Store) == 4 && (K == 1 || K == 2 || K == 4)) {
+                    // binary32: f32x2 lanes (replica pairs, or edge pairs for
+                    // single-replica tiles without the prefetch)
+                    float *xf = reinterpret_cast<float *>(t.xs);
+                    constexpr bool kPf = K > 1;
+                    if (v.wrap_p == 0)
+                        general_colours_x2<K, 4, kPf, true>(v, xf, at.x, pf);
+                    else
+                        general_colours_x2<K, 4, kPf, false>(v, xf, at.x, pf);
+                } else if constexpr (K == 2 || K == 4) {
                     general_colours_pf<Store, K, 4>(v, t.xs, at.x, pf);
                 } else {
                     for (int c = 0; c < v.C; ++c) {
@@ -1745,7 +1880,12 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 }
                 __syncthreads();
             }
-            if (dwt) {
+            // binary32 edge lists without per-update wraps: the phases are
+            // wrapped after the colours on every wrap_p-th sweep (with the
+            // twist when it falls on the same sweep)
+            const bool wrap_sweep = kMode == MODE_GENERAL && sizeof(Store) == 4 && v.wrap_p >= 1 &&
+                                    (s % v.wrap_p) == 0;
+            if (dwt || wrap_sweep) {
                 if (v.C == 0) __syncthreads();
                 float st[K];
 #pragma unroll
@@ -1753,7 +1893,8 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 for (int u = tid; u < n; u += nt) {
                     float x[K];
                     ldk<K>(t.xs + (size_t)u * K, x);
-                    dwt_apply<K>(x, t.thc, t.thc2, st);
+                    if (dwt) dwt_apply<K>(x, t.thc, t.thc2, st);
+                    if (wrap_sweep) wrap_all<K>(x);
                     stk<K>(t.xs + (size_t)u * K, x);
                 }
                 __syncthreads();

@@ -399,6 +399,7 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
         h->W += g.w[(size_t)e];
     }
     for (int c = 0; c < h->C; ++c) h->off[c + 1] += h->off[c];
+    h->wbound = colour_weight_bound(h->off, h->C, wv.data(), gd->h, g.n);
     // device copies
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -539,19 +540,34 @@ int cosm::ensure_run_buffers(cosm_handle *h, int replicas)
     return COSM_OK;
 }
 
-int32_t cosm::lattice_wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, int flags, int mode,
-                                  int storage)
+int32_t cosm::wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, int flags, int mode, int storage,
+                          int64_t wbound)
 {
-    if (mode != MODE_LATTICE2D_ || storage != COSM_F32) return 1;
+    if (storage != COSM_F32 || (mode != MODE_LATTICE2D_ && mode != MODE_GENERAL_)) return 1;
     const double a0 = std::fabs(alpha0_deg) / 360.0;
     const bool dwt = !(flags & COSM_NO_DWT) && dwt_period > 0;
-    int32_t best = 1;
-    for (int P = 2; P <= 4; ++P) {
+    const double limit = mode == MODE_LATTICE2D_ ? 0.999 : 1.999;
+    int32_t best = mode == MODE_LATTICE2D_ ? 1 : 0;
+    for (int P = 1; P <= 4; ++P) {
         const double twists = dwt ? std::ceil((double)P / dwt_period) : 0.0;
-        if (0.5 + 4.0 * P * a0 + twists * std::fabs(dwt_ratio) * a0 >= 0.999) break;
+        if (0.5 + (double)wbound * P * a0 + twists * std::fabs(dwt_ratio) * a0 >= limit) break;
         best = P;
     }
     return best;
+}
+
+int64_t cosm::colour_weight_bound(const int32_t *off, int C, const int8_t *w, const int32_t *h, int32_t n)
+{
+    int64_t b = 0;
+    for (int c = 0; c < C; ++c) {
+        int32_t mx = 0;
+        for (int32_t k = off[c]; k < off[c + 1]; ++k) mx = std::max(mx, (int32_t)std::abs((int32_t)w[k]));
+        b += mx;
+    }
+    int32_t mh = 0;
+    if (h)
+        for (int32_t v = 0; v < n; ++v) mh = std::max(mh, std::abs(h[v]));
+    return b + mh;
 }
 
 InstView cosm::inst_view(cosm_handle *h)
@@ -587,8 +603,8 @@ InstView cosm::inst_view(cosm_handle *h)
     v.words = (h->g.n + 31) / 32;
     // the scalar binary32 lattice passes stay available as a cross-check
     v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : (h->block_pairs ? 2 : 1);
-    v.wrap_p = lattice_wrap_period(h->prm.alpha0_deg, h->prm.dwt_ratio, h->prm.dwt_period, h->prm.flags, h->mode,
-                                   h->prm.storage);
+    v.wrap_p = wrap_period(h->prm.alpha0_deg, h->prm.dwt_ratio, h->prm.dwt_period, h->prm.flags, h->mode,
+                           h->prm.storage, h->wbound);
     return v;
 }
 

@@ -138,6 +138,9 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
         ij[(size_t)k] = (uint32_t)g.src[(size_t)e] | ((uint32_t)g.dst[(size_t)e] << 16);
         wv[(size_t)k] = (int8_t)g.w[(size_t)e];
     }
+    std::vector<int32_t> offc((size_t)g.C + 1);
+    for (int c = 0; c <= g.C; ++c) offc[(size_t)c] = (int32_t)count[(size_t)c];
+    const int64_t wbound = colour_weight_bound(offc.data(), g.C, wv.data(), nullptr, g.n);
     std::vector<int32_t> orig((size_t)g.n);
     for (int32_t v = 0; v < g.n; ++v) orig[(size_t)v] = v;
     const double a0 = p->alpha0_deg / 360.0;
@@ -193,7 +196,7 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
     v.seed = seed;
     v.replicas = replicas;
     v.dwt_period = (p->flags & COSM_NO_DWT) ? 0 : p->dwt_period;
-    v.wrap_p = lattice_wrap_period(p->alpha0_deg, p->dwt_ratio, p->dwt_period, p->flags, mode, p->storage);
+    v.wrap_p = wrap_period(p->alpha0_deg, p->dwt_ratio, p->dwt_period, p->flags, mode, p->storage, wbound);
     v.window = (float)(p->window_deg / 360.0);
     v.flags = p->flags;
     v.P = p->n_bisectors;

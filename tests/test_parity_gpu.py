@@ -50,6 +50,9 @@ CASES = [
     ("torus_rect", lambda: instances.torus2d(12, 20, 3), True),
     ("reg3", lambda: instances.random_regular(1000, 3, 1), False),
     ("gnm_w3", lambda: instances.sparse_gnm(777, 2300, 2), False),
+    # weights up to 20: a sweep could carry a phase out of (-2, 2), so the
+    # binary32 edge-list kernel wraps after every update here
+    ("gnm_w20", lambda: instances.sparse_gnm(600, 1800, 4, wmax=20), False),
     ("torus3d", lambda: instances.torus3d(4, 6, 8, 5), True),
 ]
 
@@ -256,9 +259,14 @@ def test_layouts_agree_bit_exact(cosm, orc):
     # bit-identical across K. The lattice kernel wraps a phase once per 2x2
     # block instead of after every update, so the two variants agree to
     # rounding per sweep (checked by the one-sweep parity tests), not bitwise.
-    inst = instances.torus2d(16, 16, 6)
-    col, C = orc.color_instance(inst)
-    for dims, Ks, kind in ((True, (1, 2, 4), 2), (False, (1, 2, 4), 0)):
+    # The binary32 edge-list kernel pairs two replicas (K = 2, 4) or two edges
+    # (K = 1) in its f32x2 lanes; with weights up to 20 it wraps after every
+    # update instead of once per sweep.
+    torus = instances.torus2d(16, 16, 6)
+    heavy = instances.sparse_gnm(500, 1500, 7, wmax=20)
+    for inst, dims, Ks, kind in ((torus, True, (1, 2, 4), 2), (torus, False, (1, 2, 4), 0),
+                                 (heavy, False, (1, 2, 4), 0)):
+        col, C = orc.color_instance(inst)
         res = []
         for K in Ks:
             os.environ["COSM_K"] = str(K)
