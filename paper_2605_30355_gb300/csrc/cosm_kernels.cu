@@ -1286,104 +1286,137 @@ __device__ __forceinline__ f32x2 p_pack(float lo, float hi)
     return ((f32x2)__float_as_uint(hi) << 32) | __float_as_uint(lo);
 }
 
-template <int K, int B, bool kPrefetch, bool kWrapEach>
-__device__ __forceinline__ void general_colours_x2(const InstView &a, float *xs, float alpha, EdgePrefetch<B> &pf)
+// One batch of B edges per thread (edges e0, e0 + nt, ...); kTail: the batch
+// may run past the end e1 of its colour (loads of slot 0, stores skipped).
+template <int K, int B, bool kWrapEach, bool kTail>
+__device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, float alpha, int e0, int e1, int nt)
 {
-    static_assert(K == 1 || K == 2 || K == 4, "K");
-    static_assert(K > 1 || B % 2 == 0, "B");
     constexpr uint32_t E = K * 4;  // bytes per slot
-    const int tid = threadIdx.x, nt = blockDim.x, step = B * nt;
-    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
-    for (int c = 0; c < a.C; ++c) {
-        const int e1 = __ldg(a.off + c + 1);
-        for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += step) {
-            uint32_t rec[B];
-            int32_t wv[B];
-            if (kPrefetch && pf.e0 == e0) {
+    uint32_t ai[B], aj[B];
+    float aw[B];
 #pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    rec[u] = pf.rec[u];
-                    wv[u] = pf.w[u];
-                }
-            } else {
-                fetch_edges<B>(a, e0, e1, rec, wv);
+    for (int u = 0; u < B; ++u) {
+        const int e = e0 + u * nt;
+        uint32_t rec = 0;
+        int w = 0;
+        if (!kTail || e < e1) {
+            rec = __ldg(a.ij + e);
+            w = __ldg(a.w + e);
+        }
+        ai[u] = xb + (rec & 0xFFFFu) * E;
+        aj[u] = xb + (rec >> 16) * E;
+        aw[u] = alpha * weight_f((int8_t)w);
+    }
+    if constexpr (K == 1) {
+        float xi[B], xj[B];
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            xi[u] = lds_f(ai[u]);
+            xj[u] = lds_f(aj[u]);
+        }
+#pragma unroll
+        for (int q = 0; q < B; q += 2) {
+            f32x2 x1 = p_pack(xi[q], xi[q + 1]), x2 = p_pack(xj[q], xj[q + 1]);
+            pair_x2(x1, x2, p_pack(aw[q], aw[q + 1]), kTwo2);
+            if constexpr (kWrapEach) {
+                x1 = p_wrap(x1);
+                x2 = p_wrap(x2);
             }
-            if (kPrefetch) {
-                // the next batch: further in this colour, else the first batch
-                // of the next colour (of colour 0 for the next sweep)
-                int n0 = e0 + step, n1 = e1;
-                if (n0 >= e1) {
-                    const int nc = (c + 1 < a.C) ? c + 1 : 0;
-                    n0 = __ldg(a.off + nc) + tid;
-                    n1 = __ldg(a.off + nc + 1);
-                }
-                fetch_edges<B>(a, n0, n1, pf.rec, pf.w);
-                pf.e0 = n0;
+            xi[q] = p_lo(x1);
+            xi[q + 1] = p_hi(x1);
+            xj[q] = p_lo(x2);
+            xj[q + 1] = p_hi(x2);
+        }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            if (!kTail || e0 + u * nt < e1) {
+                sts_f(ai[u], xi[u]);
+                sts_f(aj[u], xj[u]);
             }
-            uint32_t ai[B], aj[B];
-            float aw[B];
+        }
+    } else {
+        f32x2 xi[B][K / 2], xj[B][K / 2];
 #pragma unroll
-            for (int u = 0; u < B; ++u) {
-                ai[u] = xb + (rec[u] & 0xFFFFu) * E;
-                aj[u] = xb + (rec[u] >> 16) * E;
-                aw[u] = alpha * weight_f((int8_t)wv[u]);
-            }
-            if constexpr (K == 1) {
-                float xi[B], xj[B];
+        for (int u = 0; u < B; ++u) {
+            lds_p<K>(ai[u], xi[u]);
+            lds_p<K>(aj[u], xj[u]);
+        }
 #pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    xi[u] = lds_f(ai[u]);
-                    xj[u] = lds_f(aj[u]);
-                }
+        for (int u = 0; u < B; ++u) {
+            const f32x2 aw2 = p_pack(aw[u], aw[u]);
 #pragma unroll
-                for (int q = 0; q < B; q += 2) {
-                    f32x2 x1 = p_pack(xi[q], xi[q + 1]), x2 = p_pack(xj[q], xj[q + 1]);
-                    pair_x2(x1, x2, p_pack(aw[q], aw[q + 1]), kTwo2);
-                    if constexpr (kWrapEach) {
-                        x1 = p_wrap(x1);
-                        x2 = p_wrap(x2);
-                    }
-                    xi[q] = p_lo(x1);
-                    xi[q + 1] = p_hi(x1);
-                    xj[q] = p_lo(x2);
-                    xj[q + 1] = p_hi(x2);
-                }
-#pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    if (e0 + u * nt < e1) {
-                        sts_f(ai[u], xi[u]);
-                        sts_f(aj[u], xj[u]);
-                    }
-                }
-            } else {
-                f32x2 xi[B][K / 2], xj[B][K / 2];
-#pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    lds_p<K>(ai[u], xi[u]);
-                    lds_p<K>(aj[u], xj[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    const f32x2 aw2 = p_pack(aw[u], aw[u]);
-#pragma unroll
-                    for (int h = 0; h < K / 2; ++h) {
-                        pair_x2(xi[u][h], xj[u][h], aw2, kTwo2);
-                        if constexpr (kWrapEach) {
-                            xi[u][h] = p_wrap(xi[u][h]);
-                            xj[u][h] = p_wrap(xj[u][h]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    if (e0 + u * nt < e1) {
-                        sts_p<K>(ai[u], xi[u]);
-                        sts_p<K>(aj[u], xj[u]);
-                    }
+            for (int h = 0; h < K / 2; ++h) {
+                pair_x2(xi[u][h], xj[u][h], aw2, kTwo2);
+                if constexpr (kWrapEach) {
+                    xi[u][h] = p_wrap(xi[u][h]);
+                    xj[u][h] = p_wrap(xj[u][h]);
                 }
             }
         }
+#pragma unroll
+        for (int u = 0; u < B; ++u) {
+            if (!kTail || e0 + u * nt < e1) {
+                sts_p<K>(ai[u], xi[u]);
+                sts_p<K>(aj[u], xj[u]);
+            }
+        }
+    }
+}
+
+// The colours of one sweep: whole batches without bounds checks, then at
+// most one checked batch per thread at the end of each colour.
+template <int K, int B, bool kWrapEach>
+__device__ __forceinline__ void general_colours_x2(const InstView &a, float *xs, float alpha)
+{
+    static_assert(K == 1 || K == 2 || K == 4, "K");
+    static_assert(K > 1 || B % 2 == 0, "B");
+    const int nt = blockDim.x;
+    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
+    for (int c = 0; c < a.C; ++c) {
+        const int e1 = __ldg(a.off + c + 1);
+        int e0 = __ldg(a.off + c) + threadIdx.x;
+        for (; e0 + (B - 1) * nt < e1; e0 += B * nt) edge_batch_x2<K, B, kWrapEach, false>(a, xb, alpha, e0, e1, nt);
+        if (e0 < e1) edge_batch_x2<K, B, kWrapEach, true>(a, xb, alpha, e0, e1, nt);
         __syncthreads();
+    }
+}
+
+// The twist and / or the wrap of binary32 edge-list tiles after the colours,
+// in f32x2 words: a word holds replicas 2h, 2h + 1 of one slot (K >= 2) or
+// one replica of two slots (K = 1). The twist is dwt_x2 (the step is added
+// without a wrap); kWrap wraps every phase.
+template <int K, bool kDwt, bool kWrap>
+__device__ __forceinline__ void twist_wrap_x2(float *xs, int n, const float *thc, const float *thc2,
+                                              const float *stp_)
+{
+    constexpr int H = K >= 2 ? K / 2 : 1;  // words per slot (K = 1: a word spans two slots)
+    f32x2 th2[H], tk2[H], st2[H];
+#pragma unroll
+    for (int h = 0; h < H; ++h) {
+        const int r0 = K >= 2 ? 2 * h : 0, r1 = K >= 2 ? 2 * h + 1 : 0;
+        th2[h] = kDwt ? p_pack(thc[r0], thc[r1]) : 0ull;
+        tk2[h] = kDwt ? p_pack(thc2[r0], thc2[r1]) : 0ull;
+        st2[h] = kDwt ? p_pack(stp_[r0], stp_[r1]) : 0ull;
+    }
+    // H words at a time: one slot (K >= 2) or two slots (K = 1); an odd n
+    // with K = 1 leaves one scalar
+    const int groups = K >= 2 ? n : (n >> 1);
+    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
+    for (int q = threadIdx.x; q < groups; q += blockDim.x) {
+        f32x2 x[H];
+        lds_p<2 * H>(xb + (uint32_t)q * 8 * H, x);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+            if constexpr (kDwt) dwt_x2(x[h], th2[h], tk2[h], st2[h]);
+            if constexpr (kWrap) x[h] = p_wrap(x[h]);
+        }
+        sts_p<2 * H>(xb + (uint32_t)q * 8 * H, x);
+    }
+    if (K == 1 && (n & 1) && threadIdx.x == 0) {
+        float x[1] = {xs[n - 1]};
+        if (kDwt && in_windows(x[0], thc[0], thc2[0])) x[0] = __fadd_rn(x[0], stp_[0]);
+        if (kWrap) x[0] = wrap_c(x[0]);
+        xs[n - 1] = x[0];
     }
 }
 
@@ -1825,11 +1858,10 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                     // binary32: f32x2 lanes (replica pairs, or edge pairs for
                     // single-replica tiles without the prefetch)
                     float *xf = reinterpret_cast<float *>(t.xs);
-                    constexpr bool kPf = K > 1;
                     if (v.wrap_p == 0)
-                        general_colours_x2<K, 4, kPf, true>(v, xf, at.x, pf);
+                        general_colours_x2<K, 4, true>(v, xf, at.x);
                     else
-                        general_colours_x2<K, 4, kPf, false>(v, xf, at.x, pf);
+                        general_colours_x2<K, 4, false>(v, xf, at.x);
                 } else if constexpr (K == 2 || K == 4) {
                     general_colours_pf<Store, K, 4>(v, t.xs, at.x, pf);
                 } else {
@@ -1880,12 +1912,21 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 }
                 __syncthreads();
             }
-            // binary32 edge lists without per-update wraps: the phases are
-            // wrapped after the colours on every wrap_p-th sweep (with the
-            // twist when it falls on the same sweep)
-            const bool wrap_sweep = kMode == MODE_GENERAL && sizeof(Store) == 4 && v.wrap_p >= 1 &&
-                                    (s % v.wrap_p) == 0;
-            if (dwt || wrap_sweep) {
+            // binary32 edge lists: the twist and the wrap (on every
+            // wrap_p-th sweep, or with every twist when each update is
+            // wrapped) in one pass of f32x2 words
+            constexpr bool kGenF32 = kMode == MODE_GENERAL && sizeof(Store) == 4 && K <= 4;
+            const bool wrap_sweep = kGenF32 && (v.wrap_p == 0 ? dwt : (s % v.wrap_p) == 0);
+            if (kGenF32 && (dwt || wrap_sweep)) {
+                if constexpr (kGenF32) {
+                    if (v.C == 0) __syncthreads();
+                    float *xf = reinterpret_cast<float *>(t.xs);
+                    if (dwt && wrap_sweep) twist_wrap_x2<K, true, true>(xf, n, t.thc, t.thc2, t.stp);
+                    else if (dwt) twist_wrap_x2<K, true, false>(xf, n, t.thc, t.thc2, t.stp);
+                    else twist_wrap_x2<K, false, true>(xf, n, t.thc, t.thc2, t.stp);
+                    __syncthreads();
+                }
+            } else if (dwt) {
                 if (v.C == 0) __syncthreads();
                 float st[K];
 #pragma unroll
@@ -1893,8 +1934,7 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 for (int u = tid; u < n; u += nt) {
                     float x[K];
                     ldk<K>(t.xs + (size_t)u * K, x);
-                    if (dwt) dwt_apply<K>(x, t.thc, t.thc2, st);
-                    if (wrap_sweep) wrap_all<K>(x);
+                    dwt_apply<K>(x, t.thc, t.thc2, st);
                     stk<K>(t.xs + (size_t)u * K, x);
                 }
                 __syncthreads();
