@@ -1420,6 +1420,173 @@ __device__ __forceinline__ void twist_wrap_x2(float *xs, int n, const float *thc
     }
 }
 
+// ---------------------------------------------------------------- paired 16-bit lattice
+// Lattice passes of 16-bit storage (binary16, bfloat16) in f32x2 lanes: a
+// storage word holds two replicas of a slot, which become one f32x2 pair;
+// each update is computed as in the binary32 passes, wrapped and rounded to
+// the storage type (round to nearest even) and widened again, exactly as
+// pair_block does for one lane, so the phases equal the scalar passes' bit
+// for bit.
+template <typename H>
+__device__ __forceinline__ f32x2 h2_to_p(uint32_t w)
+{
+    const float2 f = h2_to_f2<H>(w);
+    return p_pack(f.x, f.y);
+}
+template <typename H>
+__device__ __forceinline__ uint32_t p_to_h2(f32x2 x)
+{
+    return f2_to_h2<H>(p_lo(x), p_hi(x));
+}
+template <typename H>
+__device__ __forceinline__ f32x2 p_round16(f32x2 x)
+{
+    return h2_to_p<H>(p_to_h2<H>(p_wrap(x)));
+}
+template <typename H, int NW>
+__device__ __forceinline__ void lds_h(uint32_t a, f32x2 (&x)[NW])
+{
+    uint32_t w[NW];
+    ld_words<NW>(a, w);
+#pragma unroll
+    for (int i = 0; i < NW; ++i) x[i] = h2_to_p<H>(w[i]);
+}
+template <typename H, int NW>
+__device__ __forceinline__ void sts_h(uint32_t a, const f32x2 (&x)[NW])
+{
+    uint32_t w[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) w[i] = p_to_h2<H>(x[i]);
+    st_words<NW>(a, w);
+}
+template <typename H>
+__device__ __forceinline__ void pair_h2(f32x2 &x1, f32x2 &x2, f32x2 aw2, f32x2 c2)
+{
+    pair_x2(x1, x2, aw2, c2);
+    x1 = p_round16<H>(x1);
+    x2 = p_round16<H>(x2);
+}
+
+template <typename H, int K>
+__device__ __forceinline__ void block_pass_even_h2(H *xs, const uint8_t *wnib, float alpha, int Q)
+{
+    constexpr int NW = K / 2;          // storage words (replica pairs) per slot
+    constexpr uint32_t E = K * 2;      // bytes per slot
+    const uint32_t a1 = __float_as_uint(alpha), n1 = a1 ^ 0x80000000u;
+    const f32x2 a2 = ((f32x2)a1 << 32) | a1, n2 = ((f32x2)n1 << 32) | n1;
+    const uint32_t qb = (uint32_t)Q * E, qb2 = 2 * qb, qb3 = 3 * qb, step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + threadIdx.x * E;
+    for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
+        const uint32_t wb = __ldg(wnib + f);
+        f32x2 xa[NW], xb[NW], xc[NW], xd[NW];
+        lds_h<H, NW>(ad, xa);
+        lds_h<H, NW>(ad + qb, xb);
+        lds_h<H, NW>(ad + qb2, xc);
+        lds_h<H, NW>(ad + qb3, xd);
+        const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
+        const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+            pair_h2<H>(xa[h], xb[h], w0, kTwo2);
+            pair_h2<H>(xc[h], xd[h], w1, kTwo2);
+            pair_h2<H>(xa[h], xc[h], w2, kTwo2);
+            pair_h2<H>(xb[h], xd[h], w3, kTwo2);
+        }
+        sts_h<H, NW>(ad, xa);
+        sts_h<H, NW>(ad + qb, xb);
+        sts_h<H, NW>(ad + qb2, xc);
+        sts_h<H, NW>(ad + qb3, xd);
+    }
+}
+
+template <typename H, int K, bool kRowWrap, bool kDwt>
+__device__ __forceinline__ void odd_block_h2(uint32_t ad, uint32_t oC, uint32_t oB, uint32_t oA, uint32_t wb,
+                                             uint32_t a1, f32x2 tzc, const f32x2 (&th2)[K / 2],
+                                             const f32x2 (&tk2)[K / 2], const f32x2 (&st2)[K / 2])
+{
+    constexpr int NW = K / 2;
+    constexpr f32x2 tzr = kRowWrap ? kMinusTwo2 : kTwo2;
+    const uint32_t n1 = a1 ^ 0x80000000u;
+    const f32x2 a2 = ((f32x2)a1 << 32) | a1, n2 = ((f32x2)n1 << 32) | n1;
+    f32x2 xd[NW], xc[NW], xb[NW], xa[NW];
+    lds_h<H, NW>(ad, xd);
+    lds_h<H, NW>(ad + oC, xc);
+    lds_h<H, NW>(ad + oB, xb);
+    lds_h<H, NW>(ad + oA, xa);
+    const f32x2 w0 = (wb & 1u) ? n2 : a2, w1 = (wb & 2u) ? n2 : a2;
+    const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
+#pragma unroll
+    for (int h = 0; h < NW; ++h) {
+        // colour 2: D-C, B-A; colour 3: D-B, C-A
+        pair_h2<H>(xd[h], xc[h], w0, tzc);
+        pair_h2<H>(xb[h], xa[h], w1, tzc);
+        pair_h2<H>(xd[h], xb[h], w2, tzr);
+        pair_h2<H>(xc[h], xa[h], w3, tzr);
+        if constexpr (kDwt) {
+            // the twist follows the last colour; the store rounds
+            dwt_x2(xd[h], th2[h], tk2[h], st2[h]);
+            dwt_x2(xc[h], th2[h], tk2[h], st2[h]);
+            dwt_x2(xb[h], th2[h], tk2[h], st2[h]);
+            dwt_x2(xa[h], th2[h], tk2[h], st2[h]);
+            xd[h] = p_wrap(xd[h]);
+            xc[h] = p_wrap(xc[h]);
+            xb[h] = p_wrap(xb[h]);
+            xa[h] = p_wrap(xa[h]);
+        }
+    }
+    sts_h<H, NW>(ad, xd);
+    sts_h<H, NW>(ad + oC, xc);
+    sts_h<H, NW>(ad + oB, xb);
+    sts_h<H, NW>(ad + oA, xa);
+}
+
+template <typename H, int K, bool kFixedColumn, bool kDwt>
+__device__ __forceinline__ void block_pass_odd_h2(H *xs, const uint8_t *wnib, float alpha, int Q, int Wd, int m0,
+                                                  int dm, const float *thc, const float *thc2, const float *stp_)
+{
+    constexpr uint32_t E = K * 2;  // bytes per slot
+    const uint32_t a1 = __float_as_uint(alpha);
+    f32x2 th2[K / 2], tk2[K / 2], st2[K / 2];
+#pragma unroll
+    for (int h = 0; h < K / 2; ++h) {
+        th2[h] = kDwt ? p_pack(thc[2 * h], thc[2 * h + 1]) : 0ull;
+        tk2[h] = kDwt ? p_pack(thc2[2 * h], thc2[2 * h + 1]) : 0ull;
+        st2[h] = kDwt ? p_pack(stp_[2 * h], stp_[2 * h + 1]) : 0ull;
+    }
+    const uint32_t qb = (uint32_t)Q * E;
+    const uint32_t wdb = (uint32_t)Wd * E;
+    const uint32_t rowwrap = (uint32_t)(Wd - Q) * E;
+    const uint32_t step = blockDim.x * E;
+    uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + 3 * qb + threadIdx.x * E;
+    int m = m0;
+    bool cw = (m0 == Wd - 1);
+    uint32_t goffb = cw ? (uint32_t)(1 - Wd) * E : E;
+    const int qlast = Q - Wd;
+    int f = threadIdx.x;
+    for (; f < qlast; f += blockDim.x, ad += step) {
+        if (!kFixedColumn) {
+            cw = (m == Wd - 1);
+            goffb = cw ? (uint32_t)(1 - Wd) * E : E;
+            m += dm;
+            if (m >= Wd) m -= Wd;
+        }
+        const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u);
+        odd_block_h2<H, K, false, kDwt>(ad, goffb - qb, wdb - 2 * qb, goffb + wdb - 3 * qb, wb, a1,
+                                        cw ? kMinusTwo2 : kTwo2, th2, tk2, st2);
+    }
+    for (; f < Q; f += blockDim.x, ad += step) {
+        if (!kFixedColumn) {
+            cw = (m == Wd - 1);
+            goffb = cw ? (uint32_t)(1 - Wd) * E : E;
+            m += dm;
+            if (m >= Wd) m -= Wd;
+        }
+        const uint32_t wb = __ldg(wnib + Q + f) ^ (cw ? 3u : 0u) ^ 12u;
+        odd_block_h2<H, K, true, kDwt>(ad, goffb - qb, rowwrap - 2 * qb, goffb + rowwrap - 3 * qb, wb, a1,
+                                       cw ? kMinusTwo2 : kTwo2, th2, tk2, st2);
+    }
+}
+
 // ---------------------------------------------------------------- fixed point sweep
 // Eq. (6) on the 2^-16-turn grid: with phases held as q << 16, d = x_i - x_j
 // read as int32 is the minimum angular difference (times 2^32) and the
@@ -1827,6 +1994,28 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                     else
                         block_pass_odd_x2_sel<K, false>(xf, v.wnib, at.x, v.Q, v.Wd, m0, dm, dwt, wrap, t.thc, t.thc2,
                                                         t.stp);
+                    __syncthreads();
+                }
+            } else if (sizeof(Store) == 2 && v.paired) {
+                // 16-bit storage: f32x2 lanes over the replica pairs of a word
+                if constexpr (sizeof(Store) == 2) {
+                    block_pass_even_h2<Store, K>(t.xs, v.wnib, at.x, v.Q);
+                    __syncthreads();
+                    if (dm == 0) {
+                        if (dwt)
+                            block_pass_odd_h2<Store, K, true, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, t.thc,
+                                                                    t.thc2, t.stp);
+                        else
+                            block_pass_odd_h2<Store, K, true, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, t.thc,
+                                                                     t.thc2, t.stp);
+                    } else {
+                        if (dwt)
+                            block_pass_odd_h2<Store, K, false, true>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, t.thc,
+                                                                     t.thc2, t.stp);
+                        else
+                            block_pass_odd_h2<Store, K, false, false>(t.xs, v.wnib, at.x, v.Q, v.Wd, m0, dm, t.thc,
+                                                                      t.thc2, t.stp);
+                    }
                     __syncthreads();
                 }
             } else {

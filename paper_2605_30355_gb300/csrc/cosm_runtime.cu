@@ -606,7 +606,8 @@ InstView cosm::inst_view(cosm_handle *h)
     v.energy = h->d_energy.p;
     v.bisB = h->d_bisB.p;
     v.words = (h->g.n + 31) / 32;
-    // the scalar binary32 lattice passes stay available as a cross-check
+    // the scalar lattice passes (binary32 and 16-bit storage) stay available
+    // as a cross-check
     v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : (h->block_pairs ? 2 : 1);
     v.wrap_p = wrap_period(h->prm.alpha0_deg, h->prm.dwt_ratio, h->prm.dwt_period, h->prm.flags, h->mode,
                            h->prm.storage, h->wbound);

@@ -387,6 +387,28 @@ def test_paired_f32_lattice_equals_scalar(cosm, orc, K, flags):
         os.environ.pop("COSM_SCALAR_F32", None)
 
 
+@pytest.mark.parametrize("storage", [1, 3])
+@pytest.mark.parametrize("K,flags", [(2, 0), (4, 0), (8, 0), (4, 4)])
+def test_paired_16bit_lattice_equals_scalar(cosm, orc, storage, K, flags):
+    # binary16 / bfloat16 tiles in f32x2 lanes: every update is wrapped and
+    # rounded through the storage type as in the scalar passes
+    inst = instances.torus2d(24, 32, 5)
+    os.environ["COSM_K"] = str(K)
+    try:
+        s = cosm.Solver.from_instance(inst, flags=flags, dwt_ratio=1.0, storage=storage)
+        assert s.layout()["lattice"] == 2
+        s.run(400, 3 * K, 21)
+        assert s.layout()["K"] == K
+        x_pair, c_pair = s.get_state(), s.replica_cuts()[0]
+        os.environ["COSM_SCALAR_F32"] = "1"
+        s.run(400, 3 * K, 21)
+        assert np.array_equal(s.get_state(), x_pair)
+        assert np.array_equal(s.replica_cuts()[0], c_pair)
+    finally:
+        os.environ.pop("COSM_K", None)
+        os.environ.pop("COSM_SCALAR_F32", None)
+
+
 @pytest.mark.parametrize("L1,L2,threads", [(24, 32, 64), (20, 36, 64), (16, 16, 32), (24, 32, 0), (6, 4, 0),
                                            (10, 28, 96), (8, 30, 0)])
 def test_block_pairs_equal_single_blocks(cosm, orc, L1, L2, threads):
