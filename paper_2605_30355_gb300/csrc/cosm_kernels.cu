@@ -2149,15 +2149,16 @@ __device__ __forceinline__ void run_segment(const InstView &v, const Segment &sg
 // ---------------------------------------------------------------- sweep kernel
 // One instance: CTA b runs its segment list (one whole trial per tile, or
 // the head / tail pieces of the wrap-around schedule).
-// Lattice tiles of up to 4 replicas, and binary32 edge-list tiles of two
-// replicas, may take 1024 threads (one CTA per SM holds a large tile; more
+// Lattice tiles of up to 4 replicas, and binary32 edge-list tiles of two or
+// four replicas, may take 1024 threads (one CTA per SM holds a large tile; more
 // warps hide the dependency and record-load latency) within 64 registers;
 // the others use at most 512 threads and up to 128 registers.
 template <typename Store, int K, int kMode>
 constexpr int max_threads()
 {
-    return ((kMode == MODE_LATTICE2D && K <= 4) || (kMode == MODE_GENERAL && K == 2 && sizeof(Store) == 4)) ? 1024
-                                                                                                           : 512;
+    return ((kMode == MODE_LATTICE2D && K <= 4) || (kMode == MODE_GENERAL && (K == 2 || K == 4) && sizeof(Store) == 4))
+               ? 1024
+               : 512;
 }
 
 template <typename Store, int K, int kMode>

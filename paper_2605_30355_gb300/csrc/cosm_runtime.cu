@@ -473,7 +473,7 @@ int cosm::choose_layout(cosm_handle *h, int replicas)
         const size_t smem = sweep_smem_bytes(p.storage, K, h->g.n, P, mode);
         if (smem > 227 * 1024) continue;
         // thread counts to try: edge-list kernels half a colour class's edges
-        // (at most 512, or 1,024 for binary32 tiles of two replicas); lattice
+        // (at most 512, or 1,024 for binary32 tiles of two or four replicas); lattice
         // kernels the 2x2 blocks of a sublattice, up to 512 or, for tiles of
         // at most 4 replicas, 1024 threads
         int cand[2] = {0, 0};
@@ -489,8 +489,8 @@ int cosm::choose_layout(cosm_handle *h, int replicas)
             if (cand[1] == cand[0]) cand[1] = 0;
         } else {
             cand[0] = std::min(512, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
-            // binary32 tiles of two replicas may also take 1,024 threads
-            if (mode == MODE_GENERAL_ && p.storage == COSM_F32 && K == 2)
+            // binary32 tiles of two or four replicas may also take 1,024 threads
+            if (mode == MODE_GENERAL_ && p.storage == COSM_F32 && (K == 2 || K == 4))
                 cand[1] = std::min(1024, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
             if (cand[1] == cand[0]) cand[1] = 0;
         }
