@@ -438,7 +438,7 @@ def run_ours(args):
 # kernel, from the one-pass ncu capture summarised in
 # profiles/launches_torus20k_bench.md; keyed by (workload, storage,
 # replicas, sweeps). Only the exact configuration captured gets a number.
-DRAM_TRAFFIC = {("torus20k", "f32", 1024, 100_000): 8.66e6 + 73.98e6}
+DRAM_TRAFFIC = {("torus20k", "f32", 1024, 100_000): 8.65e6 + 73.51e6}
 
 # Algorithmic FP32 operations of one edge-replica update (eq. (6) on the
 # minimum angular difference): difference, rounding to the nearest turn,

@@ -1162,7 +1162,7 @@ __device__ __forceinline__ void block_pass_odd_x2(float *xs, const uint8_t *wnib
     uint32_t goffb = cw ? (uint32_t)(1 - Wd) * E : E;
     const int qlast = Q - Wd;  // first block of the last row
     int f = threadIdx.x;
-#pragma unroll 2
+#pragma unroll 5
     for (; f < qlast; f += blockDim.x, ad += step) {
         if (!kFixedColumn) {
             cw = (m == Wd - 1);
