@@ -951,11 +951,6 @@ __device__ __forceinline__ f32x2 p_fma(f32x2 a, f32x2 b, f32x2 c)
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
     return d;
 }
-__device__ __forceinline__ f32x2 p_splat(float a)
-{
-    const uint32_t u = __float_as_uint(a);
-    return ((f32x2)u << 32) | u;
-}
 __device__ __forceinline__ float p_lo(f32x2 v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float p_hi(f32x2 v) { return __uint_as_float((uint32_t)(v >> 32)); }
 __device__ __forceinline__ f32x2 p_fma_rd(f32x2 a, f32x2 b, f32x2 c)
@@ -965,7 +960,6 @@ __device__ __forceinline__ f32x2 p_fma_rd(f32x2 a, f32x2 b, f32x2 c)
     return d;
 }
 constexpr f32x2 kMagic2 = 0x4B4000004B400000ull;  // 1.5 * 2^23 in both lanes
-constexpr f32x2 kSign2 = 0x8000000080000000ull;
 constexpr f32x2 kTwo2 = 0x4000000040000000ull;    // 2 in both lanes
 constexpr f32x2 kMinusTwo2 = 0xC0000000C0000000ull;
 __device__ __forceinline__ f32x2 p_wrap(f32x2 v) { return p_sub(v, p_sub(p_add(v, kMagic2), kMagic2)); }
@@ -1216,16 +1210,6 @@ __device__ __forceinline__ void lds_q2(uint32_t a, f32x2 &x0, f32x2 &x1)
 __device__ __forceinline__ void sts_q2(uint32_t a, f32x2 x0, f32x2 x1)
 {
     asm volatile("st.shared.v2.b64 [%0], {%1, %2};" ::"r"(a), "l"(x0), "l"(x1) : "memory");
-}
-__device__ __forceinline__ f32x2 lds_q1(uint32_t a)
-{
-    f32x2 x;
-    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(x) : "r"(a) : "memory");
-    return x;
-}
-__device__ __forceinline__ void sts_q1(uint32_t a, f32x2 x)
-{
-    asm volatile("st.shared.b64 [%0], %1;" ::"r"(a), "l"(x) : "memory");
 }
 
 __device__ __forceinline__ void block_pass_even_x2p(float *xs, const uint8_t *wnib, float alpha, int Q)
