@@ -1249,9 +1249,10 @@ __device__ __forceinline__ void block_pass_even_x2p(float *xs, const uint8_t *wn
 // The edge-list sweep of binary32 tiles in f32x2 lanes: the two lanes of an
 // instruction carry the two replicas of a pair (tiles of 2 or 4 replicas) or
 // two edges of a thread's batch (single-replica tiles); each lane rounds
-// exactly as the scalar pair_update does, so every tile size gives the same
-// phases. Slots are addressed by 32-bit shared offsets; a batch past the end
-// of its colour loads slot 0 harmlessly and skips its stores.
+// every operation as the scalar instruction does and the wrap cadence below
+// is the same for every tile size, so every tile size gives the same phases.
+// Slots are addressed by 32-bit shared offsets; a batch past the end of its
+// colour loads slot 0 harmlessly and skips its stores.
 // kWrapEach: every update is wrapped (instances whose steps per sweep could
 // carry a phase far from [-1/2, 1/2]); otherwise the phases are wrapped by the
 // pass after the colours on every wrap_p-th sweep.
