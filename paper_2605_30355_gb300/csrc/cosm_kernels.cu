@@ -2030,12 +2030,14 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 // single- and 8-replica tiles keep registers for occupancy
                 if constexpr (sizeof(Store) == 4 && (K == 1 || K == 2 || K == 4)) {
                     // binary32: f32x2 lanes (replica pairs, or edge pairs for
-                    // single-replica tiles without the prefetch)
+                    // single-replica tiles); batches of 4 edges, 2 for tiles
+                    // of four replicas (their registers)
                     float *xf = reinterpret_cast<float *>(t.xs);
+                    constexpr int kB = K == 4 ? 2 : 4;
                     if (v.wrap_p == 0)
-                        general_colours_x2<K, 4, true>(v, xf, at.x);
+                        general_colours_x2<K, kB, true>(v, xf, at.x);
                     else
-                        general_colours_x2<K, 4, false>(v, xf, at.x);
+                        general_colours_x2<K, kB, false>(v, xf, at.x);
                 } else if constexpr (K == 2 || K == 4) {
                     general_colours_pf<Store, K, 4>(v, t.xs, at.x, pf);
                 } else {
