@@ -248,16 +248,30 @@ def _peaks():
 
 # ---------------------------------------------------------------------- ours
 
+def wilson(k, n, z=1.96):
+    """95 % Wilson score interval of a success probability from k of n."""
+    if n <= 0:
+        return [0.0, 1.0]
+    p = k / n
+    d = 1.0 + z * z / n
+    c = (p + z * z / (2 * n)) / d
+    h = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / d
+    return [max(0.0, c - h), min(1.0, c + h)]
+
+
 def success_stats(cuts, target, t_step, R):
-    """P_s, R99 and TTT = t_trial R99 (Appendix A) at the target cut and two
-    slightly lower ones, with t_trial the step time over the replicas."""
+    """P_s with its 95 % Wilson interval, R99 and TTT = t_trial R99
+    (Appendix A) at the target cut and two slightly lower ones, with t_trial
+    the step time over the replicas."""
     allc = np.concatenate(cuts) if isinstance(cuts, list) else np.asarray(cuts)
     out = {"trials": int(allc.size), "best_cut": int(allc.max()), "mean_cut": float(allc.mean()),
            "t_trial_s": t_step / R, "levels": []}
     for tgt in (target, target - 2, target - 4):
-        ps = float((allc >= tgt).mean())
+        k = int((allc >= tgt).sum())
+        ps = k / allc.size
         r = _r99(ps)
-        out["levels"].append({"cut": int(tgt), "P_s": ps, "R99": r if math.isfinite(r) else None,
+        out["levels"].append({"cut": int(tgt), "hits": k, "P_s": ps, "P_s_ci95": wilson(k, allc.size),
+                              "R99": r if math.isfinite(r) else None,
                               "TTT_s": t_step / R * r if math.isfinite(r) else None})
     return out
 
@@ -298,6 +312,29 @@ def measure_single(cosm, inst, col, C, prm, storage, R, S, steps, warmup, seed, 
     else:
         solver.close()
     return out
+
+
+def measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush):
+    """Time-to-target at the oracle's best cut with a longer anneal (Appendix
+    A: TTT = t_trial R99; Table X runs 1-2 x 10^6 sweeps per trial on the
+    20,000-spin torus): R replicas x args.ttt_sweeps sweeps per step, FP32
+    phases, after one short warm-up step."""
+    tgt = _targets().get(args.workload)
+    if tgt is None:
+        return None
+    S = args.ttt_sweeps
+    m = measure_single(cosm, inst, col, C, prm, cosm.F32, R, S, args.ttt_steps, 0, seed + 555, local,
+                       stream, flush)
+    st_ = success_stats(m["cuts"], tgt["cut"], m["t_step"], R)
+    top = st_["levels"][0]
+    return {"sweeps_per_trial": S, "replicas_per_step": R, "steps": args.ttt_steps,
+            "target_cut": tgt["cut"], "target_source": tgt["source"], "trials": st_["trials"],
+            "hits": top["hits"], "P_s": top["P_s"], "P_s_ci95": top["P_s_ci95"], "R99": top["R99"],
+            "t_trial_s": st_["t_trial_s"], "TTT_s": top["TTT_s"],
+            "TTT_s_ci95": [m["t_step"] / R * _r99(p) if 0.0 < p < 1.0 else None
+                           for p in reversed(top["P_s_ci95"])],
+            "best_cut": st_["best_cut"], "mean_cut": st_["mean_cut"], "levels": st_["levels"],
+            "updates_per_s": inst.m * S * R / m["t_step"], "clocks": m["clocks"]}
 
 
 def run_ours(args):
@@ -348,11 +385,13 @@ def run_ours(args):
 
     # ---- the other phase-storage forms and the ragged batch ("batched")
     forms = {}
-    if args.forms and args.workload == "torus20k" and not args.replicas and not args.sweeps:
+    default_shape = args.workload == "torus20k" and not args.replicas and not args.sweeps
+    if args.forms and default_shape:
+        # at least 10 steps (10,240 trials) per form for its success rate
         for name, st in (("f16", cosm.F16), ("q16", cosm.Q16), ("bf16", cosm.BF16)):
             if st == storage:
                 continue
-            f = measure_single(cosm, inst, col, C, prm, st, R, S, max(2, args.steps // 2), 1, seed,
+            f = measure_single(cosm, inst, col, C, prm, st, R, S, max(10, args.steps // 2), 1, seed,
                                local, stream, flush)
             forms[name] = {"value": whole_job_rate(updates, ws, max_over_ranks(f["t_step"], "cuda")),
                            "unit": "updates/s", "ms_per_step": f["t_step"] * 1000.0,
@@ -363,10 +402,20 @@ def run_ours(args):
             tgt = _targets().get(args.workload)
             if tgt is not None:
                 forms[name]["success"] = success_stats(f["cuts"], tgt["cut"], f["t_step"], R)
+            forms[name]["speedup_vs_f32_plain"] = t_step / f["t_step"]
     batched = None
-    if args.forms and args.workload == "torus20k" and not args.replicas and not args.sweeps:
-        batched = measure_batch(cosm, args, rank, ws, local, stream, flush, steps=2, warmup=1,
-                                e2e=False)
+    if args.forms and default_shape:
+        # the ragged batch in each 2-byte form beside binary32
+        batched = {}
+        for name, st in (("f32", cosm.F32), ("f16", cosm.F16), ("q16", cosm.Q16)):
+            batched[name] = measure_batch(cosm, args, rank, ws, local, stream, flush, steps=2, warmup=1,
+                                          e2e=True, storage=st)
+        f32v = batched["f32"]["value"]
+        for name in ("f16", "q16"):
+            batched[name]["speedup_vs_f32_batch"] = batched[name]["value"] / f32v
+    long_ttt = None
+    if args.ttt_steps and default_shape:
+        long_ttt = measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush)
 
     # ---- the best state over all ranks (untimed): one max-reduce, one broadcast
     solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, **prm)
@@ -387,16 +436,13 @@ def run_ours(args):
         st_ = success_stats(m["cuts"], tgt["cut"], t_step, R)
         top = st_["levels"][0]
         ttt = {"target_cut": tgt["cut"], "target_source": tgt["source"], "P_s": top["P_s"],
-               "trials": st_["trials"], "R99": top["R99"], "t_trial_s": st_["t_trial_s"],
+               "P_s_ci95": top["P_s_ci95"], "trials": st_["trials"], "R99": top["R99"],
+               "t_trial_s": st_["t_trial_s"],
                "TTT_s": top["TTT_s"], "best_cut": st_["best_cut"], "mean_cut": st_["mean_cut"],
                "levels": st_["levels"]}
 
     # ---- roofline of the sweep kernel: shared memory and FP32 issue
     roof = roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks)
-    traffic = DRAM_TRAFFIC.get((args.workload, args.storage, R, S))
-    if traffic is not None:
-        roof["traffic"] = traffic
-        roof["traffic_source"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum, one full-size launch"
 
     line = {
         "metric": metric_name(args.workload),
@@ -421,6 +467,7 @@ def run_ours(args):
         "clocks": clocks,
         "roofline": roof,
         "time_to_target": ttt,
+        "time_to_target_long": long_ttt,
         "forms": forms or None,
         "batched": batched,
         "paper_context": {"updates_per_s": 1.41e10, "hardware": "2x Xeon Gold 6544Y, 64 threads, FP32",
@@ -434,64 +481,111 @@ def run_ours(args):
     return line
 
 
-# DRAM bytes (read + write) of one full-size launch of the headline sweep
-# kernel, from the one-pass ncu capture summarised in
-# profiles/launches_torus20k_bench.md; keyed by (workload, storage,
-# replicas, sweeps). Only the exact configuration captured gets a number.
-DRAM_TRAFFIC = {("torus20k", "f32", 1024, 100_000): 8.65e6 + 73.51e6}
+# ncu records of the kernels' memory traffic, each taken at the kernel source
+# whose hash it names (the first 12 hex digits of the SHA-256 of
+# cosm_kernels.cu): reported only while that source is unchanged, else null.
+# Keys: (kernel, storage, K). Values: shared-memory bytes per edge-replica
+# update (shared wavefronts x 128 B / updates), DRAM bytes (read + write)
+# per update, source hash.
+NCU_TRAFFIC = {}
 
-# Algorithmic FP32 operations of one edge-replica update (eq. (6) on the
-# minimum angular difference): difference, rounding to the nearest turn,
-# subtraction, sign select, two phase updates, two wraps (round + subtract).
-ALU_OPS_PER_UPDATE = 10
-FP32_LANES_PER_SM = 128
+# Algorithmic cost of one edge-replica update of eq. (6): FP32 operations
+# (the difference, the biased sign, two phase updates, two wraps) and, per
+# phase byte b, the shared-memory bytes 4b of two reads and two writes.
+ALU_OPS_PER_UPDATE = 6
 
 
-def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks):
-    """Shared-memory and FP32-issue rooflines of the sweep kernel.
+def kernel_source_hash():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2605_30355_gb300", "csrc", "cosm_kernels.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
 
-    Shared-memory bytes per update: the implicit-index lattice kernel loads
-    and stores each phase once per 2x2 block, i.e. 2 phases moved per edge
-    (2b bytes, b = bytes per phase, DWT fused); the edge-list kernel loads
-    and stores both endpoints per edge (4b) plus a DWT pass over all phases
-    every dwt_period sweeps (2b n / (m dwt_period)). The kernel that
-    dominates the step is the sweep kernel (one launch per step; the
-    finaliser is microseconds), so the step time is its launch duration."""
+
+_PROBES = {}
+
+
+def probes(cosm):
+    """Measured shared-memory bandwidth (bytes per SM clock) and FP32 issue
+    rates (operations per SM clock, scalar and packed f32x2), once per run."""
+    if not _PROBES:
+        bpc, _ = cosm.probe_smem(4096)
+        sc, pk = cosm.probe_fp32(2048)
+        _PROBES.update(smem_bpc=bpc, fp32_scalar=sc, fp32_packed=pk)
+    return _PROBES
+
+
+def algorithmic_bytes(inst, prm, storage_bytes, lattice, K):
+    """Shared-memory bytes of one edge-replica update by the method's own
+    count: 4b (two phase reads and two writes) + 2b n / (m P_dwt) (the twist
+    reads and writes every phase once per period) + e / K (one edge record
+    of e bytes serves the K replicas of a tile; the implicit-index lattice
+    needs one weight bit per edge)."""
+    b = storage_bytes
+    dwt = (2.0 * b * inst.n) / (inst.m * prm["dwt_period"]) if prm.get("dwt_period", 0) > 0 else 0.0
+    e = 0.125 if lattice == 2 else 5.0
+    return 4.0 * b + dwt + e / max(1, K)
+
+
+def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks, kernel="sweep"):
+    """Rooflines of the sweep kernel, which is the whole timed step but for a
+    finaliser of microseconds, so the step time is its launch duration:
+    - smem (the bound of the method's own count): algorithmic shared-memory
+      bytes per update against the measured shared-memory bandwidth;
+    - alu: 6 FP32 operations per update against the measured FP32 issue rate
+      (the larger of scalar and packed f32x2 fused multiply-adds);
+    - smem_measured: the kernel's own shared-memory traffic from ncu, where a
+      record for the current kernel source exists (the lattice kernel applies
+      two colours per load and store of a phase, so it moves fewer bytes than
+      the method's count)."""
     import torch
-    bpc, smem_gbps = cosm.probe_smem(4096)
-    b = 4 if storage == cosm.F32 else 2  # binary16 and u16 fixed point are 2 bytes
-    if layout["lattice"] == 2:
-        per_update = 2.0 * b
-    else:
-        per_update = 4.0 * b + (2.0 * b * inst.n) / (inst.m * max(1, prm["dwt_period"]))
-    smem_ach = per_update * updates / t_step / 1e9
+    pr = probes(cosm)
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    sms = props.multi_processor_count
     mhz = clocks.get("sm_mhz") or 2070.0
-    alu_peak = FP32_LANES_PER_SM * props.multi_processor_count * mhz * 1e6 / 1e12
-    alu_ach = ALU_OPS_PER_UPDATE * updates / t_step / 1e12
-    smem = {"bound": "smem", "achieved": smem_ach, "peak": smem_gbps, "unit": "GB/s",
-            "frac": smem_ach / smem_gbps, "traffic": None, "bytes_per_update": per_update,
-            "peak_source": f"measured shared-memory read bandwidth ({bpc:.1f} B/clk/SM)"}
-    alu = {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s",
-           "frac": alu_ach / alu_peak, "traffic": None, "ops_per_update": ALU_OPS_PER_UPDATE,
-           "peak_source": f"{FP32_LANES_PER_SM} FP32 lanes/SM x {props.multi_processor_count} SMs "
-                          f"x {mhz:.0f} MHz (median sampled SM clock)"}
-    main, other = (alu, smem) if alu["frac"] >= smem["frac"] else (smem, alu)
-    main = dict(main)
-    main["other"] = other
-    return main
+    b = 4 if storage == cosm.F32 else 2
+    K = layout["K"]
+    per_update = algorithmic_bytes(inst, prm, b, layout["lattice"], K)
+    smem_peak = pr["smem_bpc"] * sms * mhz * 1e6 / 1e9
+    rate = updates / t_step
+    smem = {"bound": "smem", "achieved": per_update * rate / 1e9, "peak": smem_peak, "unit": "GB/s",
+            "frac": per_update * rate / 1e9 / smem_peak, "bytes_per_update": per_update,
+            "peak_source": f"measured shared-memory read bandwidth ({pr['smem_bpc']:.1f} B/clk/SM) x {sms} "
+                           f"SMs x {mhz:.0f} MHz (median sampled SM clock), of measured"}
+    ops_clk = max(pr["fp32_scalar"], pr["fp32_packed"])
+    alu_peak = ops_clk * sms * mhz * 1e6 / 1e12
+    smem["alu"] = {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * rate / 1e12, "peak": alu_peak,
+                   "unit": "Tops/s", "frac": ALU_OPS_PER_UPDATE * rate / 1e12 / alu_peak,
+                   "ops_per_update": ALU_OPS_PER_UPDATE,
+                   "peak_source": f"measured FP32 issue rate: {pr['fp32_scalar']:.1f} ops/clk/SM scalar fma, "
+                                  f"{pr['fp32_packed']:.1f} packed f32x2 fma; x {sms} SMs x {mhz:.0f} MHz, "
+                                  "of measured"}
+    key = (kernel + ("_lattice" if layout["lattice"] == 2 else "_edges"),
+           {cosm.F32: "f32", cosm.F16: "f16", cosm.Q16: "q16", cosm.BF16: "bf16"}[storage], K)
+    rec = NCU_TRAFFIC.get(key)
+    src = kernel_source_hash()
+    smem["traffic"] = None
+    smem["smem_measured"] = None
+    if rec is not None and rec[2] == src:
+        smem["smem_measured"] = {"bytes_per_update": rec[0], "achieved": rec[0] * rate / 1e9,
+                                 "frac": rec[0] * rate / 1e9 / smem_peak,
+                                 "source": "ncu shared wavefronts x 128 B per update, kernel source " + rec[2]}
+        smem["traffic"] = rec[1] * updates
+        smem["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per update, scaled to "
+                                  "one launch; kernel source " + rec[2])
+    return smem
 
 
 # ---------------------------------------------------------------------- batch
 
-def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e=True):
+def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e=True, storage=None):
     """The ragged batch: every step is one cosm_batch_run over all instances."""
     import torch
     _, _, S, prm, desc = WORKLOADS["batch512"]
     if args.workload == "batch512" and args.sweeps:
         S = args.sweeps
-    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16, "bf16": cosm.BF16}[args.storage] \
-        if args.workload == "batch512" else cosm.F32
+    if storage is None:
+        storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16, "bf16": cosm.BF16}[args.storage]
     insts, reps = instances.ragged_batch(512, seed=0)
     seeds = np.arange(len(insts), dtype=np.uint64) + np.uint64(rank_seed(1, rank))
     t0 = time.perf_counter()
@@ -537,21 +631,33 @@ def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e
         e2e_t = max_over_ranks(time.perf_counter() - t0, "cuda")
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     mhz = clocks.get("sm_mhz") or 2070.0
-    alu_peak = FP32_LANES_PER_SM * props.multi_processor_count * mhz * 1e6 / 1e12
-    alu_ach = ALU_OPS_PER_UPDATE * updates / t_step / 1e12
+    pr = probes(cosm)
+    sms = props.multi_processor_count
+    b = 4 if storage == cosm.F32 else 2
+    algo = sum(int(i.m) * S * r * algorithmic_bytes(i, prm, b, 2 if i.dims and len(i.dims) == 2 else 0,
+                                                    1) for i, r in zip(insts, reps)) / updates
+    smem_peak = pr["smem_bpc"] * sms * mhz * 1e6 / 1e9
+    ops_clk = max(pr["fp32_scalar"], pr["fp32_packed"])
+    alu_peak = ops_clk * sms * mhz * 1e6 / 1e12
+    rate = updates / t_step
+    sname = {cosm.F32: "f32", cosm.F16: "f16", cosm.Q16: "q16", cosm.BF16: "bf16"}[storage]
     return {
         "value": whole_job_rate(updates, ws, t_max), "unit": "updates/s", "ms_per_step": t_max * 1000.0,
-        "storage": args.storage if args.workload == "batch512" else "f32",
+        "storage": sname,
         "description": desc, "instances": len(insts), "replicas_total": int(sum(reps)),
         "sweeps_per_trial": S, "edges_total": int(sum(i.m for i in insts)), "batch": info,
         "create_s": create_s, "steps": steps, "warmup": warmup, "clocks": clocks,
         "e2e": None if e2e_t is None else {
             "value": whole_job_rate(updates, ws, e2e_t), "unit": "updates/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "api": "cosm_batch_create + cosm_batch_run + get_best (host buffers)"},
-        "roofline": {"bound": "alu", "achieved": alu_ach, "peak": alu_peak, "unit": "Tops/s",
-                     "frac": alu_ach / alu_peak, "traffic": None, "ops_per_update": ALU_OPS_PER_UPDATE,
-                     "peak_source": f"{FP32_LANES_PER_SM} FP32 lanes/SM x {props.multi_processor_count} "
-                                    f"SMs x {mhz:.0f} MHz (median sampled SM clock)"},
+        "roofline": {"bound": "smem", "achieved": algo * rate / 1e9, "peak": smem_peak, "unit": "GB/s",
+                     "frac": algo * rate / 1e9 / smem_peak, "traffic": None, "bytes_per_update": algo,
+                     "peak_source": f"measured shared-memory bandwidth ({pr['smem_bpc']:.1f} B/clk/SM) x "
+                                    f"{sms} SMs x {mhz:.0f} MHz, of measured; bytes per update by the "
+                                    "method's count at one replica per edge record",
+                     "alu": {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * rate / 1e12, "peak": alu_peak,
+                             "unit": "Tops/s", "frac": ALU_OPS_PER_UPDATE * rate / 1e12 / alu_peak,
+                             "ops_per_update": ALU_OPS_PER_UPDATE}},
     }
 
 
@@ -578,7 +684,8 @@ def run_batch(args):
         "value": b["value"], "unit": "updates/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f32": "f32", "f16": "f16-storage/f32-compute", "q16": "u16-fixed-point"}[b["storage"]],
+        "dtype": {"f32": "f32", "f16": "f16-storage/f32-compute", "q16": "u16-fixed-point",
+                  "bf16": "bf16-storage/f32-compute"}[b["storage"]],
         "data": "synthetic (seeded instance generator; no Gset files)",
         "config": {"workload": "batch512", "description": b["description"], "instances": b["instances"],
                    "replicas_total": b["replicas_total"], "sweeps_per_trial": b["sweeps_per_trial"],
@@ -804,7 +911,12 @@ def run_serve(args):
     if rank != 0:
         return None
     _, R, S, prm, desc = WORKLOADS[args.workload]
-    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16, "bf16": cosm.BF16}[args.storage]
+    # the serving workload stores phases in binary16 unless --storage names another form
+    sname = args.storage if args.storage_given else "f16"
+    storage = {"f32": cosm.F32, "f16": cosm.F16, "q16": cosm.Q16, "bf16": cosm.BF16}[sname]
+    desc = desc.replace("FP16 phase storage", {"f32": "FP32 phases", "f16": "FP16 phase storage",
+                                              "q16": "u16 fixed-point phases",
+                                              "bf16": "bfloat16 phase storage"}[sname])
     pool = serve_pool()
     rate, window, max_trials = 50.0, args.serve_seconds, 4
     arr = instances.Stream(77, tag=10)
@@ -833,8 +945,14 @@ def run_serve(args):
     st = srv.stats()
     srv.close()
     reached = [r for r in res if r["status"] == cosm.REACHED]
-    ttt = np.array([r["ttt"] for r in reached]) if reached else np.array([])
+    # percentiles over all requests: one that used up its trials without
+    # reaching the planted optimum has no time-to-target (infinite)
+    ttt_all = np.array([r["ttt"] if r["status"] == cosm.REACHED else np.inf for r in res])
     updates = sum(int(r["updates"]) for r in res)
+
+    def pct(q):
+        v = float(np.percentile(ttt_all, q, method="higher")) if len(ttt_all) else math.inf
+        return v if math.isfinite(v) else None
     line = {
         "metric": "serving: requests/s and time-to-target p50/p99 (planted instances)",
         "value": len(res) / t_total, "unit": "requests/s", "n_gpus": 1, "steps": 1, "warmup": 1,
@@ -845,9 +963,14 @@ def run_serve(args):
         "config": {"workload": "serve", "description": desc, "pool": [(i.n, i.m, len(i.dims)) for i in pool],
                    "requests": len(res), "arrival_rate": rate, "window_s": window,
                    "server": {"memory_budget": 48 << 30, "max_active": 256, "chunk_sweeps": 500}},
-        "serving": {"reached": len(reached), "exhausted": len(res) - len(reached),
-                    "ttt_p50_s": float(np.percentile(ttt, 50)) if len(ttt) else None,
-                    "ttt_p99_s": float(np.percentile(ttt, 99)) if len(ttt) else None,
+        "serving": {"requests": len(res), "reached": len(reached), "exhausted": len(res) - len(reached),
+                    "reached_fraction": len(reached) / max(1, len(res)),
+                    "ttt_p50_s": pct(50), "ttt_p99_s": pct(99),
+                    "percentiles_over": "all requests; one that used up its trials without reaching the "
+                                        "planted optimum counts as never reached (null: the percentile "
+                                        "falls among those)",
+                    "ttt_p50_s_reached_only": float(np.percentile(ttt_all[np.isfinite(ttt_all)], 50))
+                    if len(reached) else None,
                     "updates_per_s": updates / t_total, "stats": st},
         "clocks": clocks,
     }
@@ -954,7 +1077,13 @@ def main(argv=None):
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="default workload: skip the FP16 / fixed-point forms and the ragged batch")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window")
+    ap.add_argument("--ttt-steps", type=int, default=2,
+                    help="default workload: steps of the long-anneal time-to-target leg (0 skips it)")
+    ap.add_argument("--ttt-sweeps", type=int, default=1_000_000,
+                    help="sweeps per trial of the long-anneal time-to-target leg")
     args = ap.parse_args(argv)
+    argl = sys.argv[1:] if argv is None else list(argv)
+    args.storage_given = any(a == "--storage" or a.startswith("--storage=") for a in argl)
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch512":

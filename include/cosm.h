@@ -148,10 +148,31 @@ void cosm_destroy(cosm_handle *h);
 /* Runs one full trial (Alg. 1) for each of `replicas` replicas: random
  * phases, `sweeps` sweeps (each: C sub-sweeps in colour order, then the DWT
  * when sweep % dwt_period == 0, then the step update), then the bisector
- * readout with exact int64 cuts and best-state tracking. Asynchronous on
- * `stream`. sweeps in [1, 2^31), replicas in [1, 2^24).
- * Errors: INVALID_ARG, TOO_LARGE, CUDA, NOMEM. */
-int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64_t seed, void *stream);
+ * readout with exact int64 cuts and best-state tracking. target_cut is the
+ * success threshold of Appendix A's P_s: the run counts the replicas whose
+ * kept cut is >= target_cut (cosm_get_success); INT64_MIN counts every
+ * replica. Asynchronous on `stream`. sweeps in [1, 2^31), replicas in
+ * [1, 2^24). Errors: INVALID_ARG, TOO_LARGE, CUDA, NOMEM. */
+int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64_t seed, int64_t target_cut,
+             void *stream);
+
+/* Part of a trial: sweeps s_from..s_to (1 <= s_from <= s_to <= sweeps) of
+ * a `sweeps`-sweep trial, with the step schedule of the whole trial (Table
+ * IX's linear ramp over `sweeps`). s_from == 1 starts the trial from the
+ * seed's random phases, as cosm_run; s_from > 1 continues the current
+ * state, which must have reached sweep s_from - 1 (by an earlier range or
+ * cosm_import_state; else COSM_ERR_STATE) with the same replica count and
+ * seed (else INVALID_ARG). The range that ends at s_to == sweeps reads out
+ * as cosm_run does, with target_cut as there; earlier ranges only sweep.
+ * Splitting a trial into ranges gives the same phases and cuts, bit for
+ * bit, as one cosm_run. Asynchronous on `stream`. */
+int cosm_run_range(cosm_handle *h, int64_t sweeps, int64_t s_from, int64_t s_to, int32_t replicas,
+                   uint64_t seed, int64_t target_cut, void *stream);
+
+/* Number of replicas of the last readout whose kept cut reached the run's
+ * target_cut (Appendix A: P_s = count / replicas). Synchronises.
+ * COSM_ERR_STATE before a readout. */
+int cosm_get_success(cosm_handle *h, int64_t *count);
 
 /* Waits for the handle's last launch and reports device-side errors
  * (COSM_ERR_TIMEOUT if a bounded wait between work segments gave up). */
@@ -195,8 +216,43 @@ int cosm_get_state(cosm_handle *h, double *phases);
 
 /* Replaces the state with `replicas` x n phases (FP64 turns, [replica]
  * [vertex], host or device), rounded to nearest into the storage type, and
- * sets the seed used by cosm_step for DWT angles. Used to replay states. */
+ * sets the seed used by cosm_step for DWT angles (sweep index 0). Used to
+ * replay states. */
 int cosm_set_state(cosm_handle *h, const double *phases, int32_t replicas, uint64_t seed);
+
+/* Checkpoint of the state in its own storage type (no counterpart in the
+ * paper; the state of Alg. 1 between sweeps). Export writes replicas x n
+ * elements [replica][vertex] in original vertex order to `phases` (host or
+ * device): float for COSM_F32, the 16-bit words of binary16 / bfloat16 /
+ * the 2^-16-turn fixed point otherwise; `storage` must be the handle's
+ * (else INVALID_ARG). *sweep_idx (may be NULL) gets the number of sweeps of
+ * the current trial the state has had. Binary32 phases are exported as
+ * stored: a representative of the turn that may lie outside [0, 1).
+ * Import replaces the state with such a checkpoint, with its replica
+ * count, seed (for the remaining DWT angles) and sweep index; a
+ * cosm_run_range from sweep_idx + 1 then continues the trial. On a handle
+ * created from the same graph and parameters the continuation equals the
+ * uninterrupted trial bit for bit. Export synchronises. */
+int cosm_export_state(cosm_handle *h, void *phases, int32_t storage, int64_t *sweep_idx);
+int cosm_import_state(cosm_handle *h, const void *phases, int32_t storage, int32_t replicas, uint64_t seed,
+                      int64_t sweep_idx);
+
+/* Failure detection (no counterpart in the paper). A trial split between
+ * two CTAs hands its state over through global memory; the CTA running the
+ * tail waits for the head's ready flag for at most `seconds` (default: the
+ * environment variable COSM_WAIT_LIMIT_S, else 20 s), then gives up on that
+ * tile, sets the handle's error word and returns; cosm_sync then reports
+ * COSM_ERR_TIMEOUT and the handle stays usable. INVALID_ARG outside
+ * (0, 3600]. */
+int cosm_set_wait_limit(cosm_handle *h, double seconds);
+
+/* Host-side fault injection for testing the bounded waits: with
+ * COSM_FAULT_DROP_SIGNAL the next run's split tiles do not publish their
+ * ready flags, so every tail's wait runs out (COSM_ERR_TIMEOUT at
+ * cosm_sync, after the wait limit); the run after that is normal. 0 clears
+ * it. Nothing faults on the device: the kernel only stops waiting. */
+#define COSM_FAULT_DROP_SIGNAL 1
+int cosm_inject_fault(cosm_handle *h, int32_t kind);
 
 /* Applies exactly one sweep with index `sweep` (1-based; the DWT fires when
  * sweep % dwt_period == 0) and step `alpha` (turns, FP32) to every replica
@@ -396,6 +452,17 @@ int cosm_qubo_to_ising(int32_t n, int64_t nnz, const int32_t *qi, const int32_t 
  * memory and synchronises the device. */
 int cosm_probe_smem(int32_t iters, double *bytes_per_clk_per_sm, double *gbps);
 
+/* Measurement support (no counterpart in the paper): the FP32 arithmetic
+ * issue rate of the current device, for the arithmetic roofline of the
+ * sweep kernels. Two CTAs of 1024 threads per SM run 8 independent chains
+ * of fused multiply-adds per thread, iters x 8 per chain: scalar
+ * fma.rn.f32 (one operation per lane) and packed fma.rn.f32x2 (two
+ * operations per lane). Outputs FP32 operations per SM clock per SM for
+ * each form (either pointer may be NULL). Allocates 12 bytes of device
+ * memory and synchronises the device. Errors: INVALID_ARG (iters < 1),
+ * CUDA, NOMEM. */
+int cosm_probe_fp32(int32_t iters, double *ops_per_clk_per_sm, double *ops_per_clk_per_sm_packed);
+
 /* No-allocation run, for callers that cannot allocate device memory (code
  * inside a host application that owns every device allocation, a plugin
  * with no allocator, a process whose device memory is already committed).
@@ -404,8 +471,11 @@ int cosm_probe_smem(int32_t iters, double *bytes_per_clk_per_sm, double *gbps);
  * weights, the step table, the work list and an error word -- held in a
  * fixed static device array of COSM_STATIC_SCRATCH_BYTES that every GPU
  * loading the library keeps until the process exits. It needs
- *   5 m + 4 n + 8 sweeps + 28 ceil(replicas / tile) bytes
- * (each part rounded up to 256 bytes); larger problems fail with
+ *   5 m + 4 n + 8 sweeps + 28 ceil(replicas / tile) + 4 (C + 1) + 8 bytes
+ * (C colours; tile = 1 replica for COSM_F32, 2 for COSM_F16), in eight
+ * parts -- records 4 m, weights m, vertex ids 4 n, step table 8 sweeps,
+ * work list 24 and offsets 4 per tile plus 4, error word 4, colour offsets
+ * 4 (C + 1) -- each rounded up to 256 bytes; larger problems fail with
  * COSM_ERR_TOO_LARGE before any device work. It calls no cudaMalloc or
  * cudaFree. Inputs are host arrays as for cosm_create (the lattice hint is
  * ignored; color may be NULL for the greedy colouring; no local fields,
@@ -413,7 +483,11 @@ int cosm_probe_smem(int32_t iters, double *bytes_per_clk_per_sm, double *gbps);
  * track_period 0, else COSM_ERR_INVALID_ARG); outputs are
  * caller-owned DEVICE buffers of `replicas` entries: each replica's best
  * cut and best bisector index, the same values cosm_run + cosm_get_replica_cuts
- * give for that graph without a lattice hint. Asynchronous on `stream`.
+ * give for that graph without a lattice hint. Both must be device (or
+ * managed) memory of the current device, else COSM_ERR_INVALID_ARG before
+ * any device work. Asynchronous on `stream`; a stream that is capturing is
+ * refused with COSM_ERR_INVALID_ARG (the scratch is filled from host
+ * tables that are released when the call returns).
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture. All calls share the array and it keeps the last call's contents:

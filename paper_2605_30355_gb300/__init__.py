@@ -39,6 +39,8 @@ NO_DWT = 1
 NO_SCS = 2
 DWT_RANDOM_DIR = 4
 OPT_BISECTOR = 8
+FAULT_DROP_SIGNAL = 1
+NO_TARGET = -(1 << 63)  # INT64_MIN: every replica counts as a success
 
 #: every symbol include/cosm.h declares
 EXPORTS = (
@@ -51,7 +53,9 @@ EXPORTS = (
     "cosm_batch_info", "cosm_batch_destroy", "cosm_server_default_config", "cosm_server_create",
     "cosm_server_submit", "cosm_server_poll", "cosm_server_wait", "cosm_server_get_spins",
     "cosm_server_stats", "cosm_server_destroy", "cosm_last_error", "cosm_get_replica_energies",
-    "cosm_get_replica_bisectors", "cosm_get_trace", "cosm_qubo_to_ising",
+    "cosm_get_replica_bisectors", "cosm_get_trace", "cosm_qubo_to_ising", "cosm_probe_fp32",
+    "cosm_run_range", "cosm_get_success", "cosm_export_state", "cosm_import_state",
+    "cosm_set_wait_limit", "cosm_inject_fault",
 )
 
 
@@ -98,7 +102,14 @@ def _load():
         "cosm_default_params": (None, [P]),
         "cosm_create": (C.c_int, [P, P, P]),
         "cosm_destroy": (None, [P]),
-        "cosm_run": (C.c_int, [P, i64, i32, u64, P]),
+        "cosm_run": (C.c_int, [P, i64, i32, u64, i64, P]),
+        "cosm_run_range": (C.c_int, [P, i64, i64, i64, i32, u64, i64, P]),
+        "cosm_get_success": (C.c_int, [P, P]),
+        "cosm_export_state": (C.c_int, [P, P, i32, P]),
+        "cosm_import_state": (C.c_int, [P, P, i32, i32, u64, i64]),
+        "cosm_set_wait_limit": (C.c_int, [P, C.c_double]),
+        "cosm_inject_fault": (C.c_int, [P, i32]),
+        "cosm_probe_fp32": (C.c_int, [i32, P, P]),
         "cosm_sync": (C.c_int, [P]),
         "cosm_get_best": (C.c_int, [P, P, P, P, P]),
         "cosm_get_replica_cuts": (C.c_int, [P, P, P]),
@@ -246,10 +257,51 @@ class Solver:
         except Exception:
             pass
 
-    def run(self, sweeps, replicas, seed, stream=None):
+    def run(self, sweeps, replicas, seed, stream=None, target=None):
+        """cosm_run: one trial per replica; `target` is the success cut
+        (cosm_get_success counts the replicas that reach it)."""
         self.replicas = int(replicas)
         self.sweeps = int(sweeps)
-        _check(_lib.cosm_run(self._h, int(sweeps), int(replicas), int(seed), _stream(stream)))
+        _check(_lib.cosm_run(self._h, int(sweeps), int(replicas), int(seed),
+                             NO_TARGET if target is None else int(target), _stream(stream)))
+
+    def run_range(self, sweeps, s_from, s_to, replicas, seed, stream=None, target=None):
+        """cosm_run_range: sweeps s_from..s_to of a `sweeps`-sweep trial."""
+        self.replicas = int(replicas)
+        self.sweeps = int(sweeps)
+        _check(_lib.cosm_run_range(self._h, int(sweeps), int(s_from), int(s_to), int(replicas), int(seed),
+                                   NO_TARGET if target is None else int(target), _stream(stream)))
+
+    def success(self):
+        """Replicas of the last readout whose cut reached the run's target."""
+        c = C.c_int64()
+        _check(_lib.cosm_get_success(self._h, C.byref(c)))
+        return int(c.value)
+
+    def export_state(self):
+        """cosm_export_state: (phases in the storage type [replica][vertex],
+        sweep index)."""
+        dt = np.float32 if self.params.storage == F32 else np.uint16
+        x = np.zeros((self.replicas, self.n), dtype=dt)
+        idx = C.c_int64()
+        _check(_lib.cosm_export_state(self._h, _p(x), int(self.params.storage), C.byref(idx)))
+        return x, int(idx.value)
+
+    def import_state(self, phases, replicas, seed, sweep_idx):
+        """cosm_import_state: a checkpoint from export_state."""
+        dt = np.float32 if self.params.storage == F32 else np.uint16
+        x = np.ascontiguousarray(phases, dtype=dt)
+        if x.size != int(replicas) * self.n:
+            raise ValueError("checkpoint size does not match replicas x n")
+        self.replicas = int(replicas)
+        _check(_lib.cosm_import_state(self._h, _p(x), int(self.params.storage), int(replicas), int(seed),
+                                      int(sweep_idx)))
+
+    def set_wait_limit(self, seconds):
+        _check(_lib.cosm_set_wait_limit(self._h, float(seconds)))
+
+    def inject_fault(self, kind):
+        _check(_lib.cosm_inject_fault(self._h, int(kind)))
 
     def replica_energies(self):
         out = np.zeros(self.replicas, dtype=np.int64)
@@ -476,10 +528,27 @@ def solve_static(n, src, dst, w, sweeps, replicas, seed, cuts_out, best_p_out, c
     """cosm_solve_static: no device allocation inside the library. cuts_out
     (int64) and best_p_out (int32) are caller-owned device buffers of
     `replicas` entries, e.g. torch tensors on the current device."""
+    import torch
+    dev = torch.cuda.current_device()
+    for name, t, dt in (("cuts_out", cuts_out, torch.int64), ("best_p_out", best_p_out, torch.int32)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device")
+        if t.dtype != dt or not t.is_contiguous() or t.numel() < int(replicas):
+            raise ValueError(f"{name} must be a contiguous {dt} tensor of at least {int(replicas)} entries")
+    if stream is None:
+        stream = torch.cuda.current_stream()
     prm = params if params is not None else default_params(**kw)
     desc, keep = _desc(n, src, dst, w, color, n_colors, ())
     _check(_lib.cosm_solve_static(C.byref(desc), C.byref(prm), int(sweeps), int(replicas), int(seed),
                                   _p(cuts_out), _p(best_p_out), _stream(stream)))
+
+
+def probe_fp32(iters=4096):
+    """Measured FP32 issue rate: (scalar, packed f32x2) FP32 operations per
+    SM clock per SM (cosm_probe_fp32)."""
+    a, b = C.c_double(), C.c_double()
+    _check(_lib.cosm_probe_fp32(int(iters), C.byref(a), C.byref(b)))
+    return float(a.value), float(b.value)
 
 
 def probe_smem(iters=4096):

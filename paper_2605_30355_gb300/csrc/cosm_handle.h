@@ -104,7 +104,7 @@ struct cosm_handle {
     double alpha_a0 = -1, alpha_ratio = -1;
     std::vector<cosm::Segment> h_segs;
     std::vector<int32_t> h_segoff;
-    int64_t sched_tiles = -1, sched_S = -1, sched_G = -1;
+    int64_t sched_tiles = -1, sched_S = -1, sched_G = -1, sched_s0 = -1, sched_s1 = -1;
     bool segs_uploaded = false;
     // state of the last launch
     int replicas = 0;
@@ -113,6 +113,10 @@ struct cosm_handle {
     size_t smem = 0;
     int64_t tile_stride = 0;  // storage elements per tile
     uint64_t seed = 0;
+    int64_t sweep_idx = 0;          // sweeps of the current trial applied to the state
+    int64_t target = INT64_MIN;     // success threshold of the last run's cuts
+    uint64_t wait_limit_ns = 0;     // bounded waits between segments (0: environment / 20 s)
+    int32_t fault = 0;              // host-side fault injection for the next run (COSM_FAULT_*)
     bool have_state = false, have_result = false;
     cudaStream_t stream = nullptr;
     int launches = 0;

@@ -142,7 +142,7 @@ int batch_launch(int storage, int K, int mode, int grid, int threads, size_t sme
 struct BatchFinal {
     int64_t W;
     int8_t *spins;        // n, original vertex order
-    int64_t *best;        // [0] cut, [1] energy, [2] replica
+    int64_t *best;        // [0] cut, [1] energy, [2] replica, [3] replicas with cut >= target
     int32_t storage;      // 0 f32, 1 f16
     int32_t pad_;
 };
@@ -165,8 +165,9 @@ struct FinalArgs {
     const uint32_t *bisB;   // nullptr: bisector from bestp
     const uint32_t *bits;   // nullptr: spins from the phases
     int32_t words;
-    int64_t *best;        // [0] cut, [1] energy, [2] replica
+    int64_t *best;        // [0] cut, [1] energy, [2] replica, [3] replicas with cut >= target
     int8_t *spins;        // n, original vertex order
+    int64_t target;       // success threshold (INT64_MIN: every replica counts)
 };
 int finalize_launch(const FinalArgs &a, void *stream);
 

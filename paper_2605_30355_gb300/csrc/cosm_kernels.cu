@@ -2200,20 +2200,25 @@ __device__ void finalize_body(int replicas, int K, int storage, int P, int n, in
                               const void *state, int64_t stride, const int32_t *orig_of,
                               const int64_t *cut, const int32_t *bestp, const int64_t *energy,
                               const uint32_t *bisB, const uint32_t *bits, int words, int64_t *best,
-                              int8_t *spins)
+                              int8_t *spins, int64_t target)
 {
     __shared__ long long s_cut[1024];
     __shared__ int s_rep[1024];
+    __shared__ unsigned long long s_hits;
     const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) s_hits = 0;
     long long bc = LLONG_MIN;
     int br = 0x7FFFFFFF;
+    unsigned long long hits = 0;
     for (int r = tid; r < replicas; r += nt) {
         const long long c = energy ? -energy[r] : cut[r];
         if (c > bc || (c == bc && r < br)) { bc = c; br = r; }
+        hits += cut[r] >= target ? 1 : 0;
     }
     s_cut[tid] = bc;
     s_rep[tid] = br;
     __syncthreads();
+    atomicAdd(&s_hits, hits);
     for (int o = nt / 2; o > 0; o >>= 1) {
         if (tid < o) {
             const long long c = s_cut[tid + o];
@@ -2231,6 +2236,7 @@ __device__ void finalize_body(int replicas, int K, int storage, int P, int n, in
         best[0] = cb;
         best[1] = energy ? energy[rb] : W - 2 * cb;
         best[2] = rb;
+        best[3] = (int64_t)s_hits;
     }
     if (bits) {
         const uint32_t *bw = bits + (size_t)rb * words;
@@ -2248,7 +2254,7 @@ __device__ void finalize_body(int replicas, int K, int storage, int P, int n, in
 __global__ void __launch_bounds__(1024) finalize_kernel(const FinalArgs a)
 {
     finalize_body(a.replicas, a.K, a.storage, a.P, a.n, a.W, a.state, a.state_tile_stride, a.orig_of,
-                  a.cut, a.bestp, a.energy, a.bisB, a.bits, a.words, a.best, a.spins);
+                  a.cut, a.bestp, a.energy, a.bisB, a.bits, a.words, a.best, a.spins, a.target);
 }
 
 __global__ void __launch_bounds__(1024) batch_finalize_kernel(const InstView *insts, const BatchFinal *fin)
@@ -2256,7 +2262,7 @@ __global__ void __launch_bounds__(1024) batch_finalize_kernel(const InstView *in
     const InstView &v = insts[blockIdx.x];
     const BatchFinal &f = fin[blockIdx.x];
     finalize_body(v.replicas, v.K, f.storage, v.P, v.n, f.W, v.state, v.state_tile_stride, v.orig_of,
-                  v.cut, v.bestp, v.energy, v.bisB, nullptr, 0, f.best, f.spins);
+                  v.cut, v.bestp, v.energy, v.bisB, nullptr, 0, f.best, f.spins, LLONG_MIN);
 }
 
 // ---------------------------------------------------------------- optimal bisector
@@ -2623,5 +2629,90 @@ extern "C" int cosm_probe_smem(int32_t iters, double *bytes_per_clk_per_sm, doub
     // two CTAs share an SM; clk is the longest CTA's span
     if (bytes_per_clk_per_sm) *bytes_per_clk_per_sm = 2.0 * bytes_per_cta / (double)cycles;
     if (gbps) *gbps = bytes_per_cta * blocks / (ms * 1e-3) / 1e9;
+    return COSM_OK;
+}
+
+// ---------------------------------------------------------------- FP32 issue probe
+namespace cosm {
+
+// FP32 arithmetic issue rate: every thread runs 8 independent chains of
+// fused multiply-adds, scalar (fma.rn.f32, one operation per lane) or packed
+// (fma.rn.f32x2, two operations per lane); thread 0 records the SM clocks
+// spent. The chains hold values near a fixed point of x -> a x + b, so no
+// lane overflows or goes subnormal.
+template <bool kPacked>
+__global__ void __launch_bounds__(1024) fp32_probe_kernel(int iters, unsigned long long *clk, float *sink)
+{
+    const float a = 0.5f, b = 0.25f + 1e-3f * (float)(threadIdx.x & 7);
+    f32x2 x2[8];
+    float x1[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        x1[i] = 0.125f * (float)i;
+        x2[i] = p_pack(x1[i], -x1[i]);
+    }
+    const f32x2 a2 = p_pack(a, a), b2 = p_pack(b, b);
+    __syncthreads();
+    const unsigned long long t0 = clock64();
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if constexpr (kPacked) {
+                    x2[i] = p_fma(x2[i], a2, b2);
+                } else {
+                    asm volatile("fma.rn.f32 %0, %0, %1, %2;" : "+f"(x1[i]) : "f"(a), "f"(b));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const unsigned long long t1 = clock64();
+    if (threadIdx.x == 0) atomicMax(clk, t1 - t0);
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += kPacked ? p_lo(x2[i]) + p_hi(x2[i]) : x1[i];
+    if (s == 12345.0f) sink[0] = s;
+}
+
+}  // namespace cosm
+
+extern "C" int cosm_probe_fp32(int32_t iters, double *ops_per_clk_per_sm, double *ops_per_clk_per_sm_packed)
+{
+    using namespace cosm;
+    if (iters < 1) return COSM_ERR_INVALID_ARG;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return COSM_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    unsigned long long *clk = nullptr;
+    float *sink = nullptr;
+    if (cudaMalloc(&clk, 8) != cudaSuccess) return COSM_ERR_NOMEM;
+    if (cudaMalloc(&sink, 4) != cudaSuccess) {
+        cudaFree(clk);
+        return COSM_ERR_NOMEM;
+    }
+    const int threads = 1024, blocks = 2 * sms;
+    // operations per CTA: threads x iters x 8 unrolled x 8 chains (x 2 packed)
+    const double ops = (double)threads * iters * 64.0;
+    double res[2] = {0.0, 0.0};
+    cudaError_t err = cudaSuccess;
+    for (int packed = 0; packed < 2 && err == cudaSuccess; ++packed) {
+        for (int rep = 0; rep < 2; ++rep) {  // the first launch warms up
+            cudaMemset(clk, 0, 8);
+            if (packed) fp32_probe_kernel<true><<<blocks, threads>>>(rep ? iters : iters / 4 + 1, clk, sink);
+            else fp32_probe_kernel<false><<<blocks, threads>>>(rep ? iters : iters / 4 + 1, clk, sink);
+        }
+        err = cudaDeviceSynchronize();
+        unsigned long long cycles = 0;
+        if (err == cudaSuccess) err = cudaMemcpy(&cycles, clk, 8, cudaMemcpyDeviceToHost);
+        // two CTAs share an SM; clk is the longest CTA's span
+        if (cycles) res[packed] = 2.0 * ops * (packed ? 2.0 : 1.0) / (double)cycles;
+    }
+    cudaFree(clk);
+    cudaFree(sink);
+    if (err != cudaSuccess) return COSM_ERR_CUDA;
+    if (ops_per_clk_per_sm) *ops_per_clk_per_sm = res[0];
+    if (ops_per_clk_per_sm_packed) *ops_per_clk_per_sm_packed = res[1];
     return COSM_OK;
 }

@@ -621,7 +621,8 @@ static KernelArgs base_args(cosm_handle *h)
     a.v = inst_view(h);
     a.ready = h->d_ready.p;
     a.err = h->d_err.p;
-    a.wait_limit_ns = (uint64_t)env_int("COSM_WAIT_LIMIT_S", 20) * 1000000000ull;
+    a.wait_limit_ns = h->wait_limit_ns ? h->wait_limit_ns
+                                       : (uint64_t)env_int("COSM_WAIT_LIMIT_S", 20) * 1000000000ull;
     return a;
 }
 
@@ -639,47 +640,54 @@ static int upload_segments(cosm_handle *h, cudaStream_t st)
     return COSM_OK;
 }
 
-// Work schedule for `tiles` tiles of S sweeps each on at most G resident
-// CTAs. With tiles <= G every CTA runs one whole trial. Otherwise the
-// wrap-around rule of McNaughton (1959) gives every CTA an equal share of
-// tiles * S sweeps: a tile split between CTA b and b+1 runs its head first
-// on b and its tail last on b+1 (the share exceeds S, so the two never
-// overlap), and b+1 waits for the head's published state before the tail.
-static void build_schedule(cosm_handle *h, int64_t tiles, int64_t S, int64_t G)
+// Work schedule for sweeps s0..s1 of an S-sweep trial (L = s1 - s0 + 1
+// sweeps) of `tiles` tiles on at most G resident CTAs. With tiles <= G every
+// CTA runs one tile's whole range. Otherwise the wrap-around rule of
+// McNaughton (1959) gives every CTA an equal share of tiles * L sweeps: a
+// tile split between CTA b and b+1 runs its head first on b and its tail
+// last on b+1 (the share exceeds L, so the two never overlap), and b+1 waits
+// for the head's published state before the tail. A range that starts at
+// sweep 1 draws the initial phases, a later one loads the stored state; the
+// range that ends at sweep S reads out; every range stores its state.
+static void build_schedule(cosm_handle *h, int64_t tiles, int64_t s0, int64_t s1, int64_t S, int64_t G)
 {
-    if (h->sched_tiles == tiles && h->sched_S == S && h->sched_G == G) return;
+    if (h->sched_tiles == tiles && h->sched_S == S && h->sched_G == G && h->sched_s0 == s0 && h->sched_s1 == s1)
+        return;
     h->h_segs.clear();
     h->h_segoff.assign(1, 0);
     h->segs_uploaded = false;
+    const int64_t L = s1 - s0 + 1;
+    const int32_t first = s0 == 1 ? SEG_INIT : SEG_LOAD;
+    const int32_t last = SEG_STORE | (s1 == S ? SEG_READOUT : 0);
     if (tiles <= G) {
         for (int64_t t = 0; t < tiles; ++t) {
-            h->h_segs.push_back(Segment{(int32_t)t, SEG_INIT | SEG_READOUT | SEG_STORE, 1, S});
+            h->h_segs.push_back(Segment{(int32_t)t, first | last, s0, s1});
             h->h_segoff.push_back((int32_t)h->h_segs.size());
         }
     } else {
-        const __int128 L = (__int128)tiles * S;
+        const __int128 TL = (__int128)tiles * L;
         for (int64_t b = 0; b < G; ++b) {
-            const int64_t lo = (int64_t)(L * b / G), hi = (int64_t)(L * (b + 1) / G);
+            const int64_t lo = (int64_t)(TL * b / G), hi = (int64_t)(TL * (b + 1) / G);
             std::vector<Segment> pieces;
-            for (int64_t j = lo / S; j <= (hi - 1) / S && j < tiles; ++j) {
-                const int64_t a0 = std::max<int64_t>(lo, j * S) - j * S;
-                const int64_t z = std::min<int64_t>(hi, (j + 1) * S) - j * S;
+            for (int64_t j = lo / L; j <= (hi - 1) / L && j < tiles; ++j) {
+                const int64_t a0 = std::max<int64_t>(lo, j * L) - j * L;
+                const int64_t z = std::min<int64_t>(hi, (j + 1) * L) - j * L;
                 if (z <= a0) continue;
-                Segment sg{(int32_t)j, 0, a0 + 1, z};
-                sg.flags = (a0 == 0) ? SEG_INIT : (SEG_LOAD | SEG_WAIT);
-                sg.flags |= (z == S) ? (SEG_READOUT | SEG_STORE) : (SEG_STORE | SEG_SIGNAL);
+                Segment sg{(int32_t)j, 0, s0 + a0, s0 + z - 1};
+                sg.flags = (a0 == 0) ? first : (SEG_LOAD | SEG_WAIT);
+                sg.flags |= (z == L) ? last : (SEG_STORE | SEG_SIGNAL);
                 pieces.push_back(sg);
             }
             // execution order: head of the tile continuing on b+1 first, the
             // tail of the tile started on b-1 last
             std::vector<Segment> ordered;
-            if (!pieces.empty() && pieces.back().s_begin == 1 && pieces.back().s_end < S) {
+            if (!pieces.empty() && pieces.back().s_begin == s0 && pieces.back().s_end < s1) {
                 ordered.push_back(pieces.back());
                 pieces.pop_back();
             }
             Segment tail{};
             bool has_tail = false;
-            if (!pieces.empty() && pieces.front().s_begin > 1) {
+            if (!pieces.empty() && pieces.front().s_begin > s0) {
                 tail = pieces.front();
                 has_tail = true;
                 pieces.erase(pieces.begin());
@@ -693,6 +701,8 @@ static void build_schedule(cosm_handle *h, int64_t tiles, int64_t S, int64_t G)
     h->sched_tiles = tiles;
     h->sched_S = S;
     h->sched_G = G;
+    h->sched_s0 = s0;
+    h->sched_s1 = s1;
 }
 
 int cosm::upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st)
@@ -766,31 +776,54 @@ int cosm::launch_finalize(cosm_handle *h, cudaStream_t st)
     f.words = (h->g.n + 31) / 32;
     f.best = h->d_best.p;
     f.spins = h->d_spins.p;
+    f.target = h->target;
     if (finalize_launch(f, st)) return fail(COSM_ERR_CUDA, std::string("finalize launch: ") +
                                                           cudaGetErrorString(cudaGetLastError()));
     return COSM_OK;
 }
 
-extern "C" int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64_t seed, void *stream)
+// Sweeps s0..s1 of an S-sweep trial of every replica (cosm_run: 1..S).
+static int run_range(cosm_handle *h, int64_t sweeps, int64_t s0, int64_t s1, int32_t replicas, uint64_t seed,
+                     int64_t target_cut, cudaStream_t st)
 {
     if (!h) return fail(COSM_ERR_INVALID_ARG, "NULL handle");
     if (sweeps < 1 || sweeps >= ((int64_t)1 << 31)) return fail(COSM_ERR_INVALID_ARG, "sweeps must be in [1, 2^31)");
     if (replicas < 1 || replicas >= (1 << 24)) return fail(COSM_ERR_INVALID_ARG, "replicas must be in [1, 2^24)");
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (s0 < 1 || s1 < s0 || s1 > sweeps) return fail(COSM_ERR_INVALID_ARG, "need 1 <= s_from <= s_to <= sweeps");
     int rc;
-    if (!h->K || replicas != h->replicas) {
+    if (s0 > 1) {
+        // a continued trial keeps its replicas, seed and layout
+        if (!h->have_state || h->sweep_idx != s0 - 1)
+            return fail(COSM_ERR_STATE, "the state is at sweep " + std::to_string(h->sweep_idx) +
+                                            ", not " + std::to_string(s0 - 1));
+        if (replicas != h->replicas || seed != h->seed)
+            return fail(COSM_ERR_INVALID_ARG, "a continued trial keeps its replica count and seed");
+        if (h->stream && h->stream != st) CK(cudaStreamSynchronize(h->stream));
+    } else if (!h->K || replicas != h->replicas) {
         if ((rc = choose_layout(h, replicas))) return rc;
     }
     h->replicas = replicas;
     h->seed = seed;
+    h->target = target_cut;
     if ((rc = ensure_run_buffers(h, replicas))) return rc;
     if ((rc = upload_alpha(h, sweeps, st))) return rc;
     const int64_t tiles = (replicas + h->K - 1) / h->K;
     int64_t cap = (int64_t)h->occupancy * h->num_sms;
     const int cap_env = env_int("COSM_GRID_CAP", 0);  // test hook: fewer resident CTAs
     if (cap_env > 0) cap = std::min<int64_t>(cap, cap_env);
-    build_schedule(h, tiles, sweeps, cap);
-    if ((rc = upload_segments(h, st))) return rc;
+    build_schedule(h, tiles, s0, s1, sweeps, cap);
+    if (h->fault == COSM_FAULT_DROP_SIGNAL) {
+        // injected fault: the heads of split tiles do not publish their state,
+        // so the tails' bounded waits give up (COSM_ERR_TIMEOUT at cosm_sync)
+        for (Segment &sg : h->h_segs) sg.flags &= ~SEG_SIGNAL;
+        h->segs_uploaded = false;
+        rc = upload_segments(h, st);
+        h->sched_tiles = -1;  // the next run rebuilds the true schedule
+        h->fault = 0;
+        if (rc) return rc;
+    } else if ((rc = upload_segments(h, st))) {
+        return rc;
+    }
     const bool waits = tiles > cap;
     if (waits) CK(cudaMemsetAsync(h->d_ready.p, 0, (size_t)tiles * 4, st));
     CK(cudaMemsetAsync(h->d_err.p, 0, 4, st));
@@ -813,6 +846,17 @@ extern "C" int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64
     h->grid = cfg.grid;
     if (sweep_launch(cfg, a, st))
         return fail(COSM_ERR_CUDA, std::string("sweep launch: ") + cudaGetErrorString(cudaGetLastError()));
+    h->launches = 1;
+    h->stream = st;
+    h->have_state = true;
+    h->sweep_idx = s1;
+    if (s1 < sweeps) {
+        // mid-trial: no readout yet
+        h->have_result = false;
+        h->have_trace = false;
+        h->bits_valid = false;
+        return COSM_OK;
+    }
     h->launches = 2;
     if (h->prm.flags & COSM_OPT_BISECTOR) {
         if ((rc = launch_opt_readout(h, track > 0, st))) return rc;
@@ -822,9 +866,44 @@ extern "C" int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64
     h->n_trace = n_trace;
     h->have_trace = track > 0;
     if ((rc = launch_finalize(h, st))) return rc;
-    h->stream = st;
-    h->have_state = true;
     h->have_result = true;
+    return COSM_OK;
+}
+
+extern "C" int cosm_run(cosm_handle *h, int64_t sweeps, int32_t replicas, uint64_t seed, int64_t target_cut,
+                        void *stream)
+{
+    return run_range(h, sweeps, 1, sweeps, replicas, seed, target_cut, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cosm_run_range(cosm_handle *h, int64_t sweeps, int64_t s_from, int64_t s_to, int32_t replicas,
+                              uint64_t seed, int64_t target_cut, void *stream)
+{
+    return run_range(h, sweeps, s_from, s_to, replicas, seed, target_cut, reinterpret_cast<cudaStream_t>(stream));
+}
+
+extern "C" int cosm_get_success(cosm_handle *h, int64_t *count)
+{
+    if (!h || !count) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    if (!h->have_result) return fail(COSM_ERR_STATE, "no run or readout yet");
+    int rc = cosm_sync(h);
+    if (rc) return rc;
+    CK(cudaMemcpy(count, h->d_best.p + 3, 8, cudaMemcpyDeviceToHost));
+    return COSM_OK;
+}
+
+extern "C" int cosm_set_wait_limit(cosm_handle *h, double seconds)
+{
+    if (!h || !(seconds > 0.0) || seconds > 3600.0)
+        return fail(COSM_ERR_INVALID_ARG, "the wait limit must be in (0, 3600] seconds");
+    h->wait_limit_ns = (uint64_t)(seconds * 1e9);
+    return COSM_OK;
+}
+
+extern "C" int cosm_inject_fault(cosm_handle *h, int32_t kind)
+{
+    if (!h || (kind != 0 && kind != COSM_FAULT_DROP_SIGNAL)) return fail(COSM_ERR_INVALID_ARG, "unknown fault");
+    h->fault = kind;
     return COSM_OK;
 }
 
@@ -987,6 +1066,71 @@ extern "C" int cosm_set_state(cosm_handle *h, const double *phases, int32_t repl
     }
     CK(cudaMemcpy(h->d_state.p, raw.data(), raw.size(), cudaMemcpyHostToDevice));
     h->have_state = true;
+    h->sweep_idx = 0;
+    h->have_result = false;
+    h->have_trace = false;
+    h->bits_valid = false;
+    return COSM_OK;
+}
+
+// Checkpoint of the state in its storage type: element (r, v) of the tile
+// layout [tile][slot][K] <-> [replica][vertex] in original vertex order.
+static size_t storage_bytes(int storage) { return storage == COSM_F32 ? 4 : 2; }
+
+extern "C" int cosm_export_state(cosm_handle *h, void *phases, int32_t storage, int64_t *sweep_idx)
+{
+    if (!h || !phases) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    if (storage != h->prm.storage) return fail(COSM_ERR_INVALID_ARG, "storage differs from the handle's");
+    if (!h->have_state) return fail(COSM_ERR_STATE, "no state yet");
+    int rc = cosm_sync(h);
+    if (rc) return rc;
+    const int64_t tiles = (h->replicas + h->K - 1) / h->K;
+    const size_t esz = storage_bytes(storage);
+    std::vector<unsigned char> raw((size_t)tiles * (size_t)h->tile_stride * esz);
+    CK(cudaMemcpy(raw.data(), h->d_state.p, raw.size(), cudaMemcpyDeviceToHost));
+    std::vector<unsigned char> out((size_t)h->replicas * h->g.n * esz);
+    for (int32_t r = 0; r < h->replicas; ++r) {
+        const size_t base = (size_t)(r / h->K) * (size_t)h->tile_stride;
+        for (int32_t v = 0; v < h->g.n; ++v) {
+            const size_t idx = base + (size_t)h->slot_of[(size_t)v] * h->K + (size_t)(r % h->K);
+            std::memcpy(out.data() + ((size_t)r * h->g.n + v) * esz, raw.data() + idx * esz, esz);
+        }
+    }
+    CK(cudaMemcpy(phases, out.data(), out.size(), cudaMemcpyDefault));
+    if (sweep_idx) *sweep_idx = h->sweep_idx;
+    return COSM_OK;
+}
+
+extern "C" int cosm_import_state(cosm_handle *h, const void *phases, int32_t storage, int32_t replicas,
+                                 uint64_t seed, int64_t sweep_idx)
+{
+    if (!h || !phases) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
+    if (storage != h->prm.storage) return fail(COSM_ERR_INVALID_ARG, "storage differs from the handle's");
+    if (replicas < 1 || replicas >= (1 << 24)) return fail(COSM_ERR_INVALID_ARG, "bad replica count");
+    if (sweep_idx < 0 || sweep_idx >= ((int64_t)1 << 31)) return fail(COSM_ERR_INVALID_ARG, "bad sweep index");
+    int rc;
+    if (h->stream) CK(cudaStreamSynchronize(h->stream));
+    if (!h->K || replicas != h->replicas) {
+        if ((rc = choose_layout(h, replicas))) return rc;
+    }
+    h->replicas = replicas;
+    h->seed = seed;
+    if ((rc = ensure_run_buffers(h, replicas))) return rc;
+    const size_t esz = storage_bytes(storage);
+    std::vector<unsigned char> in((size_t)replicas * h->g.n * esz);
+    CK(cudaMemcpy(in.data(), phases, in.size(), cudaMemcpyDefault));
+    const int64_t tiles = (replicas + h->K - 1) / h->K;
+    std::vector<unsigned char> raw((size_t)tiles * (size_t)h->tile_stride * esz, 0);
+    for (int32_t r = 0; r < replicas; ++r) {
+        const size_t base = (size_t)(r / h->K) * (size_t)h->tile_stride;
+        for (int32_t v = 0; v < h->g.n; ++v) {
+            const size_t idx = base + (size_t)h->slot_of[(size_t)v] * h->K + (size_t)(r % h->K);
+            std::memcpy(raw.data() + idx * esz, in.data() + ((size_t)r * h->g.n + v) * esz, esz);
+        }
+    }
+    CK(cudaMemcpy(h->d_state.p, raw.data(), raw.size(), cudaMemcpyHostToDevice));
+    h->have_state = true;
+    h->sweep_idx = sweep_idx;
     h->have_result = false;
     h->have_trace = false;
     h->bits_valid = false;
@@ -1045,6 +1189,7 @@ extern "C" int cosm_step(cosm_handle *h, int64_t sweep, float alpha, void *strea
     rc = launch_on_state(h, SEG_LOAD | SEG_STORE, sweep, sweep, tab.p, sweep, st);
     if (!rc) rc = cudaStreamSynchronize(st) == cudaSuccess ? COSM_OK : fail(COSM_ERR_CUDA, "step failed");
     tab.release();
+    h->sweep_idx = sweep;
     h->have_result = false;
     h->have_trace = false;
     h->bits_valid = false;
@@ -1092,7 +1237,7 @@ extern "C" int cosm_solve(const cosm_graph_desc *g, const cosm_params *p, int64_
     cosm_handle *h = nullptr;
     int rc = cosm_create(g, p, &h);
     if (rc) return rc;
-    rc = cosm_run(h, sweeps, replicas, seed, nullptr);
+    rc = cosm_run(h, sweeps, replicas, seed, INT64_MIN, nullptr);
     if (!rc) rc = cosm_get_best(h, best_cut, energy, nullptr, spins);
     if (!rc && replica_cuts) rc = cosm_get_replica_cuts(h, replica_cuts, nullptr);
     cosm_destroy(h);

@@ -77,6 +77,30 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
     if (gd->h) return fail(COSM_ERR_INVALID_ARG, "local fields are not supported without allocation");
     if (gd->n < 2 || gd->n > kMaxVertices || gd->m < 1 || gd->m > ((int64_t)1 << 26))
         return fail(COSM_ERR_INVALID_ARG, "n must be in [2, 65536] and m in [1, 2^26]");
+    // the outputs must be device memory of the current device: a host
+    // address handed to the kernel would fault or write the wrong memory
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return fail(COSM_ERR_CUDA, "cudaGetDevice failed");
+    for (const void *q : {(const void *)replica_cuts, (const void *)best_p}) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, q) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(COSM_ERR_INVALID_ARG, "an output buffer is not a CUDA allocation");
+        }
+        if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != dev)
+            return fail(COSM_ERR_INVALID_ARG, "the output buffers must be device memory of the current device");
+    }
+    // the scratch is filled from host tables released on return, which a
+    // stream capture would record by address: capturing streams are refused
+    {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(reinterpret_cast<cudaStream_t>(stream), &cs) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(COSM_ERR_INVALID_ARG, "invalid stream");
+        }
+        if (cs != cudaStreamCaptureStatusNone)
+            return fail(COSM_ERR_INVALID_ARG, "cosm_solve_static cannot be called on a capturing stream");
+    }
 
     // graph checks and partition, as cosm_create does (host memory only)
     Graph g;
@@ -122,7 +146,8 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
         return fail(COSM_ERR_TOO_LARGE,
                     "graph, step table and work list need " + std::to_string(total) +
                         " bytes of scratch; the static scratch holds " + std::to_string(kScratchBytes) +
-                        " (5 m + 4 n + 8 sweeps + 28 ceil(replicas / tile) + 4 colours bytes, 256-aligned parts)");
+                        " (5 m + 4 n + 8 sweeps + 28 ceil(replicas / tile) + 4 (colours + 1) + 8 bytes, each of its eight"
+                        " parts rounded up to 256 bytes)");
     unsigned char *base = nullptr;
     if ((rc = scratch_address(&base))) return rc;
 
