@@ -34,6 +34,10 @@ STORE_F64 = 0
 STORE_F16 = 1
 STORE_Q16 = 2
 STORE_BF16 = 3
+# 16-bit storage rounded once per pass of two colours (at the end of each
+# pass, the last pass taking the twist first) instead of at every write
+STORE_F16_PASS = 4
+STORE_BF16_PASS = 5
 
 
 def build(force: bool = False) -> str:

@@ -166,13 +166,14 @@ static double orc_q16_step(double a) { return floor(a * 65536.0 + 0.5) / 65536.0
 
 /* Storage rounding: 0 = none (FP64), 1 = binary16 of the phase's
  * representative in [-1/2, 1/2), 2 = fixed point (values already on the
- * grid), 3 = bfloat16 of the representative. The result is returned in
- * [0,1). */
+ * grid), 3 = bfloat16 of the representative; 4 and 5 round as 1 and 3 (they
+ * differ from them only in when a sweep rounds, orc_sweep_h). The result is
+ * returned in [0,1). */
 static double orc_store(double x, int32_t storage)
 {
-    if (storage != 1 && storage != 3) return x;
+    if (storage != 1 && storage != 3 && storage != 4 && storage != 5) return x;
     double g = (x >= 0.5) ? x - 1.0 : x;
-    g = (storage == 1) ? orc_round_binary16(g) : orc_round_bfloat16(g);
+    g = (storage == 1 || storage == 4) ? orc_round_binary16(g) : orc_round_bfloat16(g);
     g = (g < 0.0) ? g + 1.0 : g;
     return g >= 1.0 ? 0.0 : g;
 }
@@ -241,7 +242,16 @@ int orc_twist_dir(uint64_t seed, int64_t replica, int64_t sweep)
  * With flag DWT_RANDDIR the twist direction of each DWT event is drawn
  * (orc_twist_dir) instead of always +1 (Section II-D).
  * storage: 0 FP64, 1 binary16 storage rounding, 2 fixed point on the
- * 2^-16-turn grid (alpha and the twist rounded to the grid).
+ * 2^-16-turn grid (alpha and the twist rounded to the grid), 3 bfloat16
+ * storage rounding; modes 1 and 3 round every phase write (each pair update,
+ * each twist move). Modes 4 (binary16) and 5 (bfloat16) store once per pass
+ * of two consecutive colours instead: the phases stay unrounded inside a
+ * pass and every phase is rounded when it ends, after colours 2, 4, ... and
+ * at the end of the sweep; the last pass takes the field sub-sweep and the
+ * twist, when due, before its rounding. (The paper fixes no phase storage
+ * format; Section II-E only says that no double precision is needed. The
+ * 16-bit storage forms are readings of that: a stored phase is rounded,
+ * arithmetic stays exact between stores.)
  * Near-ties: an edge whose angular difference is within tie_eps of 0 or 1/2
  * when processed, a phase within tie_eps of a window edge, and a phase with
  * a field within tie_eps of 0 or 1/2, are recorded in ties[] (edge e as e,
@@ -263,8 +273,14 @@ int64_t orc_sweep_h(int32_t n, int32_t C, const int64_t *off, const int32_t *src
         step = orc_q16_step(step);
         alpha = orc_q16_step(alpha);
     }
+    /* modes 4, 5: no rounding at each write; every phase at each pass end */
+    const int per_pass = (storage == 4 || storage == 5);
+    const int32_t pass_store = storage;
+    if (per_pass) storage = 0;
     if (!(flags & ORC_NO_SCS)) {
         for (int32_t c = 0; c < C; ++c) {
+            if (per_pass && c > 0 && c % 2 == 0)
+                for (int32_t v = 0; v < n; ++v) x[v] = orc_store(x[v], pass_store);
             for (int64_t e = off[c]; e < off[c + 1]; ++e) {
                 int32_t i = src[e], j = dst[e];
                 double J = -(double)w[e];
@@ -338,6 +354,8 @@ int64_t orc_sweep_h(int32_t n, int32_t C, const int64_t *off, const int32_t *src
             if (in) x[v] = orc_store(orc_wrap(x[v] + twist), storage);
         }
     }
+    if (per_pass)
+        for (int32_t v = 0; v < n; ++v) x[v] = orc_store(x[v], pass_store);
     return nt;
 }
 

@@ -310,6 +310,53 @@ def test_f16_storage_keeps_phases_representable(orc):
     assert _circ(x, xf).max() < 8 * 2 ** -12
 
 
+def _split_passes(orc, inst):
+    """The torus's coloured graph, and its two passes as graphs of their own:
+    colours (0, 1) and colours (2, 3) renumbered (0, 1)."""
+    col, C = orc.color_instance(inst)
+    assert C == 4
+    g = orc.ColouredGraph(inst.n, inst.src, inst.dst, inst.w, col, C)
+    parts = []
+    for lo in (0, 2):
+        k = (col == lo) | (col == lo + 1)
+        parts.append(orc.ColouredGraph(inst.n, inst.src[k], inst.dst[k], inst.w[k], col[k] - lo, 2))
+    return g, parts
+
+
+def _round_turns(x, dtype):
+    torch = pytest.importorskip("torch") if dtype == "bf16" else None
+    g = np.where(x >= 0.5, x - 1.0, x)
+    if dtype == "f16":
+        g = g.astype(np.float16).astype(np.float64)
+    else:
+        g = torch.tensor(g).to(torch.bfloat16).to(torch.float64).numpy()
+    return np.mod(np.where(g < 0, g + 1.0, g), 1.0)
+
+
+@pytest.mark.parametrize("dtype", ["f16", "bf16"])
+@pytest.mark.parametrize("sweep", [2, 3])
+def test_pass_rounding_is_two_fp64_passes_each_rounded_once(orc, dtype, sweep):
+    # modes 4 / 5: a sweep of the 4-colour torus equals an FP64 sweep of
+    # colours (0, 1), one rounding of every phase (numpy / torch conversion),
+    # an FP64 sweep of colours (2, 3) with the twist when due, one rounding
+    inst = instances.torus2d(8, 12, 3)
+    g, (g01, g23) = _split_passes(orc, inst)
+    mode = orc.STORE_F16_PASS if dtype == "f16" else orc.STORE_BF16_PASS
+    x0 = _round_turns(orc.init_phases(inst.n, 4, 1), dtype)
+    a = 0.0331
+    x, _ = orc.sweep(g, x0, a, sweep, seed=4, replica=1, dwt_ratio=1.0, storage=mode)
+    y, _ = orc.sweep(g01, x0, a, sweep, seed=4, replica=1, dwt_ratio=1.0, flags=orc.NO_DWT)
+    y = _round_turns(y, dtype)
+    y, _ = orc.sweep(g23, y, a, sweep, seed=4, replica=1, dwt_ratio=1.0)
+    y = _round_turns(y, dtype)
+    assert np.array_equal(x, y)
+    # the rounding cadence matters: every-write rounding gives another state
+    xw, _ = orc.sweep(g, x0, a, sweep, seed=4, replica=1, dwt_ratio=1.0,
+                      storage=orc.STORE_F16 if dtype == "f16" else orc.STORE_BF16)
+    assert not np.array_equal(x, xw)
+    assert _circ(x, xw).max() < 4 * (2 ** -12 if dtype == "f16" else 2 ** -9)
+
+
 def test_bfloat16_rounding_matches_library(orc):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(4)
