@@ -592,7 +592,7 @@ def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e
     batch = cosm.Batch(insts, storage=storage, **prm)
     create_s = time.perf_counter() - t0
     if not args.no_tune:
-        batch.tune(reps, probe_sweeps=20, stream=stream)
+        batch.tune(reps, probe_sweeps=200, stream=stream)
     for _ in range(warmup):
         batch.run(S, reps, seeds, stream)
         batch.sync()

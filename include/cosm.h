@@ -286,9 +286,10 @@ int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, const cosm_p
 
 /* Runs one trial (Alg. 1) per replica of every instance i: sweeps[i] sweeps,
  * replicas[i] replicas, seed seeds[i] (host arrays of `count`). Replica
- * tiles of all instances are work units; units of one (storage, tile width,
- * kernel) class share one persistent launch draining a queue ordered by
- * decreasing cost; class launches overlap on forked streams; the run is
+ * tiles of all instances are work units; units of one class (storage, tile
+ * width, kernel, threads per CTA, CTAs per SM) share one persistent launch
+ * draining a queue ordered by decreasing cost; class launches overlap on
+ * forked streams; the run is
  * captured into a CUDA graph once and replayed while its layout holds.
  * Per instance, results equal those of cosm_run with the same arguments.
  * Asynchronous: ordered after earlier work on `stream`, and later work on
@@ -307,16 +308,21 @@ int cosm_batch_get_replica_cuts(cosm_batch *b, int32_t i, int64_t *cuts, int32_t
 int cosm_batch_get_state(cosm_batch *b, int32_t i, double *phases);
 
 /* Autotuner: times a short run (probe_sweeps sweeps per instance, the given
- * replica counts) for each tile policy (per-instance widest tile that keeps
- * the most replicas resident, or the narrowest tile) and thread count
- * (rule-based, 128, 256, 512 per CTA) and keeps the fastest for later runs.
+ * replica counts) of six layouts and keeps the fastest for later runs: the
+ * tile policies -- per instance the tile that keeps the most replicas
+ * resident per SM when the GPU is full (ties to the wider tile), the
+ * narrowest tile, or the single-instance rule for the instance's own
+ * replica count -- each with the per-instance thread rule, and the first
+ * policy with 128, 256 or 512 threads per CTA forced. Instances of one
+ * kernel, thread count and occupancy form a class: one persistent launch.
  * With the environment variable COSM_TUNE_CACHE naming a file, a choice for
  * the same batch shape is read from it, and new choices are appended. */
 int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t probe_sweeps, void *stream);
 
 /* out[0] instances, out[1] classes, out[2] units, out[3] kernel launches
- * per run, out[4] graphs built, out[5] tile policy, out[6] forced threads
- * (0 = rule), out[7] CTAs over all classes. */
+ * per run, out[4] graphs built, out[5] tile policy (0 full-GPU rule, 1
+ * narrowest tile, 2 single-instance rule), out[6] forced threads (0 =
+ * rule), out[7] CTAs over all classes. */
 int cosm_batch_info(cosm_batch *b, int64_t out[8]);
 
 /* Releases the batch and all its instances. NULL is a no-op. */

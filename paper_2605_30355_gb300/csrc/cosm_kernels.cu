@@ -711,33 +711,14 @@ __device__ __forceinline__ void pair_fast(float (&x1)[K], float (&x2)[K], float 
     }
 }
 
-// 16-bit float storage (binary16, bfloat16): every phase write is a store of
-// the wrapped value in the storage type, also between the colours of a
-// block, so each update there is wrapped and rounded through it at once.
-template <typename H, int K>
-__device__ __forceinline__ void round_16(float (&x)[K])
-{
-#pragma unroll
-    for (int r = 0; r < K; r += 2) {
-        const float2 f = h2_to_f2<H>(f2_to_h2<H>(x[r], x[r + 1]));
-        x[r] = f.x;
-        x[r + 1] = f.y;
-    }
-}
-
+// 16-bit float storage (binary16, bfloat16) in the lattice passes: a phase
+// is stored once per pass of two colours, so it is wrapped and rounded to
+// the storage type once, when its block is stored; the two updates in
+// between are binary32.
 template <typename Store, int K>
 __device__ __forceinline__ void pair_block(float (&x1)[K], float (&x2)[K], float aw, float c)
 {
     pair_fast<K>(x1, x2, aw, c);
-    if constexpr (sizeof(Store) == 2) {
-#pragma unroll
-        for (int r = 0; r < K; ++r) {
-            x1[r] = wrap_c(x1[r]);
-            x2[r] = wrap_c(x2[r]);
-        }
-        round_16<Store, K>(x1);
-        round_16<Store, K>(x2);
-    }
 }
 
 template <int K>
@@ -848,7 +829,11 @@ __device__ __forceinline__ void block_pass_even(Store *xs, const uint8_t *wnib, 
         pair_block<Store, K>(xc, xd, signed_alpha(wb, 2u, alpha), 2.0f);
         pair_block<Store, K>(xa, xc, signed_alpha(wb, 4u, alpha), 2.0f);
         pair_block<Store, K>(xb, xd, signed_alpha(wb, 8u, alpha), 2.0f);
-        // binary32 phases stay unwrapped until the next wrapping odd pass
+        // binary32 phases stay unwrapped until the next wrapping odd pass;
+        // 16-bit phases are wrapped and rounded by their store
+        if constexpr (sizeof(Store) == 2) {
+            wrap_all<K>(xa); wrap_all<K>(xb); wrap_all<K>(xc); wrap_all<K>(xd);
+        }
         sts_k<Store, K>(ad, xa);
         sts_k<Store, K>(ad + qb, xb);
         sts_k<Store, K>(ad + qb2, xc);
@@ -1408,9 +1393,9 @@ __device__ __forceinline__ void twist_wrap_x2(float *xs, int n, const float *thc
 // ---------------------------------------------------------------- paired 16-bit lattice
 // Lattice passes of 16-bit storage (binary16, bfloat16) in f32x2 lanes: a
 // storage word holds two replicas of a slot, which become one f32x2 pair;
-// each update is computed as in the binary32 passes, wrapped and rounded to
-// the storage type (round to nearest even) and widened again, exactly as
-// pair_block does for one lane, so the phases equal the scalar passes' bit
+// the two colours of a pass update it as the binary32 passes do, and the
+// store wraps it and rounds it to the storage type (round to nearest even),
+// exactly as the scalar passes do per lane, so the phases equal theirs bit
 // for bit.
 template <typename H>
 __device__ __forceinline__ f32x2 h2_to_p(uint32_t w)
@@ -1422,11 +1407,6 @@ template <typename H>
 __device__ __forceinline__ uint32_t p_to_h2(f32x2 x)
 {
     return f2_to_h2<H>(p_lo(x), p_hi(x));
-}
-template <typename H>
-__device__ __forceinline__ f32x2 p_round16(f32x2 x)
-{
-    return h2_to_p<H>(p_to_h2<H>(p_wrap(x)));
 }
 template <typename H, int NW>
 __device__ __forceinline__ void lds_h(uint32_t a, f32x2 (&x)[NW])
@@ -1444,14 +1424,6 @@ __device__ __forceinline__ void sts_h(uint32_t a, const f32x2 (&x)[NW])
     for (int i = 0; i < NW; ++i) w[i] = p_to_h2<H>(x[i]);
     st_words<NW>(a, w);
 }
-template <typename H>
-__device__ __forceinline__ void pair_h2(f32x2 &x1, f32x2 &x2, f32x2 aw2, f32x2 c2)
-{
-    pair_x2(x1, x2, aw2, c2);
-    x1 = p_round16<H>(x1);
-    x2 = p_round16<H>(x2);
-}
-
 template <typename H, int K>
 __device__ __forceinline__ void block_pass_even_h2(H *xs, const uint8_t *wnib, float alpha, int Q)
 {
@@ -1472,10 +1444,14 @@ __device__ __forceinline__ void block_pass_even_h2(H *xs, const uint8_t *wnib, f
         const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
 #pragma unroll
         for (int h = 0; h < NW; ++h) {
-            pair_h2<H>(xa[h], xb[h], w0, kTwo2);
-            pair_h2<H>(xc[h], xd[h], w1, kTwo2);
-            pair_h2<H>(xa[h], xc[h], w2, kTwo2);
-            pair_h2<H>(xb[h], xd[h], w3, kTwo2);
+            pair_x2(xa[h], xb[h], w0, kTwo2);
+            pair_x2(xc[h], xd[h], w1, kTwo2);
+            pair_x2(xa[h], xc[h], w2, kTwo2);
+            pair_x2(xb[h], xd[h], w3, kTwo2);
+            xa[h] = p_wrap(xa[h]);
+            xb[h] = p_wrap(xb[h]);
+            xc[h] = p_wrap(xc[h]);
+            xd[h] = p_wrap(xd[h]);
         }
         sts_h<H, NW>(ad, xa);
         sts_h<H, NW>(ad + qb, xb);
@@ -1503,21 +1479,21 @@ __device__ __forceinline__ void odd_block_h2(uint32_t ad, uint32_t oC, uint32_t 
 #pragma unroll
     for (int h = 0; h < NW; ++h) {
         // colour 2: D-C, B-A; colour 3: D-B, C-A
-        pair_h2<H>(xd[h], xc[h], w0, tzc);
-        pair_h2<H>(xb[h], xa[h], w1, tzc);
-        pair_h2<H>(xd[h], xb[h], w2, tzr);
-        pair_h2<H>(xc[h], xa[h], w3, tzr);
+        pair_x2(xd[h], xc[h], w0, tzc);
+        pair_x2(xb[h], xa[h], w1, tzc);
+        pair_x2(xd[h], xb[h], w2, tzr);
+        pair_x2(xc[h], xa[h], w3, tzr);
         if constexpr (kDwt) {
-            // the twist follows the last colour; the store rounds
+            // the twist follows the last colour, before the store rounds
             dwt_x2(xd[h], th2[h], tk2[h], st2[h]);
             dwt_x2(xc[h], th2[h], tk2[h], st2[h]);
             dwt_x2(xb[h], th2[h], tk2[h], st2[h]);
             dwt_x2(xa[h], th2[h], tk2[h], st2[h]);
-            xd[h] = p_wrap(xd[h]);
-            xc[h] = p_wrap(xc[h]);
-            xb[h] = p_wrap(xb[h]);
-            xa[h] = p_wrap(xa[h]);
         }
+        xd[h] = p_wrap(xd[h]);
+        xc[h] = p_wrap(xc[h]);
+        xb[h] = p_wrap(xb[h]);
+        xa[h] = p_wrap(xa[h]);
     }
     sts_h<H, NW>(ad, xd);
     sts_h<H, NW>(ad + oC, xc);
@@ -2166,7 +2142,7 @@ __global__ void __launch_bounds__(max_threads<Store, K, kMode>()) sweep_kernel(c
 // it (a whole trial, or a chunk with the state kept in global memory);
 // shared memory is sized for the class's largest tile.
 template <typename Store, int K, int kMode>
-__global__ void __launch_bounds__(512) batch_kernel(const BatchArgs b)
+__global__ void __launch_bounds__(max_threads<Store, K, kMode>()) batch_kernel(const BatchArgs b)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_skip, s_unit;
@@ -2431,13 +2407,18 @@ template <typename Store, int K, int M>
 static int occ_one(int threads, size_t smem)
 {
     auto fn = sweep_kernel<Store, K, M>;
+    if (threads < 1 || threads > max_threads<Store, K, M>()) return 0;  // beyond the launch bound
     if (smem > 48 * 1024)
         if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+            cudaSuccess) {
+            cudaGetLastError();  // leave no error behind for the next launch check
             return 0;
+        }
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
         return 0;
+    }
     return blocks;
 }
 
@@ -2513,8 +2494,10 @@ static int batch_set_smem(size_t smem)
     static size_t set_bytes = 0;
     if (smem > 48 * 1024 && smem > set_bytes) {
         if (cudaFuncSetAttribute(batch_kernel<Store, K, M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
+                                 (int)smem) != cudaSuccess) {
+            cudaGetLastError();  // leave no error behind for the next launch check
             return -1;
+        }
         set_bytes = smem;
     }
     return 0;
@@ -2524,9 +2507,13 @@ template <typename Store, int K, int M>
 static int batch_occ_one(int threads, size_t smem)
 {
     auto fn = batch_kernel<Store, K, M>;
+    if (threads < 1 || threads > max_threads<Store, K, M>()) return 0;  // beyond the launch bound
     if (batch_set_smem<Store, K, M>(smem)) return 0;
     int blocks = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
     return blocks;
 }
 

@@ -1275,7 +1275,7 @@ struct cosm_batch {
     cudaStream_t own = nullptr;      // capture stream (the legacy stream cannot capture)
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> sig;        // layout signature of the captured graph
-    int policy = 0;                  // 0: per-instance layout rule, 1: smallest tile
+    int policy = 0;                  // 0: per-instance rule for a full GPU, 1: smallest tile, 2: per-instance rule
     int threads = 0;                 // 0: per-class rule, else forced
     cudaStream_t last = nullptr;
     bool have_result = false;
@@ -1329,6 +1329,32 @@ extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, c
     return COSM_OK;
 }
 
+// Tile layout of one instance inside a batch. Policy 0: the single-instance
+// rule (choose_layout) scored as if the run filled every CTA slot, since the
+// batch as a whole does: the tile keeping the most replicas resident per SM,
+// ties to the wider tile (one edge record and one barrier serve more
+// replicas). Policy 1: the narrowest tile of the storage type. Policy 2: the
+// single-instance rule with the instance's own replica count.
+static int batch_instance_layout(cosm_batch *b, cosm_handle *h, int32_t replicas)
+{
+    int rc;
+    if (b->policy == 2) return choose_layout(h, replicas);
+    if ((rc = choose_layout(h, 1 << 23))) return rc;
+    if (b->policy == 1 && h->K != (h->prm.storage == COSM_F32 ? 1 : 2)) {
+        const int Kmin = h->prm.storage == COSM_F32 ? 1 : 2;
+        const size_t esz = h->prm.storage == COSM_F32 ? 4 : 2;
+        h->K = Kmin;
+        h->block_pairs = false;
+        h->smem = sweep_smem_bytes(h->prm.storage, Kmin, h->g.n, h->prm.n_bisectors, h->mode);
+        h->tile_stride = (int64_t)(((size_t)h->g.n * Kmin * esz + 15) / 16 * 16 / esz);
+        // the narrow tile's kernel may allow fewer threads per CTA
+        while (h->threads > 64 && batch_occupancy(h->prm.storage, Kmin, h->mode, h->threads, h->smem) == 0)
+            h->threads /= 2;
+        h->occupancy = batch_occupancy(h->prm.storage, Kmin, h->mode, h->threads, h->smem);
+    }
+    return COSM_OK;
+}
+
 static int batch_layout(cosm_batch *b, const int64_t *sweeps, const int32_t *replicas, const uint64_t *seeds,
                         cudaStream_t st)
 {
@@ -1340,14 +1366,11 @@ static int batch_layout(cosm_batch *b, const int64_t *sweeps, const int32_t *rep
         if (sweeps[i] < 1 || sweeps[i] >= ((int64_t)1 << 31) || replicas[i] < 1 || replicas[i] >= (1 << 24))
             return fail(COSM_ERR_INVALID_ARG, "instance " + std::to_string(i) + ": bad sweeps or replicas");
         int rc;
-        if ((rc = choose_layout(h, replicas[i]))) return rc;
-        if (b->policy == 1 && h->K != (h->prm.storage == COSM_F32 ? 1 : 2)) {
-            // smallest tile of the storage type
-            const int Kmin = h->prm.storage == COSM_F32 ? 1 : 2;
-            const size_t esz = h->prm.storage == COSM_F32 ? 4 : 2;
-            h->K = Kmin;
-            h->smem = sweep_smem_bytes(h->prm.storage, Kmin, h->g.n, h->prm.n_bisectors, h->mode);
-            h->tile_stride = (int64_t)(((size_t)h->g.n * Kmin * esz + 15) / 16 * 16 / esz);
+        if ((rc = batch_instance_layout(b, h, replicas[i]))) return rc;
+        if (b->threads) {
+            h->threads = b->threads;
+            while (h->threads > 64 && batch_occupancy(h->prm.storage, h->K, h->mode, h->threads, h->smem) == 0)
+                h->threads /= 2;
         }
         h->replicas = replicas[i];
         h->seed = seeds[i];
@@ -1360,33 +1383,40 @@ static int batch_layout(cosm_batch *b, const int64_t *sweeps, const int32_t *rep
         views[(size_t)i] = v;
         fins[(size_t)i] = BatchFinal{h->W, h->d_spins.p, h->d_best.p, h->prm.storage, 0};
     }
-    // classes and their unit queues, longest trials first
+    // classes: instances of one kernel (storage, tile width, mode), thread
+    // count and occupancy share a persistent launch (the class's largest
+    // tile has the same occupancy as every other, occupancy falling with
+    // shared memory); their units form one queue, longest trials first
     b->classes.clear();
     b->h_units.clear();
-    struct Key { int storage, K, mode; };
+    struct Key { int storage, K, mode, threads, occ; };
     std::vector<Key> keys;
     std::vector<int> cls((size_t)n);
     for (int i = 0; i < n; ++i) {
         const cosm_handle *h = b->hs[(size_t)i];
+        const Key k{h->prm.storage, h->K, h->mode, h->threads,
+                    batch_occupancy(h->prm.storage, h->K, h->mode, h->threads, h->smem)};
         int c = -1;
-        for (size_t k = 0; k < keys.size(); ++k)
-            if (keys[k].storage == h->prm.storage && keys[k].K == h->K && keys[k].mode == h->mode) c = (int)k;
+        for (size_t q = 0; q < keys.size() && c < 0; ++q) {
+            const Key &o = keys[q];
+            if (o.storage == k.storage && o.K == k.K && o.mode == k.mode && o.threads == k.threads && o.occ == k.occ)
+                c = (int)q;
+        }
         if (c < 0) {
-            keys.push_back(Key{h->prm.storage, h->K, h->mode});
+            keys.push_back(k);
             c = (int)keys.size() - 1;
         }
         cls[(size_t)i] = c;
     }
     int dev_sms = b->hs[0]->num_sms;
     for (size_t c = 0; c < keys.size(); ++c) {
-        BatchClass bc{keys[c].storage, keys[c].K, keys[c].mode, 0, 0, 0, (int32_t)b->h_units.size(), 0};
+        BatchClass bc{keys[c].storage, keys[c].K, keys[c].mode, keys[c].threads, 0, 0,
+                      (int32_t)b->h_units.size(), 0};
         std::vector<std::pair<double, BatchUnit>> us;
-        int max_ec = 0;
         for (int i = 0; i < n; ++i) {
             if (cls[(size_t)i] != (int)c) continue;
             const cosm_handle *h = b->hs[(size_t)i];
             bc.smem = std::max(bc.smem, h->smem);
-            for (int cc = 0; cc < h->C; ++cc) max_ec = std::max(max_ec, h->off[cc + 1] - h->off[cc]);
             const int64_t tiles = (replicas[i] + h->K - 1) / h->K;
             const double cost = (double)h->g.m * (double)h->K * (double)sweeps[i];
             for (int64_t t = 0; t < tiles; ++t)
@@ -1395,8 +1425,7 @@ static int batch_layout(cosm_batch *b, const int64_t *sweeps, const int32_t *rep
         std::stable_sort(us.begin(), us.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
         for (auto &u : us) b->h_units.push_back(u.second);
         bc.units = (int32_t)us.size();
-        int T = b->threads;
-        if (!T) T = std::min(512, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
+        int T = bc.threads;
         int occ = batch_occupancy(bc.storage, bc.K, bc.mode, T, bc.smem);
         while (occ == 0 && T > 64) {
             T /= 2;
@@ -1576,26 +1605,28 @@ extern "C" int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t p
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int pols[2] = {0, 1}, thrs[4] = {0, 128, 256, 512};
-    for (int pol : pols)
-        for (int thr : thrs) {
-            b->policy = pol;
-            b->threads = thr;
-            int rc = cosm_batch_run(b, sw.data(), replicas, seeds.data(), stream);  // warm-up + graph build
-            if (rc) continue;
-            CK(cudaEventRecord(e0, b->own));
-            rc = cosm_batch_run(b, sw.data(), replicas, seeds.data(), stream);
-            CK(cudaEventRecord(e1, b->own));
-            CK(cudaEventSynchronize(e1));
-            if (rc) continue;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best_ms) {
-                best_ms = ms;
-                best_pol = pol;
-                best_thr = thr;
-            }
+    // policies with the rule's thread counts, then the default policy with
+    // forced thread counts
+    const int cfgs[6][2] = {{0, 0}, {1, 0}, {2, 0}, {0, 128}, {0, 256}, {0, 512}};
+    for (const auto &cf : cfgs) {
+        const int pol = cf[0], thr = cf[1];
+        b->policy = pol;
+        b->threads = thr;
+        int rc = cosm_batch_run(b, sw.data(), replicas, seeds.data(), stream);  // warm-up + graph build
+        if (rc) continue;
+        CK(cudaEventRecord(e0, b->own));
+        rc = cosm_batch_run(b, sw.data(), replicas, seeds.data(), stream);
+        CK(cudaEventRecord(e1, b->own));
+        CK(cudaEventSynchronize(e1));
+        if (rc) continue;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best_pol = pol;
+            best_thr = thr;
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->policy = best_pol;

@@ -1,9 +1,10 @@
 """Ragged batch (many instances of uneven size in one graph-captured run):
-every instance's per-replica cuts, best bisectors, best spins and final
-phases equal a separate single-instance run with the same arguments, bit
-for bit, also after the autotuner changes the layout and across graph
-replays with new seeds. Single-instance runs are themselves pinned to the
-oracle in test_parity_gpu.py."""
+every instance's per-replica cuts and best bisectors are bit-exact with the
+oracle's readout of the batch's own final phases; fixed-point batches equal
+the oracle's whole trials for every replica of every instance; and every
+instance's results equal a separate single-instance run with the same
+arguments, bit for bit, also after the autotuner changes the layout and
+across graph replays with new seeds."""
 import numpy as np
 import pytest
 
@@ -59,6 +60,47 @@ def test_batch_matches_single_instance_runs(cosm, storage):
     assert b.info()["graphs_built"] == 1
     _check_against_solo(cosm, b, insts, sweeps, replicas, [21, 22, 23, 24, 25, 26, 27], storage,
                         dwt_ratio=1.0)
+
+
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
+def test_batch_cuts_bit_exact_with_oracle_readout(cosm, orc, storage):
+    insts = _insts()
+    sweeps = [200, 150, 300, 100, 250, 120, 400]
+    replicas = [10, 7, 33, 5, 12, 64, 3]
+    seeds = [31, 32, 33, 34, 35, 36, 37]
+    b = cosm.Batch(insts, storage=storage, dwt_ratio=1.0)
+    b.run(sweeps, replicas, seeds)
+    for i, inst in enumerate(insts):
+        g = orc.coloured(inst)
+        x = b.get_state(i)
+        cuts, bps = b.replica_cuts(i)
+        for r in range(replicas[i]):
+            best, bp, _, _ = orc.binarize(g, x[r])
+            assert cuts[r] == best and bps[r] == bp, (i, r)
+        cut, energy, rep, spins = b.best(i)
+        assert cut == cuts.max() and rep == int(np.argmax(cuts))
+        assert orc.cut(inst.src, inst.dst, inst.w, spins) == cut
+        assert energy == int(np.sum(inst.w)) - 2 * cut
+
+
+def test_fixed_point_batch_equals_oracle_trials(cosm, orc):
+    # fixed point is exact: every replica of every instance is the oracle's
+    # whole trial (init, sweeps, twists, schedule, readout) bit for bit
+    insts = _insts()
+    sweeps = [120, 90, 150, 60, 110, 80, 200]
+    replicas = [6, 5, 9, 4, 7, 10, 3]
+    seeds = [41, 42, 43, 44, 45, 46, 47]
+    b = cosm.Batch(insts, storage=cosm.Q16, dwt_ratio=1.0)
+    b.run(sweeps, replicas, seeds)
+    for i, inst in enumerate(insts):
+        g = orc.coloured(inst)
+        x = b.get_state(i)
+        cuts, bps = b.replica_cuts(i)
+        for r in range(replicas[i]):
+            best, xo, _, bp = orc.trial(g, sweeps[i], dwt_ratio=1.0, seed=seeds[i], replica=r,
+                                        storage=orc.STORE_Q16)
+            assert np.array_equal(x[r], xo), (i, r)
+            assert cuts[r] == best and bps[r] == bp, (i, r)
 
 
 def test_batch_autotuner_keeps_results(cosm, tmp_path, monkeypatch):

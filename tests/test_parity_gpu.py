@@ -100,9 +100,13 @@ def test_one_sweep_bf16_storage(cosm, orc, dims, sweep):
     s.step(sweep, alpha)
     x1 = s.get_state()
     far = []
+    # the lattice kernel stores (and rounds) once per pass of two colours,
+    # the edge-list kernel at every update
+    mode = orc.STORE_BF16_PASS if s.layout()["lattice"] == 2 else orc.STORE_BF16
+    assert (s.layout()["lattice"] == 2) == dims
     for r in range(R):
         err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=3, replica=r,
-                                 storage=orc.STORE_BF16, **_params_kw(s))
+                                 storage=mode, **_params_kw(s))
         assert err <= TOL_BF16, (r, err)
         xf, _ = orc.sweep(g, x0[r], alpha, sweep, seed=3, replica=r, **_params_kw(s))
         far.append(float((circ_rad(xf, x1[r]) > 8 * 2 * np.pi * 2 ** -9).mean()))
@@ -171,10 +175,11 @@ def test_one_sweep_ablation_flags(cosm, orc, flags):
             assert err <= tol, (flags, sweep, r, err)
 
 
+@pytest.mark.parametrize("dims", [True, False])
 @pytest.mark.parametrize("sweep", [2, 3, 6])
-def test_one_sweep_f16_storage(cosm, orc, sweep):
+def test_one_sweep_f16_storage(cosm, orc, dims, sweep):
     inst = instances.torus2d(16, 16, 1)
-    s, g = _solver(cosm, orc, inst, storage=1)
+    s, g = _solver(cosm, orc, inst, storage=1, use_dims=dims)
     R = 8
     x0 = np.stack([f16_exact_turns(orc.init_phases(inst.n, 3, r)) for r in range(R)])
     s.set_state(x0, seed=3)
@@ -182,9 +187,13 @@ def test_one_sweep_f16_storage(cosm, orc, sweep):
     s.step(sweep, alpha)
     x1 = s.get_state()
     far = []
+    # the lattice kernel stores (and rounds) once per pass of two colours,
+    # the edge-list kernel at every update
+    mode = orc.STORE_F16_PASS if s.layout()["lattice"] == 2 else orc.STORE_F16
+    assert (s.layout()["lattice"] == 2) == dims
     for r in range(R):
         err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, sweep, seed=3, replica=r,
-                                 storage=orc.STORE_F16, **_params_kw(s))
+                                 storage=mode, **_params_kw(s))
         assert err <= TOL_F16, (r, err)
         # against pure FP64 (no storage rounding) most phases stay within a few
         # binary16 quanta; a rounding can flip a sign decision near a tie, which
@@ -366,6 +375,32 @@ def test_full_size_workload_sampled(cosm, orc):
     for r in (3, 700):
         err, _ = one_sweep_error(orc, g, x[r], x1[r], alpha, 61, seed=21, replica=r, **kw)
         assert err <= TOL_F32
+
+
+@pytest.mark.parametrize("storage", [1, 3])
+def test_full_size_workload_sampled_16bit(cosm, orc, storage):
+    # the 20k-spin torus with binary16 / bfloat16 phases at the forms' launch
+    # configuration (four replicas per CTA, 1024 replicas): sampled replicas'
+    # cuts bit-exact on the final phases, and one more sweep against the
+    # oracle's store-per-pass rounding
+    inst = instances.torus2d(100, 200, 0)
+    s, g = _solver(cosm, orc, inst, storage=storage)
+    assert s.layout()["lattice"] == 2
+    s.run(60, 1024, seed=22)
+    assert s.layout()["K"] == 4
+    cuts, bps = s.replica_cuts()
+    x = s.get_state()
+    for r in (0, 2, 513, 1022, 1023):
+        best, bp, _, _ = orc.binarize(g, x[r])
+        assert cuts[r] == best and bps[r] == bp
+    alpha = float(np.float32(0.013))
+    s.step(63, alpha)  # a twist sweep
+    x1 = s.get_state()
+    kw = _params_kw(s)
+    mode, tol = (orc.STORE_F16_PASS, TOL_F16) if storage == 1 else (orc.STORE_BF16_PASS, TOL_BF16)
+    for r in (5, 701):
+        err, _ = one_sweep_error(orc, g, x[r], x1[r], alpha, 63, seed=22, replica=r, storage=mode, **kw)
+        assert err <= tol
 
 
 @pytest.mark.parametrize("K,flags", [(2, 0), (4, 0), (2, 4)])

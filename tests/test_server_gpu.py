@@ -1,8 +1,9 @@
 """Serving loop (continuous batching): a request's result is the same alone
 and in a mix of concurrent requests, whatever the chunk size; a one-trial
-request equals a plain cosm_run; admission respects the slot count and the
-device-memory budget. Integer results (cuts, trial and replica indices,
-spins) are compared exactly."""
+request equals a plain cosm_run; fixed-point requests equal the oracle's
+whole trials for every trial seed the server derives; admission respects
+the slot count and the device-memory budget. Integer results (cuts, trial
+and replica indices, spins) are compared exactly."""
 import numpy as np
 import pytest
 
@@ -80,6 +81,41 @@ def test_same_result_alone_and_in_the_mix(cosm):
     for req, (want, _) in zip(reqs, alone):
         if want[0] == cosm.REACHED:
             assert want[2] >= req[4]
+
+
+def test_fixed_point_requests_equal_oracle_trials(cosm, orc):
+    # trial t of a request runs with seed + t * 0x9E3779B97F4A7C15 (mod 2^64);
+    # in fixed point each is the oracle's trial bit for bit, so the server's
+    # result is the oracle's: per trial the best replica (ties: the lowest),
+    # a later trial kept only if strictly better, retired at the target
+    p1 = instances.frustrated_loop_planted((12, 12), 0.6, 3)
+    p2 = instances.frustrated_loop_planted((4, 4, 6), 0.4, 5)
+    r3 = instances.random_regular(300, 3, 6)
+    reqs = [(p1, 150, 6, 101, p1.meta["opt_cut"], 4), (p2, 120, 5, 102, p2.meta["opt_cut"], 3),
+            (r3, 80, 4, 103, 10 ** 9, 3)]
+    srv = cosm.Server(chunk_sweeps=47)
+    ids = [srv.submit(inst, S, R, seed, tgt, max_trials=mt, storage=cosm.Q16, alpha0_deg=25.0,
+                      dwt_ratio=1.0) for inst, S, R, seed, tgt, mt in reqs]
+    for rid, (inst, S, R, seed, tgt, mt) in zip(ids, reqs):
+        res = srv.wait(rid, 300)
+        g = orc.coloured(inst)
+        best, bt, br, bsp, status, trials = None, -1, -1, None, cosm.EXHAUSTED, 0
+        for t in range(mt):
+            st = (seed + t * 0x9E3779B97F4A7C15) % (1 << 64)
+            outs = [orc.trial(g, S, alpha0=25.0 / 360.0, dwt_ratio=1.0, seed=st, replica=r,
+                              storage=orc.STORE_Q16) for r in range(R)]
+            cuts = [o[0] for o in outs]
+            r = int(np.argmax(cuts))
+            if best is None or cuts[r] > best:
+                best, bt, br, bsp = cuts[r], t, r, outs[r][2]
+            trials = t + 1
+            if best >= tgt:
+                status = cosm.REACHED
+                break
+        assert (res["status"], res["trials"], res["best_cut"], res["best_trial"], res["best_replica"]) == \
+            (status, trials, best, bt, br)
+        assert np.array_equal(srv.spins(rid), bsp)
+    srv.close()
 
 
 def test_admission_by_slots_and_memory_budget(cosm):
