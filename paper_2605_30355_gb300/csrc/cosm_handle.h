@@ -110,6 +110,7 @@ struct cosm_handle {
     int replicas = 0;
     int K = 0, threads = 0, occupancy = 0, grid = 0;
     bool block_pairs = false;  // binary32 lattice tiles of two replicas: two 2x2 blocks per thread (even pass)
+    bool staged = false;       // binary32 edge lists: colour records staged in shared memory
     size_t smem = 0;
     int64_t tile_stride = 0;  // storage elements per tile
     uint64_t seed = 0;

@@ -73,7 +73,17 @@ struct InstView {
     int32_t words;        // (n + 31) / 32
     int32_t paired;       // binary32 lattice tiles: packed f32x2 passes (0 scalar, 1 single blocks, 2 block pairs in the even pass)
     int32_t wrap_p;       // binary32 lattice phases: wrapped on sweeps s with s % wrap_p == 0
+    // binary32 edge lists: bytes of the record and weight parts of each of
+    // the two shared-memory staging buffers after the tile (0: records are
+    // read from global memory)
+    int32_t stage_ij;
+    int32_t stage_w;
 };
+
+// Bytes of the record and weight parts of one staging buffer for colours of
+// at most max_ec edges (16-byte chunks covering the colour's range).
+inline int32_t stage_ij_bytes(int max_ec) { return (int32_t)(((size_t)(max_ec + 8) * 4 + 15) & ~(size_t)15); }
+inline int32_t stage_w_bytes(int max_ec) { return (int32_t)(((size_t)max_ec + 32 + 15) & ~(size_t)15); }
 
 // Single-instance launch: the instance plus the CTAs' segment lists.
 struct KernelArgs {

@@ -1258,8 +1258,11 @@ __device__ __forceinline__ f32x2 p_pack(float lo, float hi)
 
 // One batch of B edges per thread (edges e0, e0 + nt, ...); kTail: the batch
 // may run past the end e1 of its colour (loads of slot 0, stores skipped).
-template <int K, int B, bool kWrapEach, bool kTail>
-__device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, float alpha, int e0, int e1, int nt)
+// kStaged: the colour's records sit in shared memory (edge e's record at
+// sij + 4 e, its weight at sw + e), else they are read from global memory.
+template <int K, int B, bool kWrapEach, bool kTail, bool kStaged = false>
+__device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, float alpha, int e0, int e1, int nt,
+                                              uint32_t sij = 0, uint32_t sw = 0)
 {
     constexpr uint32_t E = K * 4;  // bytes per slot
     uint32_t ai[B], aj[B];
@@ -1270,8 +1273,13 @@ __device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, fl
         uint32_t rec = 0;
         int w = 0;
         if (!kTail || e < e1) {
-            rec = __ldg(a.ij + e);
-            w = __ldg(a.w + e);
+            if constexpr (kStaged) {
+                asm volatile("ld.shared.b32 %0, [%1];" : "=r"(rec) : "r"(sij + 4u * (uint32_t)e) : "memory");
+                asm volatile("ld.shared.s8 %0, [%1];" : "=r"(w) : "r"(sw + (uint32_t)e) : "memory");
+            } else {
+                rec = __ldg(a.ij + e);
+                w = __ldg(a.w + e);
+            }
         }
         ai[u] = xb + (rec & 0xFFFFu) * E;
         aj[u] = xb + (rec >> 16) * E;
@@ -1348,6 +1356,69 @@ __device__ __forceinline__ void general_colours_x2(const InstView &a, float *xs,
         for (; e0 + (B - 1) * nt < e1; e0 += B * nt) edge_batch_x2<K, B, kWrapEach, false>(a, xb, alpha, e0, e1, nt);
         if (e0 < e1) edge_batch_x2<K, B, kWrapEach, true>(a, xb, alpha, e0, e1, nt);
         __syncthreads();
+    }
+}
+
+// Edge records staged in shared memory: while colour c runs, colour c + 1's
+// records (packed slots and weights) stream into the other of two buffers
+// with cp.async (16-byte chunks, cached in L2 only), so a colour's record
+// loads are shared-memory loads instead of global loads on the critical
+// path. A buffer holds the 16-byte chunks that cover the colour: records
+// from off[c] rounded down to a multiple of 4, weights from off[c] rounded
+// down to a multiple of 16 (the device arrays are padded so the chunks after
+// the last colour exist).
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void stage_colour(const InstView &a, int c, uint32_t buf)
+{
+    const int e0 = __ldg(a.off + c), e1 = __ldg(a.off + c + 1);
+    const int i0 = e0 & ~3, i1 = (e1 + 3) & ~3;
+    const int w0 = e0 & ~15, w1 = (e1 + 15) & ~15;
+    const int nij = (i1 - i0) >> 2, nw = (w1 - w0) >> 4;
+    const uint32_t bw = buf + (uint32_t)a.stage_ij;
+    for (int k = threadIdx.x; k < nij + nw; k += blockDim.x) {
+        if (k < nij) cp_async16(buf + 16u * (uint32_t)k, a.ij + i0 + 4 * k);
+        else cp_async16(bw + 16u * (uint32_t)(k - nij), a.w + w0 + 16 * (k - nij));
+    }
+    cp_async_commit();
+}
+
+// The colours of one sweep with staged records. `cur` is the buffer that
+// holds colour 0's records (staged by the previous sweep, or here when
+// `first`); the last colour stages colour 0 of the next sweep unless `last`.
+template <int K, int B, bool kWrapEach>
+__device__ __forceinline__ void general_colours_x2s(const InstView &a, float *xs, float alpha, uint32_t stage,
+                                                    bool first, bool last, int &cur)
+{
+    static_assert(K == 1 || K == 2 || K == 4, "K");
+    static_assert(K > 1 || B % 2 == 0, "B");
+    const int nt = blockDim.x;
+    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
+    const uint32_t SB = (uint32_t)(a.stage_ij + a.stage_w);
+    if (first) {
+        stage_colour(a, 0, stage + (uint32_t)cur * SB);
+        cp_async_wait_all();
+        __syncthreads();
+    }
+    for (int c = 0; c < a.C; ++c) {
+        if (c + 1 < a.C) stage_colour(a, c + 1, stage + (uint32_t)(cur ^ 1) * SB);
+        else if (!last) stage_colour(a, 0, stage + (uint32_t)(cur ^ 1) * SB);
+        const int ec = __ldg(a.off + c), e1 = __ldg(a.off + c + 1);
+        const uint32_t buf = stage + (uint32_t)cur * SB;
+        const uint32_t sij = buf - 4u * (uint32_t)(ec & ~3);
+        const uint32_t sw = buf + (uint32_t)a.stage_ij - (uint32_t)(ec & ~15);
+        int e0 = ec + threadIdx.x;
+        for (; e0 + (B - 1) * nt < e1; e0 += B * nt)
+            edge_batch_x2<K, B, kWrapEach, false, true>(a, xb, alpha, e0, e1, nt, sij, sw);
+        if (e0 < e1) edge_batch_x2<K, B, kWrapEach, true, true>(a, xb, alpha, e0, e1, nt, sij, sw);
+        cp_async_wait_all();
+        __syncthreads();
+        cur ^= 1;
     }
 }
 
@@ -1524,6 +1595,7 @@ __device__ __forceinline__ void block_pass_odd_h2(H *xs, const uint8_t *wnib, fl
     uint32_t goffb = cw ? (uint32_t)(1 - Wd) * E : E;
     const int qlast = Q - Wd;
     int f = threadIdx.x;
+#pragma unroll 4
     for (; f < qlast; f += blockDim.x, ad += step) {
         if (!kFixedColumn) {
             cw = (m == Wd - 1);
@@ -1914,6 +1986,7 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
     int phase = dwt_on ? (int)(sg.s_begin % v.dwt_period) : 1;
     EdgePrefetch<4> pf;
     pf.e0 = -1;
+    int stage_cur = 0;  // staged edge records: the buffer holding colour 0
     for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
         const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));
         const bool dwt = dwt_on && phase == 0;
@@ -2010,10 +2083,19 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                     // of four replicas (their registers)
                     float *xf = reinterpret_cast<float *>(t.xs);
                     constexpr int kB = K == 4 ? 2 : 4;
-                    if (v.wrap_p == 0)
+                    if (v.stage_ij) {
+                        const uint32_t stage = (uint32_t)__cvta_generic_to_shared(smem) +
+                                               (uint32_t)smem_bytes<Store, K>(v.n, v.P, false);
+                        const bool first = s == sg.s_begin, last = s == sg.s_end;
+                        if (v.wrap_p == 0)
+                            general_colours_x2s<K, kB, true>(v, xf, at.x, stage, first, last, stage_cur);
+                        else
+                            general_colours_x2s<K, kB, false>(v, xf, at.x, stage, first, last, stage_cur);
+                    } else if (v.wrap_p == 0) {
                         general_colours_x2<K, kB, true>(v, xf, at.x);
-                    else
+                    } else {
                         general_colours_x2<K, kB, false>(v, xf, at.x);
+                    }
                 } else if constexpr (K == 2 || K == 4) {
                     general_colours_pf<Store, K, 4>(v, t.xs, at.x, pf);
                 } else {

@@ -403,7 +403,12 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
     // device copies
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
-    if ((rc = h->d_ij.ensure((size_t)g.m)) || (rc = h->d_w.ensure((size_t)g.m)) ||
+    // records and weights padded with zeros past a multiple of 16 edges: the
+    // staged edge-list sweep copies whole 16-byte chunks around each colour
+    const size_t m_pad = (((size_t)g.m + 15) & ~(size_t)15) + 16;
+    ij.resize(m_pad, 0u);
+    wv.resize(m_pad, 0);
+    if ((rc = h->d_ij.ensure(m_pad)) || (rc = h->d_w.ensure(m_pad)) ||
         (rc = h->d_orig.ensure((size_t)g.n)) || (rc = h->d_off.ensure((size_t)h->C + 1)) ||
         (rc = h->d_err.ensure(1)) ||
         (rc = h->d_best.ensure(4)) || (rc = h->d_spins.ensure((size_t)g.n))) {
@@ -524,6 +529,19 @@ int cosm::choose_layout(cosm_handle *h, int replicas)
     h->block_pairs = pairs_ok && bestK == 2;
     h->occupancy = bestOcc;
     h->smem = sweep_smem_bytes(p.storage, bestK, h->g.n, P, mode);
+    // binary32 edge lists may stage each colour's records in shared memory
+    // (two buffers after the tile) where that keeps the tile's occupancy.
+    // Measured slower than the global loads in every case tried (the records
+    // stay in L1 / L2, and the copies cost more than their latency), so it is
+    // taken only when the environment variable COSM_STAGE is set.
+    h->staged = false;
+    if (mode == MODE_GENERAL_ && p.storage == COSM_F32 && h->C >= 1 && std::getenv("COSM_STAGE")) {
+        const size_t sb = 2 * (size_t)(stage_ij_bytes(max_ec) + stage_w_bytes(max_ec));
+        if (h->smem + sb <= 227 * 1024 && sweep_occupancy(p.storage, bestK, mode, bestT, h->smem + sb) >= bestOcc) {
+            h->staged = true;
+            h->smem += sb;
+        }
+    }
     const size_t esz = p.storage == COSM_F32 ? 4 : 2;
     h->tile_stride = (int64_t)(((size_t)h->g.n * bestK * esz + 15) / 16 * 16 / esz);
     return COSM_OK;
@@ -611,6 +629,12 @@ InstView cosm::inst_view(cosm_handle *h)
     v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : (h->block_pairs ? 2 : 1);
     v.wrap_p = wrap_period(h->prm.alpha0_deg, h->prm.dwt_ratio, h->prm.dwt_period, h->prm.flags, h->mode,
                            h->prm.storage, h->wbound);
+    if (h->staged) {
+        int max_ec = 0;
+        for (int c = 0; c < h->C; ++c) max_ec = std::max(max_ec, h->off[c + 1] - h->off[c]);
+        v.stage_ij = stage_ij_bytes(max_ec);
+        v.stage_w = stage_w_bytes(max_ec);
+    }
     return v;
 }
 
@@ -1345,6 +1369,7 @@ static int batch_instance_layout(cosm_batch *b, cosm_handle *h, int32_t replicas
         const size_t esz = h->prm.storage == COSM_F32 ? 4 : 2;
         h->K = Kmin;
         h->block_pairs = false;
+        h->staged = false;
         h->smem = sweep_smem_bytes(h->prm.storage, Kmin, h->g.n, h->prm.n_bisectors, h->mode);
         h->tile_stride = (int64_t)(((size_t)h->g.n * Kmin * esz + 15) / 16 * 16 / esz);
         // the narrow tile's kernel may allow fewer threads per CTA

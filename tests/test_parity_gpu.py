@@ -329,6 +329,34 @@ def test_chunked_schedule_matches_single_segment(cosm, orc):
             assert np.array_equal(out[1], ref[1])
 
 
+@pytest.mark.parametrize("K", [1, 2, 4])
+@pytest.mark.parametrize("make,ratio", [(lambda: instances.sparse_gnm(900, 2600, 3), 1.0),
+                                        (lambda: instances.sparse_gnm(600, 1800, 4, wmax=20), 1.0),
+                                        (lambda: instances.random_regular(1000, 3, 1), 1.0)])
+def test_staged_records_equal_global_loads(cosm, orc, K, make, ratio):
+    # binary32 edge lists can stream each colour's records into shared memory
+    # ahead of use (COSM_STAGE); the phases and cuts are those of the
+    # global-load sweep, bit for bit, also across the segment hand-offs of
+    # the wrap-around schedule (records staged again after each hand-off)
+    inst = make()
+    col, C = orc.color_greedy(inst.n, inst.src, inst.dst)
+    out = []
+    for env in ({}, {"COSM_STAGE": "1"}, {"COSM_STAGE": "1", "COSM_GRID_CAP": "5"}):
+        os.environ["COSM_K"] = str(K)
+        os.environ.update(env)
+        try:
+            s = cosm.Solver(inst.n, inst.src, inst.dst, inst.w, color=col, n_colors=C, dwt_ratio=ratio)
+            s.run(301, 6 * K + 1, seed=8)
+            out.append((s.get_state(), s.replica_cuts()[0], s.layout()))
+        finally:
+            for k in ("COSM_K", "COSM_STAGE", "COSM_GRID_CAP"):
+                os.environ.pop(k, None)
+    assert out[0][2]["K"] == K and out[1][2]["K"] == K
+    assert out[1][2]["smem"] > out[0][2]["smem"]  # the staging buffers
+    for x, c, _ in out[1:]:
+        assert np.array_equal(x, out[0][0]) and np.array_equal(c, out[0][1])
+
+
 def test_edge_cases(cosm, orc):
     # single edge, odd n, one replica, one bisector, weights up to 127
     s = cosm.Solver(3, [0], [2], [127], n_bisectors=1)
