@@ -314,6 +314,64 @@ def measure_single(cosm, inst, col, C, prm, storage, R, S, steps, warmup, seed, 
     return out
 
 
+def circ_rad(a, b):
+    d = np.mod(np.asarray(a, dtype=np.float64) - np.asarray(b, dtype=np.float64), 1.0)
+    return 2 * math.pi * np.minimum(d, 1.0 - d)
+
+
+def cut_distribution(cuts):
+    c = np.concatenate(cuts) if isinstance(cuts, list) else np.asarray(cuts)
+    q = np.percentile(c, [1, 10, 50, 90, 99])
+    return {"trials": int(c.size), "mean": float(c.mean()), "std": float(c.std()),
+            "sem": float(c.std() / math.sqrt(c.size)), "min": int(c.min()), "max": int(c.max()),
+            "p1_p10_p50_p90_p99": [float(v) for v in q]}
+
+
+def measure_precision(cosm, inst, col, C, prm, R, S, steps, seed, local, stream, flush, f32_cuts):
+    """Binary16 storage against binary32 on a bounded-degree graph: the
+    final-cut distributions of both over the same trials (seeds), and the
+    per-sweep phase difference of one sweep from an identical state (the
+    FP16 trial's own state before sweeps 1, 10, 100 and 1000), binary16
+    storage against binary32 phases. (The FP64 oracle's side of the same
+    comparison is a GPU test.)"""
+    f = measure_single(cosm, inst, col, C, prm, cosm.F16, R, S, steps, 1, seed, local, stream, flush)
+    d32, d16 = cut_distribution(f32_cuts), cut_distribution(f["cuts"])
+    diff = d16["mean"] - d32["mean"]
+    se = math.sqrt(d16["sem"] ** 2 + d32["sem"] ** 2)
+    per_sweep = {}
+    Rs = 16
+    h16 = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=cosm.F16, **prm)
+    h32 = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=cosm.F32, **prm)
+    init = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=cosm.F16,
+                                     **dict(prm, alpha0_deg=0.0))
+    init.run_range(S, 1, 1, Rs, seed)  # alpha 0, no twist at sweep 1: the initial phases
+    a0 = prm["alpha0_deg"] / 360.0
+    for sw in (1, 10, 100, 1000):
+        if sw == 1:
+            x0 = init.get_state()
+        else:
+            h16.run_range(S, 1, sw - 1, Rs, seed)
+            x0 = h16.get_state()
+        alpha = float(np.float32(a0 * (S - sw) / (S - 1)))
+        h16.set_state(x0, seed=seed)
+        h16.step(sw, alpha)
+        h32.set_state(x0, seed=seed)
+        h32.step(sw, alpha)
+        e = circ_rad(h16.get_state(), h32.get_state())
+        per_sweep[str(sw)] = {"max_rad": float(e.max()), "p99_rad": float(np.percentile(e, 99)),
+                              "median_rad": float(np.median(e)),
+                              "frac_above_2e-3_rad": float((e > 2e-3).mean())}
+    for h_ in (h16, h32, init):
+        h_.close()
+    return {"f32": d32, "f16": d16, "mean_difference_f16_minus_f32": diff,
+            "mean_difference_ci95": [diff - 1.96 * se, diff + 1.96 * se],
+            "f16_updates_per_s": inst.m * S * R / f["t_step"],
+            "per_sweep_f16_vs_f32": per_sweep,
+            "per_sweep_note": f"one sweep of {Rs} replicas from the binary16 trial's own state before "
+                              "that sweep, binary16 storage against binary32 phases, circular "
+                              "difference in rad over all phases"}
+
+
 def measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush):
     """Time-to-target at the oracle's best cut with a longer anneal (Appendix
     A: TTT = t_trial R99; Table X runs 1-2 x 10^6 sweeps per trial on the
@@ -413,6 +471,10 @@ def run_ours(args):
         f32v = batched["f32"]["value"]
         for name in ("f16", "q16"):
             batched[name]["speedup_vs_f32_batch"] = batched[name]["value"] / f32v
+    precision = None
+    if args.forms and args.workload in ("reg3_20k", "reg4_20k") and not args.replicas and not args.sweeps:
+        precision = measure_precision(cosm, inst, col, C, prm, R, S, args.steps, seed, local, stream, flush,
+                                      m["cuts"])
     long_ttt = None
     if args.ttt_steps and default_shape:
         long_ttt = measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush)
@@ -468,6 +530,7 @@ def run_ours(args):
         "roofline": roof,
         "time_to_target": ttt,
         "time_to_target_long": long_ttt,
+        "precision": precision,
         "forms": forms or None,
         "batched": batched,
         "paper_context": {"updates_per_s": 1.41e10, "hardware": "2x Xeon Gold 6544Y, 64 threads, FP32",
