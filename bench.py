@@ -981,7 +981,18 @@ def run_serve(args):
                                               "q16": "u16 fixed-point phases",
                                               "bf16": "bfloat16 phase storage"}[sname])
     pool = serve_pool()
-    rate, window, max_trials = 50.0, args.serve_seconds, 4
+    rate, window, max_trials = 50.0, args.serve_seconds, args.serve_trials
+    R = args.replicas or R
+    S = args.sweeps or S
+    def req_sweeps(inst):
+        # with --serve-scale, anneals lengthen with the instance: S sweeps per
+        # 10,000 spins, at least S
+        return max(S, int(round(S * inst.n / 10000))) if args.serve_scale else S
+
+    desc = desc.replace("32 replicas x 2000 sweeps per trial, up to 4 trials",
+                        f"{R} replicas x {S} sweeps per trial" +
+                        (" per 10,000 spins (at least 2000)" if args.serve_scale else "") +
+                        f", up to {max_trials} trials")
     arr = instances.Stream(77, tag=10)
     gaps = -np.log(1.0 - (arr.u64(100000) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) / rate
     t_arr = np.cumsum(gaps)
@@ -1000,7 +1011,7 @@ def run_serve(args):
         if delay > 0:
             time.sleep(delay)
         inst = pool[int(picks[k])]
-        ids.append(srv.submit(inst, S, R, 1000 + k, inst.meta["opt_cut"], max_trials=max_trials,
+        ids.append(srv.submit(inst, req_sweeps(inst), R, 1000 + k, inst.meta["opt_cut"], max_trials=max_trials,
                               storage=storage, **prm))
     res = [srv.wait(r, 3600) for r in ids]
     t_total = time.perf_counter() - t0
@@ -1008,6 +1019,13 @@ def run_serve(args):
     st = srv.stats()
     srv.close()
     reached = [r for r in res if r["status"] == cosm.REACHED]
+    by_inst = []
+    for k, inst in enumerate(pool):
+        mine = [r for r, pk in zip(res, picks) if int(pk) == k]
+        by_inst.append({"n": int(inst.n), "dims": list(inst.dims), "loop_density": inst.meta.get("rho"),
+                        "sweeps": req_sweeps(inst),
+                        "requests": len(mine), "reached": sum(r["status"] == cosm.REACHED for r in mine),
+                        "mean_trials": float(np.mean([r["trials"] for r in mine])) if mine else None})
     # percentiles over all requests: one that used up its trials without
     # reaching the planted optimum has no time-to-target (infinite)
     ttt_all = np.array([r["ttt"] if r["status"] == cosm.REACHED else np.inf for r in res])
@@ -1034,7 +1052,7 @@ def run_serve(args):
                                         "falls among those)",
                     "ttt_p50_s_reached_only": float(np.percentile(ttt_all[np.isfinite(ttt_all)], 50))
                     if len(reached) else None,
-                    "updates_per_s": updates / t_total, "stats": st},
+                    "updates_per_s": updates / t_total, "stats": st, "by_instance": by_inst},
         "clocks": clocks,
     }
     print(json.dumps(line))
@@ -1140,6 +1158,9 @@ def main(argv=None):
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="default workload: skip the FP16 / fixed-point forms and the ragged batch")
     ap.add_argument("--serve-seconds", type=float, default=10.0, help="serving: arrival window")
+    ap.add_argument("--serve-trials", type=int, default=4, help="serving: trials per request at most")
+    ap.add_argument("--serve-scale", action="store_true",
+                    help="serving: sweeps per trial grow with the instance (S per 10,000 spins)")
     ap.add_argument("--ttt-steps", type=int, default=2,
                     help="default workload: steps of the long-anneal time-to-target leg (0 skips it)")
     ap.add_argument("--ttt-sweeps", type=int, default=1_000_000,

@@ -10,6 +10,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/cosm.h"
@@ -1334,16 +1335,46 @@ extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, c
     *out = nullptr;
     cosm_batch *b = new (std::nothrow) cosm_batch();
     if (!b) return fail(COSM_ERR_NOMEM, "host allocation failed");
+    // instances are created by host worker threads (validation, colouring
+    // and device tables of each run in parallel), each with the caller's
+    // device current; the first failing instance is reported
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        delete b;
+        return fail(COSM_ERR_CUDA, "cudaGetDevice failed");
+    }
+    b->hs.assign((size_t)count, nullptr);
+    std::vector<int> rcs((size_t)count, COSM_OK);
+    std::vector<std::string> msgs((size_t)count);
+    const int workers = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    auto work = [&](int t) {
+        cudaSetDevice(dev);
+        for (int32_t i = t; i < count; i += workers) {
+            const cosm_params *pi = shared_params ? &params[0] : &params[i];
+            int rc = single_only(&graphs[i], pi);
+            if (!rc) rc = cosm_create(&graphs[i], pi, &b->hs[(size_t)i]);
+            if (rc) {
+                rcs[(size_t)i] = rc;
+                msgs[(size_t)i] = g_err;
+            }
+        }
+    };
+    if (workers == 1 || count < 4) {
+        work(0);
+        for (int t = 1; t < workers; ++t) work(t);
+    } else {
+        std::vector<std::thread> pool;
+        for (int t = 0; t < workers; ++t) pool.emplace_back(work, t);
+        for (auto &th : pool) th.join();
+    }
     for (int32_t i = 0; i < count; ++i) {
-        cosm_handle *h = nullptr;
-        int rc = single_only(&graphs[i], shared_params ? &params[0] : &params[i]);
-        if (!rc) rc = cosm_create(&graphs[i], shared_params ? &params[0] : &params[i], &h);
-        if (rc) {
-            std::string msg = "instance " + std::to_string(i) + ": " + g_err;
+        if (rcs[(size_t)i]) {
+            std::string msg = "instance " + std::to_string(i) + ": " + msgs[(size_t)i];
+            const int rc = rcs[(size_t)i];
+            b->hs.erase(std::remove(b->hs.begin(), b->hs.end(), nullptr), b->hs.end());
             cosm_batch_destroy(b);
             return fail(rc, msg);
         }
-        b->hs.push_back(h);
     }
     if (cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess) {
         cosm_batch_destroy(b);
