@@ -1333,6 +1333,11 @@ extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, c
     if (!graphs || !params || !out || count < 1 || count > (1 << 20))
         return fail(COSM_ERR_INVALID_ARG, "bad batch arguments");
     *out = nullptr;
+    // host-side checks of every instance before any device work
+    for (int32_t i = 0; i < count; ++i) {
+        const int rc = single_only(&graphs[i], shared_params ? &params[0] : &params[i]);
+        if (rc) return fail(rc, "instance " + std::to_string(i) + ": " + g_err);
+    }
     cosm_batch *b = new (std::nothrow) cosm_batch();
     if (!b) return fail(COSM_ERR_NOMEM, "host allocation failed");
     // instances are created by host worker threads (validation, colouring
@@ -1351,8 +1356,7 @@ extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, c
         cudaSetDevice(dev);
         for (int32_t i = t; i < count; i += workers) {
             const cosm_params *pi = shared_params ? &params[0] : &params[i];
-            int rc = single_only(&graphs[i], pi);
-            if (!rc) rc = cosm_create(&graphs[i], pi, &b->hs[(size_t)i]);
+            const int rc = cosm_create(&graphs[i], pi, &b->hs[(size_t)i]);
             if (rc) {
                 rcs[(size_t)i] = rc;
                 msgs[(size_t)i] = g_err;
