@@ -372,17 +372,17 @@ def measure_precision(cosm, inst, col, C, prm, R, S, steps, seed, local, stream,
                               "difference in rad over all phases"}
 
 
-def measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush):
+def measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush, storage=None):
     """Time-to-target at the oracle's best cut with a longer anneal (Appendix
     A: TTT = t_trial R99; Table X runs 1-2 x 10^6 sweeps per trial on the
     20,000-spin torus): R replicas x args.ttt_sweeps sweeps per step, FP32
-    phases, after one short warm-up step."""
+    phases unless another storage is given."""
     tgt = _targets().get(args.workload)
     if tgt is None:
         return None
     S = args.ttt_sweeps
-    m = measure_single(cosm, inst, col, C, prm, cosm.F32, R, S, args.ttt_steps, 0, seed + 555, local,
-                       stream, flush)
+    m = measure_single(cosm, inst, col, C, prm, cosm.F32 if storage is None else storage, R, S, args.ttt_steps,
+                       0, seed + 555, local, stream, flush)
     st_ = success_stats(m["cuts"], tgt["cut"], m["t_step"], R)
     top = st_["levels"][0]
     return {"sweeps_per_trial": S, "replicas_per_step": R, "steps": args.ttt_steps,
@@ -455,7 +455,7 @@ def run_ours(args):
                            "unit": "updates/s", "ms_per_step": f["t_step"] * 1000.0,
                            "replicas_per_cta": f["layout"]["K"],
                            "roofline": roofline(cosm, inst, prm, st, f["layout"], updates, f["t_step"],
-                                                f["clocks"]),
+                                                f["clocks"], args.workload, R, S),
                            "clocks": f["clocks"]}
             tgt = _targets().get(args.workload)
             if tgt is not None:
@@ -478,6 +478,15 @@ def run_ours(args):
     long_ttt = None
     if args.ttt_steps and default_shape:
         long_ttt = measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush)
+        if long_ttt is not None and args.forms:
+            # the 2-byte forms on the same long anneal (same seeds)
+            long_ttt["forms"] = {}
+            for name, st in (("f16", cosm.F16), ("q16", cosm.Q16)):
+                f = measure_long_ttt(cosm, args, inst, col, C, prm, R, seed, local, stream, flush, storage=st)
+                f.pop("levels", None)
+                f["TTT_speedup_vs_f32"] = (long_ttt["TTT_s"] / f["TTT_s"]
+                                           if f["TTT_s"] and long_ttt["TTT_s"] else None)
+                long_ttt["forms"][name] = f
 
     # ---- the best state over all ranks (untimed): one max-reduce, one broadcast
     solver = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=storage, **prm)
@@ -504,7 +513,7 @@ def run_ours(args):
                "levels": st_["levels"]}
 
     # ---- roofline of the sweep kernel: shared memory and FP32 issue
-    roof = roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks)
+    roof = roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks, args.workload, R, S)
 
     line = {
         "metric": metric_name(args.workload),
@@ -544,13 +553,20 @@ def run_ours(args):
     return line
 
 
-# ncu records of the kernels' memory traffic, each taken at the kernel source
-# whose hash it names (the first 12 hex digits of the SHA-256 of
-# cosm_kernels.cu): reported only while that source is unchanged, else null.
-# Keys: (kernel, storage, K). Values: shared-memory bytes per edge-replica
-# update (shared wavefronts x 128 B / updates), DRAM bytes (read + write)
-# per update, source hash.
-NCU_TRAFFIC = {}
+# ncu records of the sweep kernel's memory traffic on the bench's workloads,
+# each taken at the kernel source whose hash it names (the first 12 hex
+# digits of the SHA-256 of cosm_kernels.cu): reported only while that source
+# is unchanged, else null. Keys: (workload, storage). Values: shared-memory
+# bytes per edge-replica update (shared wavefronts x 128 B / updates, from a
+# small capture of the same kernel and layout), and DRAM bytes (read +
+# write) of one full-size launch with its (replicas, sweeps) -- DRAM traffic
+# follows the state, not the sweeps, so it is not scaled from a small case.
+NCU_TRAFFIC = {
+    ("torus20k", "f32"): (8.60, (83.77e6, 1024, 100_000), "755e8d0eb189"),
+    ("torus20k", "f16"): (4.43, None, "755e8d0eb189"),
+    ("torus20k", "q16"): (4.54, None, "755e8d0eb189"),
+    ("reg3_20k", "f32"): (23.8, None, "755e8d0eb189"),
+}
 
 # Algorithmic cost of one edge-replica update of eq. (6): FP32 operations
 # (the difference, the biased sign, two phase updates, two wraps) and, per
@@ -590,7 +606,7 @@ def algorithmic_bytes(inst, prm, storage_bytes, lattice, K):
     return 4.0 * b + dwt + e / max(1, K)
 
 
-def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks, kernel="sweep"):
+def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks, workload=None, replicas=0, sweeps=0):
     """Rooflines of the sweep kernel, which is the whole timed step but for a
     finaliser of microseconds, so the step time is its launch duration:
     - smem (the bound of the method's own count): algorithmic shared-memory
@@ -623,8 +639,7 @@ def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks, kernel="
                    "peak_source": f"measured FP32 issue rate: {pr['fp32_scalar']:.1f} ops/clk/SM scalar fma, "
                                   f"{pr['fp32_packed']:.1f} packed f32x2 fma; x {sms} SMs x {mhz:.0f} MHz, "
                                   "of measured"}
-    key = (kernel + ("_lattice" if layout["lattice"] == 2 else "_edges"),
-           {cosm.F32: "f32", cosm.F16: "f16", cosm.Q16: "q16", cosm.BF16: "bf16"}[storage], K)
+    key = (workload, {cosm.F32: "f32", cosm.F16: "f16", cosm.Q16: "q16", cosm.BF16: "bf16"}[storage])
     rec = NCU_TRAFFIC.get(key)
     src = kernel_source_hash()
     smem["traffic"] = None
@@ -633,9 +648,10 @@ def roofline(cosm, inst, prm, storage, layout, updates, t_step, clocks, kernel="
         smem["smem_measured"] = {"bytes_per_update": rec[0], "achieved": rec[0] * rate / 1e9,
                                  "frac": rec[0] * rate / 1e9 / smem_peak,
                                  "source": "ncu shared wavefronts x 128 B per update, kernel source " + rec[2]}
-        smem["traffic"] = rec[1] * updates
-        smem["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum per update, scaled to "
-                                  "one launch; kernel source " + rec[2])
+        if rec[1] is not None and rec[1][1:] == (replicas, sweeps):
+            smem["traffic"] = rec[1][0]
+            smem["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one full-size "
+                                      "launch; kernel source " + rec[2])
     return smem
 
 
@@ -679,6 +695,7 @@ def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e
     t_max = max_over_ranks(t_step, "cuda")
     updates = sum(int(i.m) * S * r for i, r in zip(insts, reps))
     info = batch.info()
+    lays = [batch.layout(i) for i in range(len(insts))]
     batch.close()
     e2e_t = None
     h2d = sum(i.src.nbytes + i.dst.nbytes + i.w.nbytes for i in insts)
@@ -697,8 +714,8 @@ def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e
     pr = probes(cosm)
     sms = props.multi_processor_count
     b = 4 if storage == cosm.F32 else 2
-    algo = sum(int(i.m) * S * r * algorithmic_bytes(i, prm, b, 2 if i.dims and len(i.dims) == 2 else 0,
-                                                    1) for i, r in zip(insts, reps)) / updates
+    algo = sum(int(i.m) * S * r * algorithmic_bytes(i, prm, b, lay["lattice"], lay["K"])
+               for i, r, lay in zip(insts, reps, lays)) / updates
     smem_peak = pr["smem_bpc"] * sms * mhz * 1e6 / 1e9
     ops_clk = max(pr["fp32_scalar"], pr["fp32_packed"])
     alu_peak = ops_clk * sms * mhz * 1e6 / 1e12
@@ -717,7 +734,7 @@ def measure_batch(cosm, args, rank, ws, local, stream, flush, steps, warmup, e2e
                      "frac": algo * rate / 1e9 / smem_peak, "traffic": None, "bytes_per_update": algo,
                      "peak_source": f"measured shared-memory bandwidth ({pr['smem_bpc']:.1f} B/clk/SM) x "
                                     f"{sms} SMs x {mhz:.0f} MHz, of measured; bytes per update by the "
-                                    "method's count at one replica per edge record",
+                                    "method's count with each instance's tile width",
                      "alu": {"bound": "alu", "achieved": ALU_OPS_PER_UPDATE * rate / 1e12, "peak": alu_peak,
                              "unit": "Tops/s", "frac": ALU_OPS_PER_UPDATE * rate / 1e12 / alu_peak,
                              "ops_per_update": ALU_OPS_PER_UPDATE}},

@@ -325,6 +325,11 @@ int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t probe_sweeps
  * rule), out[7] CTAs over all classes. */
 int cosm_batch_info(cosm_batch *b, int64_t out[8]);
 
+/* Layout of instance i in the last run, as cosm_layout gives it for a
+ * single instance (out[0] replicas per tile, out[1] threads per CTA, out[2]
+ * shared bytes per CTA, ...). COSM_ERR_STATE before a run. */
+int cosm_batch_layout(cosm_batch *b, int32_t i, int32_t out[8]);
+
 /* Releases the batch and all its instances. NULL is a no-op. */
 void cosm_batch_destroy(cosm_batch *b);
 

@@ -55,7 +55,7 @@ EXPORTS = (
     "cosm_server_stats", "cosm_server_destroy", "cosm_last_error", "cosm_get_replica_energies",
     "cosm_get_replica_bisectors", "cosm_get_trace", "cosm_qubo_to_ising", "cosm_probe_fp32",
     "cosm_run_range", "cosm_get_success", "cosm_export_state", "cosm_import_state",
-    "cosm_set_wait_limit", "cosm_inject_fault",
+    "cosm_set_wait_limit", "cosm_inject_fault", "cosm_batch_layout",
 )
 
 
@@ -134,6 +134,7 @@ def _load():
         "cosm_batch_get_state": (C.c_int, [P, i32, P]),
         "cosm_batch_tune": (C.c_int, [P, P, i64, P]),
         "cosm_batch_info": (C.c_int, [P, P]),
+        "cosm_batch_layout": (C.c_int, [P, i32, P]),
         "cosm_batch_destroy": (None, [P]),
         "cosm_server_default_config": (None, [P]),
         "cosm_server_create": (C.c_int, [P, P]),
@@ -421,6 +422,13 @@ class Batch:
         x = np.zeros((self.replicas[i], self.n[i]), dtype=np.float64)
         _check(_lib.cosm_batch_get_state(self._h, int(i), _p(x)))
         return x
+
+    def layout(self, i):
+        """Layout of instance i in the last run (cosm_batch_layout)."""
+        out = (C.c_int32 * 8)()
+        _check(_lib.cosm_batch_layout(self._h, int(i), out))
+        keys = ("K", "threads", "smem", "occupancy", "lattice", "grid", "launches", "colors")
+        return dict(zip(keys, list(out)))
 
     def info(self):
         out = (C.c_int64 * 8)()

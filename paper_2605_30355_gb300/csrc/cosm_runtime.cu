@@ -1701,6 +1701,13 @@ extern "C" int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t p
     return COSM_OK;
 }
 
+extern "C" int cosm_batch_layout(cosm_batch *b, int32_t i, int32_t out[8])
+{
+    if (!b || i < 0 || i >= (int32_t)b->hs.size()) return fail(COSM_ERR_INVALID_ARG, "bad instance index");
+    if (!b->have_result) return fail(COSM_ERR_STATE, "no batch run yet");
+    return cosm_layout(b->hs[(size_t)i], out);
+}
+
 extern "C" int cosm_batch_info(cosm_batch *b, int64_t out[8])
 {
     if (!b || !out) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
