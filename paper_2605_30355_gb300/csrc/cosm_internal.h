@@ -115,9 +115,10 @@ struct BatchArgs {
 enum KernelMode { MODE_GENERAL_ = 0, MODE_ACCUM_ = 1, MODE_LATTICE2D_ = 2 };
 
 // Sweeps between wraps of binary32 phases (InstView::wrap_p). One sweep moves
-// a phase by at most alpha0 * wbound (wbound: the sum over colours of the
-// largest |w| in the colour, as a vertex meets at most one edge per colour,
-// plus the largest |h|), and by the twist on the DWT sweeps. 2D lattice: the
+// a phase by at most alpha0 * wbound (wbound: the smaller of the sum over
+// colours of the largest |w| in the colour, as a vertex meets at most one
+// edge per colour, plus the largest |h|, and the largest sum of |w| over a
+// vertex's own edges plus its |h|), and by the twist on the DWT sweeps. 2D lattice: the
 // largest P <= 4 for which P sweeps keep a phase wrapped to [-1/2, 1/2] inside
 // |g| < 1; edge lists: inside |g| < 2, or 0 (every update is wrapped) when
 // one sweep could leave that range; 1 for the other modes and storages.
@@ -126,6 +127,9 @@ int32_t wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, int fla
 // wbound of a colour-major weight array (off: C + 1 colour offsets) and the
 // local fields h (nullptr: none).
 int64_t colour_weight_bound(const int32_t *off, int C, const int8_t *w, const int32_t *h, int32_t n);
+// The largest sum of |w| over one vertex's edges plus its |h| (h may be nullptr).
+int64_t vertex_weight_bound(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *w,
+                            const int32_t *h);
 
 struct LaunchCfg {
     int mode;      // KernelMode

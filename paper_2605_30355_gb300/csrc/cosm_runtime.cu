@@ -400,7 +400,8 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
         h->W += g.w[(size_t)e];
     }
     for (int c = 0; c < h->C; ++c) h->off[c + 1] += h->off[c];
-    h->wbound = colour_weight_bound(h->off, h->C, wv.data(), gd->h, g.n);
+    h->wbound = std::min(colour_weight_bound(h->off, h->C, wv.data(), gd->h, g.n),
+                         vertex_weight_bound(g.n, g.m, g.src.data(), g.dst.data(), g.w.data(), gd->h));
     // device copies
     cudaGetDevice(&h->device);
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -578,6 +579,20 @@ int32_t cosm::wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, i
         best = P;
     }
     return best;
+}
+
+int64_t cosm::vertex_weight_bound(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *w,
+                                  const int32_t *h)
+{
+    std::vector<int64_t> sum((size_t)n, 0);
+    for (int64_t e = 0; e < m; ++e) {
+        const int64_t a = std::abs((int64_t)w[e]);
+        sum[(size_t)src[e]] += a;
+        sum[(size_t)dst[e]] += a;
+    }
+    int64_t b = 0;
+    for (int32_t v = 0; v < n; ++v) b = std::max(b, sum[(size_t)v] + (h ? std::abs((int64_t)h[v]) : 0));
+    return b;
 }
 
 int64_t cosm::colour_weight_bound(const int32_t *off, int C, const int8_t *w, const int32_t *h, int32_t n)

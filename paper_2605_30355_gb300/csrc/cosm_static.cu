@@ -9,6 +9,7 @@
 // process exits.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -165,7 +166,8 @@ extern "C" int cosm_solve_static(const cosm_graph_desc *gd, const cosm_params *p
     }
     std::vector<int32_t> offc((size_t)g.C + 1);
     for (int c = 0; c <= g.C; ++c) offc[(size_t)c] = (int32_t)count[(size_t)c];
-    const int64_t wbound = colour_weight_bound(offc.data(), g.C, wv.data(), nullptr, g.n);
+    const int64_t wbound = std::min(colour_weight_bound(offc.data(), g.C, wv.data(), nullptr, g.n),
+                                    vertex_weight_bound(g.n, g.m, g.src.data(), g.dst.data(), g.w.data(), nullptr));
     std::vector<int32_t> orig((size_t)g.n);
     for (int32_t v = 0; v < g.n; ++v) orig[(size_t)v] = v;
     const double a0 = p->alpha0_deg / 360.0;
