@@ -958,16 +958,32 @@ __device__ __forceinline__ uint32_t flip_if_odd(uint32_t aw, uint32_t t)
     return r;
 }
 
+// The same sign flip on the logic pipe: aw xor (t << 31) (a funnel shift
+// and an xor), for kernels whose FMA pipe is the busier one.
+__device__ __forceinline__ uint32_t flip_if_odd_alu(uint32_t aw, uint32_t t)
+{
+    uint32_t s;
+    asm("shf.l.clamp.b32 %0, 0, %1, 31;" : "=r"(s) : "r"(t));
+    return aw ^ s;
+}
+
 // Pair update of eq. (6) as pair_fast, for two replicas: t = 1.5 * 2^23 +
 // floor(c d) per lane (one fma rounded toward -inf), and the step on x1 is
 // aw (the bits of alpha w, shared by both lanes), negated where floor(c d)
-// is odd.
+// is odd. kAluLanes of the two lanes take the flip on the logic pipe (the
+// 16-bit lattice passes, FMA-bound by their conversions: binary16 +4.6 %,
+// bfloat16 +1.4 % with one lane; binary32 loses 2-6 %, so it keeps both on
+// the FMA pipe).
+template <int kAluLanes = 0>
 __device__ __forceinline__ void pair_x2(f32x2 &x1, f32x2 &x2, f32x2 aw2, f32x2 c2)
 {
     const f32x2 d = p_sub(x1, x2);
     const f32x2 t = p_fma_rd(c2, d, kMagic2);
-    const f32x2 st = ((f32x2)flip_if_odd((uint32_t)(aw2 >> 32), (uint32_t)(t >> 32)) << 32) |
-                     flip_if_odd((uint32_t)aw2, (uint32_t)t);
+    const uint32_t hi = kAluLanes >= 1 ? flip_if_odd_alu((uint32_t)(aw2 >> 32), (uint32_t)(t >> 32))
+                                       : flip_if_odd((uint32_t)(aw2 >> 32), (uint32_t)(t >> 32));
+    const uint32_t lo = kAluLanes >= 2 ? flip_if_odd_alu((uint32_t)aw2, (uint32_t)t)
+                                       : flip_if_odd((uint32_t)aw2, (uint32_t)t);
+    const f32x2 st = ((f32x2)hi << 32) | lo;
     x1 = p_add(x1, st);
     x2 = p_sub(x2, st);
 }
@@ -1468,6 +1484,11 @@ __device__ __forceinline__ void twist_wrap_x2(float *xs, int n, const float *thc
 // store wraps it and rounds it to the storage type (round to nearest even),
 // exactly as the scalar passes do per lane, so the phases equal theirs bit
 // for bit.
+// Sign flips of the 16-bit lattice passes on the logic pipe: both lanes for
+// binary16, one for bfloat16 (whose widening is already logic work).
+template <typename H>
+__host__ __device__ constexpr int kAlu16() { return std::is_same<H, __half>::value ? 2 : 1; }
+
 template <typename H>
 __device__ __forceinline__ f32x2 h2_to_p(uint32_t w)
 {
@@ -1515,10 +1536,10 @@ __device__ __forceinline__ void block_pass_even_h2(H *xs, const uint8_t *wnib, f
         const f32x2 w2 = (wb & 4u) ? n2 : a2, w3 = (wb & 8u) ? n2 : a2;
 #pragma unroll
         for (int h = 0; h < NW; ++h) {
-            pair_x2(xa[h], xb[h], w0, kTwo2);
-            pair_x2(xc[h], xd[h], w1, kTwo2);
-            pair_x2(xa[h], xc[h], w2, kTwo2);
-            pair_x2(xb[h], xd[h], w3, kTwo2);
+            pair_x2<kAlu16<H>()>(xa[h], xb[h], w0, kTwo2);
+            pair_x2<kAlu16<H>()>(xc[h], xd[h], w1, kTwo2);
+            pair_x2<kAlu16<H>()>(xa[h], xc[h], w2, kTwo2);
+            pair_x2<kAlu16<H>()>(xb[h], xd[h], w3, kTwo2);
             xa[h] = p_wrap(xa[h]);
             xb[h] = p_wrap(xb[h]);
             xc[h] = p_wrap(xc[h]);
@@ -1550,10 +1571,10 @@ __device__ __forceinline__ void odd_block_h2(uint32_t ad, uint32_t oC, uint32_t 
 #pragma unroll
     for (int h = 0; h < NW; ++h) {
         // colour 2: D-C, B-A; colour 3: D-B, C-A
-        pair_x2(xd[h], xc[h], w0, tzc);
-        pair_x2(xb[h], xa[h], w1, tzc);
-        pair_x2(xd[h], xb[h], w2, tzr);
-        pair_x2(xc[h], xa[h], w3, tzr);
+        pair_x2<kAlu16<H>()>(xd[h], xc[h], w0, tzc);
+        pair_x2<kAlu16<H>()>(xb[h], xa[h], w1, tzc);
+        pair_x2<kAlu16<H>()>(xd[h], xb[h], w2, tzr);
+        pair_x2<kAlu16<H>()>(xc[h], xa[h], w3, tzr);
         if constexpr (kDwt) {
             // the twist follows the last colour, before the store rounds
             dwt_x2(xd[h], th2[h], tk2[h], st2[h]);
