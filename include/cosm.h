@@ -308,12 +308,13 @@ int cosm_batch_get_replica_cuts(cosm_batch *b, int32_t i, int64_t *cuts, int32_t
 int cosm_batch_get_state(cosm_batch *b, int32_t i, double *phases);
 
 /* Autotuner: times a short run (probe_sweeps sweeps per instance, the given
- * replica counts) of six layouts and keeps the fastest for later runs: the
- * tile policies -- per instance the tile that keeps the most replicas
+ * replica counts) of eight layouts and keeps the fastest for later runs:
+ * the tile policies -- per instance the tile that keeps the most replicas
  * resident per SM when the GPU is full (ties to the wider tile), the
- * narrowest tile, or the single-instance rule for the instance's own
- * replica count -- each with the per-instance thread rule, and the first
- * policy with 128, 256 or 512 threads per CTA forced. Instances of one
+ * narrowest tile, the single-instance rule for the instance's own replica
+ * count, or the first rule with ties to the narrower tile -- each with the
+ * per-instance thread rule, the first policy with 128, 256 or 512 threads
+ * per CTA forced, and the last with 256. Instances of one
  * kernel, thread count and occupancy form a class: one persistent launch.
  * With the environment variable COSM_TUNE_CACHE naming a file, a choice for
  * the same batch shape is read from it, and new choices are appended. */
@@ -321,8 +322,9 @@ int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t probe_sweeps
 
 /* out[0] instances, out[1] classes, out[2] units, out[3] kernel launches
  * per run, out[4] graphs built, out[5] tile policy (0 full-GPU rule, 1
- * narrowest tile, 2 single-instance rule), out[6] forced threads (0 =
- * rule), out[7] CTAs over all classes. */
+ * narrowest tile, 2 single-instance rule, 3 full-GPU rule with ties to the
+ * narrower tile), out[6] forced threads (0 = rule), out[7] CTAs over all
+ * classes. */
 int cosm_batch_info(cosm_batch *b, int64_t out[8]);
 
 /* Layout of instance i in the last run, as cosm_layout gives it for a

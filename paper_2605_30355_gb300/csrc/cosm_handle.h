@@ -126,7 +126,9 @@ struct cosm_handle {
 namespace cosm {
 
 int env_int(const char *name, int dflt);
-int choose_layout(cosm_handle *h, int replicas);
+// narrow_ties: among tiles keeping as many replicas resident, the narrower
+// one (more CTAs per SM) instead of the wider one on a full GPU.
+int choose_layout(cosm_handle *h, int replicas, bool narrow_ties = false);
 int ensure_run_buffers(cosm_handle *h, int replicas);
 InstView inst_view(cosm_handle *h);
 int upload_alpha(cosm_handle *h, int64_t S, cudaStream_t st);

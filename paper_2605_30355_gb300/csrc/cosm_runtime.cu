@@ -456,7 +456,7 @@ int cosm::env_int(const char *name, int dflt)
 
 // Replicas per CTA (K) and threads per CTA: maximise resident replicas per
 // SM (COSM_K / COSM_THREADS override for experiments).
-int cosm::choose_layout(cosm_handle *h, int replicas)
+int cosm::choose_layout(cosm_handle *h, int replicas, bool narrow_ties)
 {
     const cosm_params &p = h->prm;
     const int mode = h->mode;
@@ -516,7 +516,7 @@ int cosm::choose_layout(cosm_handle *h, int replicas)
             // SMs; then more resident threads hide more latency
             const long resident = std::min<long>((long)occ * K, std::max<long>(1, tiles * K / h->num_sms));
             const bool full = tiles >= (long)occ * h->num_sms;
-            const long score = resident * 100000 + (full ? K : -K) * 4096 + (long)occ * T;
+            const long score = resident * 100000 + ((full && !narrow_ties) ? K : -K) * 4096 + (long)occ * T;
             if (score > bestScore) {
                 bestScore = score;
                 bestK = K;
@@ -1315,7 +1315,8 @@ struct cosm_batch {
     cudaStream_t own = nullptr;      // capture stream (the legacy stream cannot capture)
     cudaGraphExec_t exec = nullptr;
     std::vector<int64_t> sig;        // layout signature of the captured graph
-    int policy = 0;                  // 0: per-instance rule for a full GPU, 1: smallest tile, 2: per-instance rule
+    int policy = 0;                  // 0: per-instance rule for a full GPU, 1: smallest tile, 2: per-instance rule,
+                                     // 3: rule for a full GPU with ties to the narrower tile
     int threads = 0;                 // 0: per-class rule, else forced
     cudaStream_t last = nullptr;
     bool have_result = false;
@@ -1408,12 +1409,14 @@ extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, c
 // batch as a whole does: the tile keeping the most replicas resident per SM,
 // ties to the wider tile (one edge record and one barrier serve more
 // replicas). Policy 1: the narrowest tile of the storage type. Policy 2: the
-// single-instance rule with the instance's own replica count.
+// single-instance rule with the instance's own replica count. Policy 3: as
+// policy 0 with ties to the narrower tile (more CTAs per SM, whose barriers
+// and record loads overlap).
 static int batch_instance_layout(cosm_batch *b, cosm_handle *h, int32_t replicas)
 {
     int rc;
     if (b->policy == 2) return choose_layout(h, replicas);
-    if ((rc = choose_layout(h, 1 << 23))) return rc;
+    if ((rc = choose_layout(h, 1 << 23, b->policy == 3))) return rc;
     if (b->policy == 1 && h->K != (h->prm.storage == COSM_F32 ? 1 : 2)) {
         const int Kmin = h->prm.storage == COSM_F32 ? 1 : 2;
         const size_t esz = h->prm.storage == COSM_F32 ? 4 : 2;
@@ -1682,7 +1685,7 @@ extern "C" int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t p
     CK(cudaEventCreate(&e1));
     // policies with the rule's thread counts, then the default policy with
     // forced thread counts
-    const int cfgs[6][2] = {{0, 0}, {1, 0}, {2, 0}, {0, 128}, {0, 256}, {0, 512}};
+    const int cfgs[8][2] = {{0, 0}, {1, 0}, {2, 0}, {3, 0}, {0, 128}, {0, 256}, {0, 512}, {3, 256}};
     for (const auto &cf : cfgs) {
         const int pol = cf[0], thr = cf[1];
         b->policy = pol;
