@@ -12,10 +12,22 @@
 #include "../../include/cosm.h"
 #include "cosm_internal.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace cosm {
 
 // Records msg for cosm_last_error() and returns code.
 int fail(int code, const std::string &msg);
+
+// An NVTX range over the scope of one ABI call (host side: create, run,
+// readout, batch and server steps), visible to profilers that attach an
+// NVTX tool and free otherwise.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace cosm
 

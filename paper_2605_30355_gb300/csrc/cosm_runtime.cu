@@ -299,6 +299,7 @@ static void balance_banks(int64_t *e, int64_t cnt, const std::vector<int32_t> &s
 
 extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm_handle **out)
 {
+    NvtxRange range("cosm_create");
     if (!gd || !out) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     int rc = check_params(p);
@@ -826,6 +827,7 @@ int cosm::launch_finalize(cosm_handle *h, cudaStream_t st)
 static int run_range(cosm_handle *h, int64_t sweeps, int64_t s0, int64_t s1, int32_t replicas, uint64_t seed,
                      int64_t target_cut, cudaStream_t st)
 {
+    NvtxRange range("cosm_run");
     if (!h) return fail(COSM_ERR_INVALID_ARG, "NULL handle");
     if (sweeps < 1 || sweeps >= ((int64_t)1 << 31)) return fail(COSM_ERR_INVALID_ARG, "sweeps must be in [1, 2^31)");
     if (replicas < 1 || replicas >= (1 << 24)) return fail(COSM_ERR_INVALID_ARG, "replicas must be in [1, 2^24)");
@@ -1210,6 +1212,7 @@ static int launch_on_state(cosm_handle *h, int32_t flags, int64_t s0, int64_t s1
 
 extern "C" int cosm_step(cosm_handle *h, int64_t sweep, float alpha, void *stream)
 {
+    NvtxRange range("cosm_step");
     if (!h) return fail(COSM_ERR_INVALID_ARG, "NULL handle");
     if (!h->have_state) return fail(COSM_ERR_STATE, "no state yet");
     if (sweep < 1 || sweep >= ((int64_t)1 << 31)) return fail(COSM_ERR_INVALID_ARG, "bad sweep index");
@@ -1239,6 +1242,7 @@ extern "C" int cosm_step(cosm_handle *h, int64_t sweep, float alpha, void *strea
 
 extern "C" int cosm_readout(cosm_handle *h, void *stream)
 {
+    NvtxRange range("cosm_readout");
     if (!h) return fail(COSM_ERR_INVALID_ARG, "NULL handle");
     if (!h->have_state) return fail(COSM_ERR_STATE, "no state yet");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -1346,6 +1350,7 @@ extern "C" void cosm_batch_destroy(cosm_batch *b)
 extern "C" int cosm_batch_create(int32_t count, const cosm_graph_desc *graphs, const cosm_params *params,
                                  int32_t shared_params, cosm_batch **out)
 {
+    NvtxRange range("cosm_batch_create");
     if (!graphs || !params || !out || count < 1 || count > (1 << 20))
         return fail(COSM_ERR_INVALID_ARG, "bad batch arguments");
     *out = nullptr;
@@ -1559,6 +1564,7 @@ static int batch_enqueue(cosm_batch *b, cudaStream_t st)
 extern "C" int cosm_batch_run(cosm_batch *b, const int64_t *sweeps, const int32_t *replicas,
                               const uint64_t *seeds, void *stream)
 {
+    NvtxRange range("cosm_batch_run");
     if (!b || !sweeps || !replicas || !seeds) return fail(COSM_ERR_INVALID_ARG, "NULL argument");
     cudaStream_t user = reinterpret_cast<cudaStream_t>(stream);
     cudaStream_t st = b->own;
@@ -1649,6 +1655,7 @@ extern "C" int cosm_batch_get_state(cosm_batch *b, int32_t i, double *phases)
 // from / appended to that text file, keyed by the batch's shape.
 extern "C" int cosm_batch_tune(cosm_batch *b, const int32_t *replicas, int64_t probe_sweeps, void *stream)
 {
+    NvtxRange range("cosm_batch_tune");
     if (!b || !replicas || probe_sweeps < 1) return fail(COSM_ERR_INVALID_ARG, "bad tuning arguments");
     const size_t n = b->hs.size();
     uint64_t key = 1469598103934665603ull;  // FNV-1a over the batch's shape

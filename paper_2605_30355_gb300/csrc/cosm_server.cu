@@ -244,7 +244,11 @@ static void worker_main(cosm_server *s)
             s->max_concurrent = std::max<int64_t>(s->max_concurrent, (int64_t)act.size());
         }
         if (act.empty()) continue;
-        int rc = run_chunk(s, act);
+        int rc;
+        {
+            NvtxRange range("cosm_server_chunk");
+            rc = run_chunk(s, act);
+        }
         std::vector<Request *> keep;
         for (Request *r : act) {
             if (rc) {
