@@ -8,10 +8,15 @@ one full trial of every replica (init, all sweeps, DWT, schedule, readout
 with exact cuts and best-state tracking).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--storage f32|f16] [--workload torus20k|torus10k|...]
+                  [--storage f32|f16|q16|bf16] [--workload torus20k|torus10k|...]
 
-Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU
-oracle on the host cores on a bounded sample of the same workload.
+Prints one JSON line (rank 0). Beside the headline it carries, on the
+default workload: the end-to-end rate through the host-buffer call, the
+rooflines (the method's shared-memory byte count and 6 FP32 operations per
+update against measured peaks, and ncu-measured traffic), time-to-target
+with Wilson intervals at 10^5 and 10^6 sweeps per trial, the 2-byte storage
+forms, and the ragged batch in three forms. ``--impl reference`` times the
+FP64 CPU oracle on the host cores on a bounded sample of the same workload.
 """
 from __future__ import annotations
 
