@@ -232,7 +232,9 @@ int cosm_set_state(cosm_handle *h, const double *phases, int32_t replicas, uint6
  * count, seed (for the remaining DWT angles) and sweep index; a
  * cosm_run_range from sweep_idx + 1 then continues the trial. On a handle
  * created from the same graph and parameters the continuation equals the
- * uninterrupted trial bit for bit. Export synchronises. */
+ * uninterrupted trial bit for bit. The checkpoint holds the phases only:
+ * with track_period > 0 the readouts kept before it are not carried over
+ * to another handle. Export synchronises. */
 int cosm_export_state(cosm_handle *h, void *phases, int32_t storage, int64_t *sweep_idx);
 int cosm_import_state(cosm_handle *h, const void *phases, int32_t storage, int32_t replicas, uint64_t seed,
                       int64_t sweep_idx);
