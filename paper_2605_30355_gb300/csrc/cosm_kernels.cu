@@ -2100,10 +2100,12 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 // single- and 8-replica tiles keep registers for occupancy
                 if constexpr (sizeof(Store) == 4 && (K == 1 || K == 2 || K == 4)) {
                     // binary32: f32x2 lanes (replica pairs, or edge pairs for
-                    // single-replica tiles); batches of 4 edges, 2 for tiles
-                    // of four replicas (their registers)
+                    // single-replica tiles); batches of 3 edges for tiles of
+                    // two replicas (4 and 5 were 1-5 % slower: the last,
+                    // checked batch of a colour wastes fewer slots), 2 for
+                    // tiles of four (their registers), 4 for one (pairs)
                     float *xf = reinterpret_cast<float *>(t.xs);
-                    constexpr int kB = K == 4 ? 2 : 4;
+                    constexpr int kB = K == 4 ? 2 : (K == 2 ? 3 : 4);
                     if (v.stage_ij) {
                         const uint32_t stage = (uint32_t)__cvta_generic_to_shared(smem) +
                                                (uint32_t)smem_bytes<Store, K>(v.n, v.P, false);
