@@ -537,9 +537,12 @@ def solve_static(n, src, dst, w, sweeps, replicas, seed, cuts_out, best_p_out, c
     (int64) and best_p_out (int32) are caller-owned device buffers of
     `replicas` entries, e.g. torch tensors on the current device."""
     import torch
+    for name, t in (("cuts_out", cuts_out), ("best_p_out", best_p_out)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise ValueError(f"{name} must be a CUDA tensor on the current device")
     dev = torch.cuda.current_device()
     for name, t, dt in (("cuts_out", cuts_out, torch.int64), ("best_p_out", best_p_out, torch.int32)):
-        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != dev:
+        if t.device.index != dev:
             raise ValueError(f"{name} must be a CUDA tensor on the current device")
         if t.dtype != dt or not t.is_contiguous() or t.numel() < int(replicas):
             raise ValueError(f"{name} must be a contiguous {dt} tensor of at least {int(replicas)} entries")

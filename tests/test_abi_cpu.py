@@ -152,3 +152,40 @@ def test_field_and_tracking_parameters_validated(cosm):
     with pytest.raises(cosm.CosmError):
         cosm.Solver(inst.n, inst.src, inst.dst, inst.w, h=np.ones(inst.n, np.int32),
                     flags=cosm.OPT_BISECTOR)
+
+
+def test_run_control_entries_reject_bad_arguments_on_the_host(cosm):
+    # the entries added for run control and failure detection check their
+    # arguments before any device work (no GPU needed here)
+    import ctypes as C
+    L = cosm.lib()
+    NULL = None
+    assert L.cosm_set_wait_limit(NULL, 1.0) == cosm.ERR_INVALID_ARG
+    assert L.cosm_inject_fault(NULL, cosm.FAULT_DROP_SIGNAL) == cosm.ERR_INVALID_ARG
+    c = C.c_int64()
+    assert L.cosm_get_success(NULL, C.byref(c)) == cosm.ERR_INVALID_ARG
+    assert L.cosm_run_range(NULL, 100, 1, 10, 4, 1, cosm.NO_TARGET, NULL) == cosm.ERR_INVALID_ARG
+    assert L.cosm_run(NULL, 100, 4, 1, cosm.NO_TARGET, NULL) == cosm.ERR_INVALID_ARG
+    buf = np.zeros(16, np.float32)
+    assert L.cosm_export_state(NULL, cosm._p(buf), cosm.F32, NULL) == cosm.ERR_INVALID_ARG
+    assert L.cosm_import_state(NULL, cosm._p(buf), cosm.F32, 1, 1, 0) == cosm.ERR_INVALID_ARG
+    out = (C.c_int32 * 8)()
+    assert L.cosm_batch_layout(NULL, 0, out) == cosm.ERR_INVALID_ARG
+    a, b = C.c_double(), C.c_double()
+    assert L.cosm_probe_fp32(0, C.byref(a), C.byref(b)) == cosm.ERR_INVALID_ARG
+
+
+def test_static_entry_checks_output_buffers_before_device_work(cosm):
+    # host arrays are not device memory: refused with INVALID_ARG, never
+    # handed to a kernel (on a machine without a GPU the pointer query fails
+    # the same way)
+    import ctypes as C
+    inst = instances.torus2d(8, 8, 1)
+    desc, keep = cosm._desc(inst.n, inst.src, inst.dst, inst.w)
+    p = cosm.default_params()
+    cuts = np.zeros(4, np.int64)
+    bps = np.zeros(4, np.int32)
+    rc = cosm.lib().cosm_solve_static(C.byref(desc), C.byref(p), 10, 4, 1, cosm._p(cuts), cosm._p(bps), None)
+    assert rc in (cosm.ERR_INVALID_ARG, cosm.ERR_CUDA)
+    with pytest.raises(ValueError):
+        cosm.solve_static(inst.n, inst.src, inst.dst, inst.w, 10, 4, 1, cuts, bps)
