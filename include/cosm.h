@@ -47,6 +47,8 @@ extern "C" {
 #define COSM_ERR_TIMEOUT -6       /* a bounded device wait gave up           */
 #define COSM_ERR_STATE -7         /* call out of order (e.g. no run yet)     */
 #define COSM_ERR_NOMEM -8         /* host or device allocation failed        */
+#define COSM_ERR_CHECK -9         /* a device-side index check failed (only the
+                                   * checked build, libcosm_checked.so, has them) */
 
 /* ---- phase storage ----------------------------------------------------- */
 #define COSM_F32 0 /* binary32 phases, FP32 arithmetic                      */

@@ -19,7 +19,9 @@ import numpy as np
 from . import build as _build
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libcosm.so")
+# COSM_LIBRARY=checked loads the checked build (device index checks on)
+LIB_PATH = os.path.join(_HERE, "libcosm_checked.so" if os.environ.get("COSM_LIBRARY") == "checked"
+                        else "libcosm.so")
 
 OK = 0
 ERR_INVALID_ARG = -1
@@ -30,6 +32,7 @@ ERR_CUDA = -5
 ERR_TIMEOUT = -6
 ERR_STATE = -7
 ERR_NOMEM = -8
+ERR_CHECK = -9
 
 F32 = 0
 F16 = 1

@@ -78,6 +78,7 @@ struct InstView {
     // read from global memory)
     int32_t stage_ij;
     int32_t stage_w;
+    int32_t *check;       // error word for the checked build's device checks (nullptr: none)
 };
 
 // Bytes of the record and weight parts of one staging buffer for colours of

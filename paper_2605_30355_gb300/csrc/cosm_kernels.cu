@@ -75,6 +75,27 @@ __device__ __forceinline__ uint32_t phase_q(float g)
     return (uint32_t)(unsigned long long)__float2ll_rd(g * 4294967296.0f);
 }
 
+// ---------------------------------------------------------------- checked build
+// With COSM_CHECKS defined (the checked library, a stand-in for a memory
+// checker), device code validates the indices it is given: an edge record's
+// two slots must lie below n and a lattice layout must tile its slots; a
+// failed check sets bit 2 of the handle's error word (cosm_sync then reports
+// COSM_ERR_CHECK) and the access goes to slot 0 instead. The normal build
+// compiles the checks away.
+__device__ __forceinline__ uint32_t checked_rec(const InstView &a, uint32_t rec)
+{
+#ifdef COSM_CHECKS
+    if ((rec & 0xFFFFu) >= (uint32_t)a.n || (rec >> 16) >= (uint32_t)a.n) {
+        if (a.check) atomicOr(a.check, 2);
+        return 0u;
+    }
+#else
+    (void)a;
+#endif
+    return rec;
+}
+__device__ __forceinline__ uint32_t load_rec(const InstView &a, int e) { return checked_rec(a, __ldg(a.ij + e)); }
+
 // ---------------------------------------------------------------- storage
 template <int K>
 __device__ __forceinline__ void ldk(const float *p, float (&x)[K])
@@ -345,7 +366,7 @@ __device__ bool seg_begin(const InstView &v, const Segment &sg, const Tile<Store
             while (atomicAdd(&ready[sg.tile], 0) < need) {
                 asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
                 if (t1 - t0 > wait_limit_ns) {
-                    atomicExch(err, 1);
+                    atomicOr(err, 1);
                     *s_skip = 1;
                     break;
                 }
@@ -356,6 +377,16 @@ __device__ bool seg_begin(const InstView &v, const Segment &sg, const Tile<Store
     }
     __syncthreads();
     if (*s_skip) return false;
+#ifdef COSM_CHECKS
+    // the lattice passes address slots from Q and Wd alone: they must tile n
+    // (four sublattices of Q slots, Q a whole number of rows); the tile must
+    // be one of the run's
+    if (tid == 0) {
+        const bool bad_tile = sg.tile < 0 || (int64_t)sg.tile * K >= (int64_t)v.replicas + K - 1;
+        const bool bad_lat = v.mode == MODE_LATTICE2D_ && (v.Q * 4 != v.n || v.Wd < 1 || v.Q % v.Wd != 0);
+        if ((bad_tile || bad_lat) && v.check) atomicOr(v.check, 2);
+    }
+#endif
     const Store *gst = reinterpret_cast<const Store *>(v.state) + (size_t)sg.tile * v.state_tile_stride;
     if (sg.flags & SEG_INIT) {
         // Alg. 1 "Set x_i random": Philox keyed by seed, counter (v/4, r, 0, 0)
@@ -409,7 +440,7 @@ __device__ __noinline__ void tile_readout(const InstView &a, int tile, const Til
 #pragma unroll
         for (int r = 0; r < K; ++r) cs[r] = fs[r] = 0;
         for (int e = tid; e < m; e += nt) {
-            const uint32_t rec = __ldg(a.ij + e);
+            const uint32_t rec = load_rec(a, e);
             const int wv = (int)__ldg(a.w + e);
             uint32_t qis[K], qjs[K];
             ld_q32<Store, K>(t.xs + (size_t)(rec & 0xFFFFu) * K, qis);
@@ -443,7 +474,7 @@ __device__ __noinline__ void tile_readout(const InstView &a, int tile, const Til
 #pragma unroll
         for (int r = 0; r < K; ++r) base[r] = 0;
         for (int e = tid; e < m; e += nt) {
-            const uint32_t rec = __ldg(a.ij + e);
+            const uint32_t rec = load_rec(a, e);
             const int wv = (int)__ldg(a.w + e);
             const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
             uint32_t qis[K], qjs[K];
@@ -589,7 +620,7 @@ __device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int e = e0 + u * nt;
-            rec[u] = e < e1 ? __ldg(a.ij + e) : 0u;
+            rec[u] = e < e1 ? load_rec(a, e) : 0u;
             aw[u] = e < e1 ? alpha * weight_f(__ldg(a.w + e)) : 0.0f;
         }
         float xi[kBatch][K], xj[kBatch][K];
@@ -632,7 +663,7 @@ __device__ __forceinline__ void fetch_edges(const InstView &a, int e0, int e1, u
 #pragma unroll
     for (int u = 0; u < B; ++u) {
         const int e = e0 + u * nt;
-        rec[u] = e < e1 ? __ldg(a.ij + e) : 0u;
+        rec[u] = e < e1 ? load_rec(a, e) : 0u;
         w[u] = e < e1 ? (int32_t)__ldg(a.w + e) : 0;
     }
 }
@@ -1292,8 +1323,9 @@ __device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, fl
             if constexpr (kStaged) {
                 asm volatile("ld.shared.b32 %0, [%1];" : "=r"(rec) : "r"(sij + 4u * (uint32_t)e) : "memory");
                 asm volatile("ld.shared.s8 %0, [%1];" : "=r"(w) : "r"(sw + (uint32_t)e) : "memory");
+                rec = checked_rec(a, rec);
             } else {
-                rec = __ldg(a.ij + e);
+                rec = load_rec(a, e);
                 w = __ldg(a.w + e);
             }
         }
@@ -1678,7 +1710,7 @@ __device__ __forceinline__ void general_colour_q(const InstView &a, uint16_t *xs
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int e = e0 + u * nt;
-            rec[u] = e < e1 ? __ldg(a.ij + e) : 0u;
+            rec[u] = e < e1 ? load_rec(a, e) : 0u;
             ap[u] = e < e1 ? (uint32_t)((int32_t)aq * (int32_t)__ldg(a.w + e)) << 16 : 0u;
         }
         uint32_t xi[kBatch][K], xj[kBatch][K];
@@ -1934,7 +1966,7 @@ __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment
                 for (int c = 0; c < v.C; ++c) {
                     const int e1 = __ldg(v.off + c + 1);
                     for (int e = __ldg(v.off + c) + tid; e < e1; e += nt) {
-                        const uint32_t rec = __ldg(v.ij + e);
+                        const uint32_t rec = load_rec(v, e);
                         const uint32_t ap = (uint32_t)((int32_t)aq * (int32_t)__ldg(v.w + e)) << 16;
                         const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
                         uint32_t xi[K], xj[K];
@@ -2138,7 +2170,7 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                 for (int c = 0; c < v.C; ++c) {
                     const int e1 = __ldg(v.off + c + 1);
                     for (int e = __ldg(v.off + c) + tid; e < e1; e += nt) {
-                        const uint32_t rec = __ldg(v.ij + e);
+                        const uint32_t rec = load_rec(v, e);
                         const float aw = at.x * (float)__ldg(v.w + e);
                         const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
                         float xi[K], xj[K];
@@ -2381,7 +2413,7 @@ __global__ void __launch_bounds__(1024) opt_readout_kernel(const OptArgs o)
         __syncthreads();
         long long c0 = 0;
         for (int e = tid; e < m; e += nt) {
-            const uint32_t rec = __ldg(v.ij + e);
+            const uint32_t rec = load_rec(v, e);
             const int wv = (int)__ldg(v.w + e);
             const int i = (int)(rec & 0xFFFFu), j = (int)(rec >> 16);
             const uint32_t qi = qb[i], qj = qb[j];

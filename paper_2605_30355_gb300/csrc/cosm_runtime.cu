@@ -646,6 +646,7 @@ InstView cosm::inst_view(cosm_handle *h)
     v.paired = std::getenv("COSM_SCALAR_F32") ? 0 : (h->block_pairs ? 2 : 1);
     v.wrap_p = wrap_period(h->prm.alpha0_deg, h->prm.dwt_ratio, h->prm.dwt_period, h->prm.flags, h->mode,
                            h->prm.storage, h->wbound);
+    v.check = h->d_err.p;
     if (h->staged) {
         int max_ec = 0;
         for (int c = 0; c < h->C; ++c) max_ec = std::max(max_ec, h->off[c + 1] - h->off[c]);
@@ -955,6 +956,7 @@ extern "C" int cosm_sync(cosm_handle *h)
     CK(cudaStreamSynchronize(h->stream));
     int err = 0;
     CK(cudaMemcpy(&err, h->d_err.p, 4, cudaMemcpyDeviceToHost));
+    if (err & 2) return fail(COSM_ERR_CHECK, "a device-side index check of the checked build failed");
     if (err) return fail(COSM_ERR_TIMEOUT, "a bounded wait between work segments gave up");
     return COSM_OK;
 }
