@@ -83,6 +83,7 @@ struct cosm_handle {
     int32_t C = 0;
     DevBuf<uint32_t> d_ij;
     DevBuf<int8_t> d_w;
+    DevBuf<uint32_t> d_ijs;         // +-1 weights on <= 2^15 slots: records with the sign in bit 31
     DevBuf<int32_t> d_orig;
     DevBuf<int32_t> d_off;          // colour offsets
     int mode = cosm::MODE_GENERAL_;       // kernel variant

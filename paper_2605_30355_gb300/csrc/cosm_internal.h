@@ -38,6 +38,10 @@ struct InstView {
     const int32_t *off;   // device: colour offsets into ij / w (C + 1)
     const uint32_t *ij;   // edge records: slot(src) | slot(dst) << 16, colour-major
     const int8_t *w;      // Max-Cut weights, colour-major
+    // the same records for +-1 weights on at most 2^15 slots with the weight
+    // in bit 0 ([w = -1] | slot(src) << 1 | slot(dst) << 16), so the
+    // binary32 edge-list sweep loads one word per edge; nullptr otherwise
+    const uint32_t *ijs;
     const int32_t *orig_of;  // slot -> original vertex id (Philox init key)
     // 2D lattice mode: Q = n/4 slots per sublattice, Wd = L2/2 columns;
     // wnib[pass * Q + f] holds the weight bits of the four edges of 2x2
@@ -121,8 +125,10 @@ enum KernelMode { MODE_GENERAL_ = 0, MODE_ACCUM_ = 1, MODE_LATTICE2D_ = 2 };
 // edge per colour, plus the largest |h|, and the largest sum of |w| over a
 // vertex's own edges plus its |h|), and by the twist on the DWT sweeps. 2D lattice: the
 // largest P <= 4 for which P sweeps keep a phase wrapped to [-1/2, 1/2] inside
-// |g| < 1; edge lists: inside |g| < 2, or 0 (every update is wrapped) when
-// one sweep could leave that range; 1 for the other modes and storages.
+// |g| < 1; edge lists: the largest P <= 12 (preferring a multiple of the
+// twist period, whose pass takes the wrap along) that keeps it inside
+// |g| < 2, or 0 (every update is wrapped) when one sweep could leave that
+// range; 1 for the other modes and storages.
 int32_t wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, int flags, int mode, int storage,
                     int64_t wbound);
 // wbound of a colour-major weight array (off: C + 1 colour offsets) and the

@@ -95,6 +95,18 @@ __device__ __forceinline__ uint32_t checked_rec(const InstView &a, uint32_t rec)
     return rec;
 }
 __device__ __forceinline__ uint32_t load_rec(const InstView &a, int e) { return checked_rec(a, __ldg(a.ij + e)); }
+// A record of a.ijs ([w = -1] | slot(src) << 1 | slot(dst) << 16).
+__device__ __forceinline__ uint32_t load_rec_sgn(const InstView &a, int e)
+{
+    const uint32_t rec = __ldg(a.ijs + e);
+#ifdef COSM_CHECKS
+    if (((rec & 0xFFFFu) >> 1) >= (uint32_t)a.n || (rec >> 16) >= (uint32_t)a.n) {
+        if (a.check) atomicOr(a.check, 2);
+        return 0u;
+    }
+#endif
+    return rec;
+}
 
 // ---------------------------------------------------------------- storage
 template <int K>
@@ -1307,10 +1319,14 @@ __device__ __forceinline__ f32x2 p_pack(float lo, float hi)
 // may run past the end e1 of its colour (loads of slot 0, stores skipped).
 // kStaged: the colour's records sit in shared memory (edge e's record at
 // sij + 4 e, its weight at sw + e), else they are read from global memory.
-template <int K, int B, bool kWrapEach, bool kTail, bool kStaged = false>
+// kSgn: the records of a.ijs, whose bit 0 is the sign of a +-1 weight, so
+// alpha w is alpha + bit 0 * 2^31 in integer arithmetic (the sign bit
+// flipped; no weight load or conversion).
+template <int K, int B, bool kWrapEach, bool kTail, bool kStaged = false, bool kSgn = false>
 __device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, float alpha, int e0, int e1, int nt,
                                               uint32_t sij = 0, uint32_t sw = 0)
 {
+    static_assert(!(kStaged && kSgn), "staged records carry their weights apart");
     constexpr uint32_t E = K * 4;  // bytes per slot
     uint32_t ai[B], aj[B];
     float aw[B];
@@ -1324,14 +1340,21 @@ __device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, fl
                 asm volatile("ld.shared.b32 %0, [%1];" : "=r"(rec) : "r"(sij + 4u * (uint32_t)e) : "memory");
                 asm volatile("ld.shared.s8 %0, [%1];" : "=r"(w) : "r"(sw + (uint32_t)e) : "memory");
                 rec = checked_rec(a, rec);
+            } else if constexpr (kSgn) {
+                rec = load_rec_sgn(a, e);
             } else {
                 rec = load_rec(a, e);
                 w = __ldg(a.w + e);
             }
         }
-        ai[u] = xb + (rec & 0xFFFFu) * E;
         aj[u] = xb + (rec >> 16) * E;
-        aw[u] = alpha * weight_f((int8_t)w);
+        if constexpr (kSgn) {
+            ai[u] = xb + (rec & 0xFFFEu) * (E / 2);
+            aw[u] = __uint_as_float(flip_if_odd(__float_as_uint(alpha), rec));
+        } else {
+            ai[u] = xb + (rec & 0xFFFFu) * E;
+            aw[u] = alpha * weight_f((int8_t)w);
+        }
     }
     if constexpr (K == 1) {
         float xi[B], xj[B];
@@ -1390,8 +1413,10 @@ __device__ __forceinline__ void edge_batch_x2(const InstView &a, uint32_t xb, fl
 }
 
 // The colours of one sweep: whole batches without bounds checks, then at
-// most one checked batch per thread at the end of each colour.
-template <int K, int B, bool kWrapEach>
+// most one checked batch per thread at the end of each colour. (Trimming
+// that last batch to the ceil(rem / nt) slots the block's remaining rem
+// edges need cost 3-6 % on G(n, m) graphs: more code for little saving.)
+template <int K, int B, bool kWrapEach, bool kSgn = false>
 __device__ __forceinline__ void general_colours_x2(const InstView &a, float *xs, float alpha)
 {
     static_assert(K == 1 || K == 2 || K == 4, "K");
@@ -1401,8 +1426,9 @@ __device__ __forceinline__ void general_colours_x2(const InstView &a, float *xs,
     for (int c = 0; c < a.C; ++c) {
         const int e1 = __ldg(a.off + c + 1);
         int e0 = __ldg(a.off + c) + threadIdx.x;
-        for (; e0 + (B - 1) * nt < e1; e0 += B * nt) edge_batch_x2<K, B, kWrapEach, false>(a, xb, alpha, e0, e1, nt);
-        if (e0 < e1) edge_batch_x2<K, B, kWrapEach, true>(a, xb, alpha, e0, e1, nt);
+        for (; e0 + (B - 1) * nt < e1; e0 += B * nt)
+            edge_batch_x2<K, B, kWrapEach, false, false, kSgn>(a, xb, alpha, e0, e1, nt);
+        if (e0 < e1) edge_batch_x2<K, B, kWrapEach, true, false, kSgn>(a, xb, alpha, e0, e1, nt);
         __syncthreads();
     }
 }
@@ -2148,6 +2174,8 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                             general_colours_x2s<K, kB, false>(v, xf, at.x, stage, first, last, stage_cur);
                     } else if (v.wrap_p == 0) {
                         general_colours_x2<K, kB, true>(v, xf, at.x);
+                    } else if (v.ijs) {
+                        general_colours_x2<K, kB, false, true>(v, xf, at.x);
                     } else {
                         general_colours_x2<K, kB, false>(v, xf, at.x);
                     }

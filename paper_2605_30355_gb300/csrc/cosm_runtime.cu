@@ -134,7 +134,7 @@ extern "C" void cosm_destroy(cosm_handle *h)
 {
     if (!h) return;
     if (h->stream || h->have_state) cudaStreamSynchronize(h->stream);
-    h->d_ij.release(); h->d_w.release(); h->d_orig.release(); h->d_off.release(); h->d_state.release();
+    h->d_ij.release(); h->d_w.release(); h->d_ijs.release(); h->d_orig.release(); h->d_off.release(); h->d_state.release();
     h->d_cut.release(); h->d_bestp.release(); h->d_alpha.release(); h->d_segs.release();
     h->d_segoff.release(); h->d_ready.release(); h->d_err.release(); h->d_best.release();
     h->d_spins.release();
@@ -427,6 +427,22 @@ extern "C" int cosm_create(const cosm_graph_desc *gd, const cosm_params *p, cosm
         cosm_destroy(h);
         return fail(COSM_ERR_CUDA, "copying the graph to the device failed");
     }
+    // +-1 weights on at most 2^15 slots: the weight folded into the record
+    bool unit = g.n <= (1 << 15);
+    for (int64_t k = 0; unit && k < g.m; ++k) unit = wv[(size_t)k] == 1 || wv[(size_t)k] == -1;
+    if (unit) {
+        std::vector<uint32_t> ijs(m_pad, 0u);
+        for (int64_t k = 0; k < g.m; ++k)
+            ijs[(size_t)k] = ((ij[(size_t)k] & 0xFFFFu) << 1) | (ij[(size_t)k] & 0xFFFF0000u) | (wv[(size_t)k] < 0 ? 1u : 0u);
+        if ((rc = h->d_ijs.ensure(m_pad))) {
+            cosm_destroy(h);
+            return rc;
+        }
+        if (cudaMemcpy(h->d_ijs.p, ijs.data(), ijs.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cosm_destroy(h);
+            return fail(COSM_ERR_CUDA, "copying the graph to the device failed");
+        }
+    }
     if (h->fields) {
         std::vector<int32_t> hs((size_t)g.n);
         for (int32_t v = 0; v < g.n; ++v) hs[(size_t)h->slot_of[(size_t)v]] = gd->h[v];
@@ -572,14 +588,18 @@ int32_t cosm::wrap_period(double alpha0_deg, double dwt_ratio, int dwt_period, i
     if (storage != COSM_F32 || (mode != MODE_LATTICE2D_ && mode != MODE_GENERAL_)) return 1;
     const double a0 = std::fabs(alpha0_deg) / 360.0;
     const bool dwt = !(flags & COSM_NO_DWT) && dwt_period > 0;
-    const double limit = mode == MODE_LATTICE2D_ ? 0.999 : 1.999;
-    int32_t best = mode == MODE_LATTICE2D_ ? 1 : 0;
-    for (int P = 1; P <= 4; ++P) {
+    const bool lattice = mode == MODE_LATTICE2D_;
+    const double limit = lattice ? 0.999 : 1.999;
+    int32_t best = lattice ? 1 : 0, best_dwt = 0;
+    for (int P = 1; P <= (lattice ? 4 : 12); ++P) {
         const double twists = dwt ? std::ceil((double)P / dwt_period) : 0.0;
         if (0.5 + (double)wbound * P * a0 + twists * std::fabs(dwt_ratio) * a0 >= limit) break;
         best = P;
+        if (dwt && P % dwt_period == 0) best_dwt = P;
     }
-    return best;
+    // edge lists wrap in the twist's pass: a multiple of the twist period
+    // needs no pass of its own
+    return (!lattice && best_dwt) ? best_dwt : best;
 }
 
 int64_t cosm::vertex_weight_bound(int32_t n, int64_t m, const int32_t *src, const int32_t *dst, const int32_t *w,
@@ -619,6 +639,7 @@ InstView cosm::inst_view(cosm_handle *h)
     v.off = h->d_off.p;
     v.ij = h->d_ij.p;
     v.w = h->d_w.p;
+    v.ijs = std::getenv("COSM_SPLIT_W") ? nullptr : h->d_ijs.p;
     v.orig_of = h->d_orig.p;
     v.wnib = h->d_wnib.p;
     v.Q = h->Q;

@@ -1,7 +1,8 @@
 """The checked build (libcosm_checked.so: the kernels compiled with device
 index checks, a stand-in for a memory checker, which is not available on
 this GPU pool) runs every kernel family -- lattice passes in four storages,
-edge lists at three tile widths, the simultaneous-update ablation, local
+edge lists at three tile widths (split records and weights, and records
+carrying a +-1 weight's sign), the simultaneous-update ablation, local
 fields with tracking and the optimal bisector, the ragged batch, the
 wrap-around schedule -- with no check failing (cosm_sync would report
 COSM_ERR_CHECK), and gives the normal build's results bit for bit."""
@@ -60,6 +61,7 @@ def _cases(cosm):
 
     torus = instances.torus2d(16, 20, 1)
     gnm = instances.sparse_gnm(700, 2000, 2)
+    reg3 = instances.random_regular(600, 3, 3)  # +-1 weights: records carrying the sign
     planted = instances.frustrated_loop_planted((12, 12), 0.6, 4)
     fields = instances.aligned_fields(planted, 1, 0.2)
     return [
@@ -70,6 +72,8 @@ def _cases(cosm):
         ("edges_f32_k1", single(gnm, 150, 7, 15, env={"COSM_K": "1"}, dwt_ratio=1.0)),
         ("edges_f32_k2", single(gnm, 150, 8, 16, env={"COSM_K": "2"}, dwt_ratio=1.0)),
         ("edges_f32_k4", single(gnm, 150, 8, 17, env={"COSM_K": "4"}, dwt_ratio=1.0)),
+        ("edges_signed_k2", single(reg3, 150, 8, 25, env={"COSM_K": "2"}, dwt_ratio=1.0)),
+        ("edges_signed_k1", single(reg3, 150, 7, 26, env={"COSM_K": "1"}, dwt_ratio=1.0)),
         ("edges_f16", single(gnm, 150, 8, 18, storage=cosm.F16, dwt_ratio=1.0)),
         ("edges_q16", single(gnm, 150, 8, 19, storage=cosm.Q16, dwt_ratio=1.0)),
         ("no_scs_f32", single(gnm, 100, 6, 20, flags=cosm.NO_SCS, dwt_ratio=1.0)),

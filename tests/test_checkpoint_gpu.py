@@ -146,3 +146,27 @@ def test_bounded_wait_times_out_on_dropped_signal(cosm, orc):
     ref.run(401, 37, seed=4)
     assert np.array_equal(ref.replica_cuts()[0], cuts)
     assert np.array_equal(ref.get_state(), x)
+
+
+@pytest.mark.parametrize("storage", [0, 2])
+def test_tracked_trial_split_into_ranges_on_one_handle(cosm, orc, storage):
+    # mid-anneal tracking (Fig. 10) across ranges of one handle: the readouts
+    # every T sweeps, the kept readout and its spins equal the uninterrupted
+    # tracked trial's (the tracking state stays on the handle)
+    inst = instances.torus2d(12, 16, 4)
+    S, R, seed, T = 180, 5, 33, 25
+
+    def solver():
+        return cosm.Solver.from_instance(inst, storage=storage, track_period=T, dwt_ratio=1.0)
+
+    ref = solver()
+    ref.run(S, R, seed)
+    a = solver()
+    a.run_range(S, 1, 60, R, seed)
+    a.run_range(S, 61, 133, R, seed)
+    a.run_range(S, 134, S, R, seed)
+    assert np.array_equal(a.trace(), ref.trace())
+    assert np.array_equal(a.replica_cuts()[0], ref.replica_cuts()[0])
+    assert np.array_equal(a.replica_energies(), ref.replica_energies())
+    ra, rr = a.best(), ref.best()
+    assert ra[:3] == rr[:3] and np.array_equal(ra[3], rr[3])

@@ -357,6 +357,50 @@ def test_staged_records_equal_global_loads(cosm, orc, K, make, ratio):
         assert np.array_equal(x, out[0][0]) and np.array_equal(c, out[0][1])
 
 
+@pytest.mark.parametrize("K", [1, 2, 4])
+@pytest.mark.parametrize("threads", [64, 96])
+@pytest.mark.parametrize("wmax", [1, 3])
+def test_edge_list_tails_and_signed_records(cosm, orc, K, threads, wmax):
+    # binary32 edge lists: whole batches of B edges per thread, then one
+    # checked batch; a greedy colouring of G(n, m) has colours of every size,
+    # so at small thread counts the rem edges left after the whole batches
+    # of a colour take every count of valid slots in the checked batch: one
+    # sweep against the oracle. With +-1 weights on at most 2^15 slots the
+    # sweep reads records carrying the weight's sign (the default); they
+    # equal split records and weights bit for bit over whole trials.
+    inst = instances.sparse_gnm(700, 2100, 5, wmax=wmax)
+    col, C = orc.color_greedy(inst.n, inst.src, inst.dst)
+    sizes = np.bincount(col, minlength=C)
+    B = {1: 4, 2: 3, 4: 2}[K]
+    rems = sizes % (B * threads)
+    assert (rems > 0).any() and (rems <= threads).any() and (rems > (B - 1) * threads).any()
+    env = {"COSM_K": str(K), "COSM_THREADS": str(threads)}
+    out = []
+    for split in (False, True):
+        os.environ.update(env)
+        if split:
+            os.environ["COSM_SPLIT_W"] = "1"
+        try:
+            s, g = _solver(cosm, orc, inst, use_dims=False, color=col, C=C, dwt_ratio=1.0)
+            R = 2 * K + 1
+            x0 = np.stack([orc.init_phases(inst.n, 6, r) for r in range(R)])
+            s.set_state(x0, seed=6)
+            alpha = float(np.float32(orc.alpha(3, 1000, A14)))
+            s.step(3, alpha)
+            x1 = s.get_state()
+            assert s.layout()["K"] == K and s.layout()["threads"] == threads
+            for r in range(R):
+                err, _ = one_sweep_error(orc, g, x0[r], x1[r], alpha, 3, seed=6, replica=r, **_params_kw(s))
+                assert err <= TOL_F32, (r, err)
+            s.run(201, R, seed=9)
+            out.append((x1, s.get_state(), s.replica_cuts()[0]))
+        finally:
+            for k in list(env) + ["COSM_SPLIT_W"]:
+                os.environ.pop(k, None)
+    for a, b in zip(out[0], out[1]):
+        assert np.array_equal(a, b)
+
+
 def test_edge_cases(cosm, orc):
     # single edge, odd n, one replica, one bisector, weights up to 127
     s = cosm.Solver(3, [0], [2], [127], n_bisectors=1)
