@@ -1700,152 +1700,206 @@ __device__ __forceinline__ void block_pass_odd_h2(H *xs, const uint8_t *wnib, fl
 }
 
 // ---------------------------------------------------------------- fixed point sweep
-// Eq. (6) on the 2^-16-turn grid: with phases held as q << 16, d = x_i - x_j
+// Eq. (6) on the 2^-16-turn grid: with a phase held as q << 16, d = x_i - x_j
 // read as int32 is the minimum angular difference (times 2^32) and the
-// biased sign of eq. (4) is d >= 0 (d = -2^31, exactly opposite, gives -1).
-// ap = (alpha quanta x w) << 16; every operation is exact.
-template <int K>
-__device__ __forceinline__ void pair_q(uint32_t (&xi)[K], uint32_t (&xj)[K], uint32_t ap)
+// biased sign of eq. (4) is d >= 0 (d = -2^31, exactly opposite, gives -1);
+// the step is (alpha quanta x w) << 16 and every operation is exact. The
+// dual window twist moves a phase iff ((q << 16) + c) mod 2^31 < QW, with
+// c = QW/2 - q_theta per replica (2^-32 turn).
+
+// Fixed-point phases stay packed in the sweeps below: a 32-bit word holds
+// the u16 phases of replicas 2h (low half) and 2h + 1 (high half) of a
+// slot, and add.u16x2 adds per half modulo 2^16, which is the grid's
+// circle arithmetic -- the same values as the q << 16 form, without
+// widening and packing each phase. Per half, x_j + ~x_i =
+// ~(x_i - x_j), whose sign bit is the complement of the sign bit that
+// decides eq. (4) (ties and the exactly-opposite value included), and prmt
+// replicates each half's sign bit over the half.
+__device__ __forceinline__ uint32_t add_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("add.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t half_signs(uint32_t v)
+{
+    uint32_t m;
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(m) : "r"(v));
+    return m;
+}
+// The low 16 bits of v in both halves.
+__device__ __forceinline__ uint32_t both_halves(uint32_t v) { return __byte_perm(v, 0u, 0x1010); }
+
+// Eq. (6) on NW packed words of x_i and x_j: pw is the step alpha w (grid
+// quanta) in both halves, nw its negation; x_i gains pw where x_i - x_j >= 0
+// and nw elsewhere, x_j the opposite.
+template <int NW>
+__device__ __forceinline__ void pair_qw(uint32_t (&xi)[NW], uint32_t (&xj)[NW], uint32_t pw, uint32_t nw)
 {
 #pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const uint32_t st = ((int32_t)(xi[r] - xj[r]) >= 0) ? ap : 0u - ap;
-        xi[r] += st;
-        xj[r] -= st;
+    for (int h = 0; h < NW; ++h) {
+        const uint32_t ge = half_signs(add_u16x2(xj[h], ~xi[h]));
+        xi[h] = add_u16x2(xi[h], (pw & ge) | (nw & ~ge));
+        xj[h] = add_u16x2(xj[h], (nw & ge) | (pw & ~ge));
     }
 }
 
-// Dual window twist on the grid: inside iff ((q - q_theta + QW/2) mod 2^31)
-// < QW; c = QW/2 - q_theta per replica.
-template <int K>
-__device__ __forceinline__ void dwt_q(uint32_t (&x)[K], const uint32_t *c, uint32_t qw, const uint32_t (&sq)[K])
+// The dual window twist on a packed word. With c = ch 2^16 + cl
+// (cl < 2^16), ((q << 16) + c) mod 2^31 = ((q + ch) mod 2^15) 2^16 + cl, so
+// the test against QW is (q + ch) mod 2^15 < T with T = ceil((QW - cl) /
+// 2^16) (0 when QW <= cl): per half, the sign of (q + ch) mod 2^15 - T.
+// chw, ntw (= -T), sqw: ch, -T and the step of the word's two replicas.
+__device__ __forceinline__ void dwt_qw(uint32_t &x, uint32_t chw, uint32_t ntw, uint32_t sqw)
 {
-#pragma unroll
-    for (int r = 0; r < K; ++r)
-        if (((x[r] + c[r]) & 0x7FFFFFFFu) < qw) x[r] += sq[r];
+    const uint32_t y = add_u16x2(x, chw) & 0x7FFF7FFFu;
+    x = add_u16x2(x, sqw & half_signs(add_u16x2(y, ntw)));
 }
 
-template <int K>
-__device__ __forceinline__ void general_colour_q(const InstView &a, uint16_t *xs, int c, uint32_t aq)
+// chw, ntw, sqw of the words of a tile from the per-replica c (QW/2 minus
+// the window centre, 2^-32 turn), QW and the steps sq (q << 16 form).
+template <int NW>
+__device__ __forceinline__ void dwt_qw_consts(const uint32_t *c, uint32_t qw, const uint32_t *sq, uint32_t (&chw)[NW],
+                                              uint32_t (&ntw)[NW], uint32_t (&sqw)[NW])
 {
+#pragma unroll
+    for (int h = 0; h < NW; ++h) {
+        uint32_t nt[2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const uint32_t cl = c[2 * h + k] & 0xFFFFu;
+            const uint32_t T = qw > cl ? (qw - cl + 0xFFFFu) >> 16 : 0u;
+            nt[k] = (0u - T) & 0xFFFFu;
+        }
+        chw[h] = __byte_perm(c[2 * h], c[2 * h + 1], 0x7632);
+        ntw[h] = nt[0] | (nt[1] << 16);
+        sqw[h] = __byte_perm(sq[2 * h], sq[2 * h + 1], 0x7632);
+    }
+}
+
+// NW packed words of a slot at a 32-bit shared address.
+template <int NW>
+__device__ __forceinline__ void lds_w(uint32_t a, uint32_t (&x)[NW])
+{
+    if constexpr (NW == 1) {
+        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(x[0]) : "r"(a) : "memory");
+    } else if constexpr (NW == 2) {
+        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(x[0]), "=r"(x[1]) : "r"(a) : "memory");
+    } else {
+        static_assert(NW == 4, "NW");
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(x[0]), "=r"(x[1]), "=r"(x[2]), "=r"(x[3]) : "r"(a) : "memory");
+    }
+}
+template <int NW>
+__device__ __forceinline__ void sts_w(uint32_t a, const uint32_t (&x)[NW])
+{
+    if constexpr (NW == 1) {
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(x[0]) : "memory");
+    } else if constexpr (NW == 2) {
+        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(x[0]), "r"(x[1]) : "memory");
+    } else {
+        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(x[0]), "r"(x[1]), "r"(x[2]),
+                     "r"(x[3]) : "memory");
+    }
+}
+
+// One colour of the edge-list sweep on packed words.
+template <int K>
+__device__ __forceinline__ void general_colour_qw(const InstView &a, uint16_t *xs, int c, uint32_t aq)
+{
+    constexpr int NW = K / 2;
+    constexpr uint32_t E = K * 2;  // bytes per slot
     const int tid = threadIdx.x, nt = blockDim.x;
+    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
     const int e1 = __ldg(a.off + c + 1);
     constexpr int kBatch = edge_batch<K>();
     for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += kBatch * nt) {
-        uint32_t rec[kBatch], ap[kBatch];
+        uint32_t ai[kBatch], aj[kBatch], pw[kBatch];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             const int e = e0 + u * nt;
-            rec[u] = e < e1 ? load_rec(a, e) : 0u;
-            ap[u] = e < e1 ? (uint32_t)((int32_t)aq * (int32_t)__ldg(a.w + e)) << 16 : 0u;
+            const uint32_t rec = e < e1 ? load_rec(a, e) : 0u;
+            const int32_t w = e < e1 ? (int32_t)__ldg(a.w + e) : 0;
+            ai[u] = xb + (rec & 0xFFFFu) * E;
+            aj[u] = xb + (rec >> 16) * E;
+            pw[u] = (uint32_t)((int32_t)aq * w);
         }
-        uint32_t xi[kBatch][K], xj[kBatch][K];
+        uint32_t xi[kBatch][NW], xj[kBatch][NW];
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             if (e0 + u * nt < e1) {
-                ldq<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
-                ldq<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+                lds_w<NW>(ai[u], xi[u]);
+                lds_w<NW>(aj[u], xj[u]);
+            } else {
+#pragma unroll
+                for (int h = 0; h < NW; ++h) xi[u][h] = xj[u][h] = 0u;
             }
         }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) pair_q<K>(xi[u], xj[u], ap[u]);
+        for (int u = 0; u < kBatch; ++u) pair_qw<NW>(xi[u], xj[u], both_halves(pw[u]), both_halves(0u - pw[u]));
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
             if (e0 + u * nt < e1) {
-                stq<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
-                stq<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
+                sts_w<NW>(ai[u], xi[u]);
+                sts_w<NW>(aj[u], xj[u]);
             }
         }
     }
 }
 
-__device__ __forceinline__ uint32_t signed_q(uint32_t wb, uint32_t bit, uint32_t ap)
-{
-    return (wb & bit) ? 0u - ap : ap;
-}
-
-// Fixed-point phases at a 32-bit shared address (two u16 phases per word).
+// The lattice passes of the fixed-point sweep on packed words (the 2x2
+// blocks of block_pass_even / block_pass_odd). pw, nw: alpha quanta and
+// their negation in both halves; a set weight bit (w = -1) swaps them.
 template <int K>
-__device__ __forceinline__ void lds_q(uint32_t a, uint32_t (&x)[K])
+__device__ __forceinline__ void block_pass_even_qw(uint16_t *xs, const uint8_t *wnib, uint32_t pw, uint32_t nw, int Q)
 {
-    if constexpr (K == 2) {
-        uint32_t w;
-        asm volatile("ld.shared.b32 %0, [%1];" : "=r"(w) : "r"(a) : "memory");
-        x[0] = w << 16; x[1] = w & 0xFFFF0000u;
-    } else if constexpr (K == 4) {
-        uint32_t w0, w1;
-        asm volatile("ld.shared.v2.b32 {%0, %1}, [%2];" : "=r"(w0), "=r"(w1) : "r"(a) : "memory");
-        x[0] = w0 << 16; x[1] = w0 & 0xFFFF0000u;
-        x[2] = w1 << 16; x[3] = w1 & 0xFFFF0000u;
-    } else {
-        static_assert(K == 8, "K");
-        uint32_t w[4];
-        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                     : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]) : "r"(a) : "memory");
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            x[2 * i] = w[i] << 16;
-            x[2 * i + 1] = w[i] & 0xFFFF0000u;
-        }
-    }
-}
-template <int K>
-__device__ __forceinline__ void sts_q(uint32_t a, const uint32_t (&x)[K])
-{
-    if constexpr (K == 2) {
-        asm volatile("st.shared.b32 [%0], %1;" ::"r"(a), "r"(pack_q(x[0], x[1])) : "memory");
-    } else if constexpr (K == 4) {
-        asm volatile("st.shared.v2.b32 [%0], {%1, %2};" ::"r"(a), "r"(pack_q(x[0], x[1])),
-                     "r"(pack_q(x[2], x[3])) : "memory");
-    } else {
-        asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(a), "r"(pack_q(x[0], x[1])),
-                     "r"(pack_q(x[2], x[3])), "r"(pack_q(x[4], x[5])), "r"(pack_q(x[6], x[7])) : "memory");
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void block_pass_even_q(uint16_t *xs, const uint8_t *wnib, uint32_t ap, int Q)
-{
+    constexpr int NW = K / 2;
     constexpr uint32_t E = K * 2;  // bytes per slot
     const uint32_t qb = (uint32_t)Q * E, qb2 = 2 * qb, qb3 = 3 * qb, step = blockDim.x * E;
     uint32_t ad = (uint32_t)__cvta_generic_to_shared(xs) + threadIdx.x * E;
     for (int f = threadIdx.x; f < Q; f += blockDim.x, ad += step) {
         const uint32_t wb = __ldg(wnib + f);
-        uint32_t xa[K], xb[K], xc[K], xd[K];
-        lds_q<K>(ad, xa);
-        lds_q<K>(ad + qb, xb);
-        lds_q<K>(ad + qb2, xc);
-        lds_q<K>(ad + qb3, xd);
-        pair_q<K>(xa, xb, signed_q(wb, 1u, ap));
-        pair_q<K>(xc, xd, signed_q(wb, 2u, ap));
-        pair_q<K>(xa, xc, signed_q(wb, 4u, ap));
-        pair_q<K>(xb, xd, signed_q(wb, 8u, ap));
-        sts_q<K>(ad, xa);
-        sts_q<K>(ad + qb, xb);
-        sts_q<K>(ad + qb2, xc);
-        sts_q<K>(ad + qb3, xd);
+        uint32_t xa[NW], xb[NW], xc[NW], xd[NW];
+        lds_w<NW>(ad, xa);
+        lds_w<NW>(ad + qb, xb);
+        lds_w<NW>(ad + qb2, xc);
+        lds_w<NW>(ad + qb3, xd);
+        pair_qw<NW>(xa, xb, (wb & 1u) ? nw : pw, (wb & 1u) ? pw : nw);
+        pair_qw<NW>(xc, xd, (wb & 2u) ? nw : pw, (wb & 2u) ? pw : nw);
+        pair_qw<NW>(xa, xc, (wb & 4u) ? nw : pw, (wb & 4u) ? pw : nw);
+        pair_qw<NW>(xb, xd, (wb & 8u) ? nw : pw, (wb & 8u) ? pw : nw);
+        sts_w<NW>(ad, xa);
+        sts_w<NW>(ad + qb, xb);
+        sts_w<NW>(ad + qb2, xc);
+        sts_w<NW>(ad + qb3, xd);
     }
 }
 
 // In the shifted blocks the second slot holds the smaller original id at a
 // torus wrap; the roles of eq. (6) then swap exactly (the exactly-opposite
 // tie is an integer value on the grid, so no shortcut is taken).
-template <int K>
-__device__ __forceinline__ void pair_q_oriented(uint32_t (&x1)[K], uint32_t (&x2)[K], uint32_t ap, bool swp)
+template <int NW>
+__device__ __forceinline__ void pair_qw_oriented(uint32_t (&x1)[NW], uint32_t (&x2)[NW], uint32_t pw, uint32_t nw,
+                                                 bool swp)
 {
-    if (swp) pair_q<K>(x2, x1, ap);
-    else pair_q<K>(x1, x2, ap);
+    if (swp) pair_qw<NW>(x2, x1, pw, nw);
+    else pair_qw<NW>(x1, x2, pw, nw);
 }
 
 template <int K, bool kFixedColumn>
-__device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wnib, uint32_t ap, int Q, int Wd,
-                                                 int m0, int dm, bool dwt, const uint32_t *c, uint32_t qw,
-                                                 const uint32_t *sqs)
+__device__ __forceinline__ void block_pass_odd_qw(uint16_t *xs, const uint8_t *wnib, uint32_t pw, uint32_t nw, int Q,
+                                                  int Wd, int m0, int dm, bool dwt, const uint32_t *c, uint32_t qw,
+                                                  const uint32_t *sqs)
 {
+    constexpr int NW = K / 2;
     constexpr uint32_t E = K * 2;  // bytes per slot
-    uint32_t sq[K];  // the twist step of each replica
+    uint32_t chw[NW], ntw[NW], sqw[NW];  // the twist's constants per word (steps 0 off the DWT sweeps)
+    if (dwt) {
+        dwt_qw_consts<NW>(c, qw, sqs, chw, ntw, sqw);
+    } else {
 #pragma unroll
-    for (int r = 0; r < K; ++r) sq[r] = dwt ? sqs[r] : 0u;
+        for (int h = 0; h < NW; ++h) chw[h] = ntw[h] = sqw[h] = 0u;
+    }
     // byte offsets from D[f] to C[g], B[h], A[gh] (g: next column, h: next row)
     const uint32_t qb = (uint32_t)Q * E, wdb = (uint32_t)Wd * E, rowwrap = (uint32_t)(Wd - Q) * E;
     const uint32_t step = blockDim.x * E;
@@ -1866,25 +1920,28 @@ __device__ __forceinline__ void block_pass_odd_q(uint16_t *xs, const uint8_t *wn
         const uint32_t hoffb = rw ? rowwrap : wdb;
         const uint32_t aC = ad - qb + goffb, aB = ad - 2 * qb + hoffb, aA = ad - 3 * qb + goffb + hoffb;
         const uint32_t wb = __ldg(wnib + Q + f);
-        uint32_t xd[K], xc[K], xb[K], xa[K];
-        lds_q<K>(ad, xd);
-        lds_q<K>(aC, xc);
-        lds_q<K>(aB, xb);
-        lds_q<K>(aA, xa);
-        pair_q_oriented<K>(xd, xc, signed_q(wb, 1u, ap), cw);
-        pair_q_oriented<K>(xb, xa, signed_q(wb, 2u, ap), cw);
-        pair_q_oriented<K>(xd, xb, signed_q(wb, 4u, ap), rw);
-        pair_q_oriented<K>(xc, xa, signed_q(wb, 8u, ap), rw);
+        uint32_t xd[NW], xc[NW], xb[NW], xa[NW];
+        lds_w<NW>(ad, xd);
+        lds_w<NW>(aC, xc);
+        lds_w<NW>(aB, xb);
+        lds_w<NW>(aA, xa);
+        pair_qw_oriented<NW>(xd, xc, (wb & 1u) ? nw : pw, (wb & 1u) ? pw : nw, cw);
+        pair_qw_oriented<NW>(xb, xa, (wb & 2u) ? nw : pw, (wb & 2u) ? pw : nw, cw);
+        pair_qw_oriented<NW>(xd, xb, (wb & 4u) ? nw : pw, (wb & 4u) ? pw : nw, rw);
+        pair_qw_oriented<NW>(xc, xa, (wb & 8u) ? nw : pw, (wb & 8u) ? pw : nw, rw);
         if (dwt) {
-            dwt_q<K>(xd, c, qw, sq);
-            dwt_q<K>(xc, c, qw, sq);
-            dwt_q<K>(xb, c, qw, sq);
-            dwt_q<K>(xa, c, qw, sq);
+#pragma unroll
+            for (int h = 0; h < NW; ++h) {
+                dwt_qw(xd[h], chw[h], ntw[h], sqw[h]);
+                dwt_qw(xc[h], chw[h], ntw[h], sqw[h]);
+                dwt_qw(xb[h], chw[h], ntw[h], sqw[h]);
+                dwt_qw(xa[h], chw[h], ntw[h], sqw[h]);
+            }
         }
-        sts_q<K>(ad, xd);
-        sts_q<K>(aC, xc);
-        sts_q<K>(aB, xb);
-        sts_q<K>(aA, xa);
+        sts_w<NW>(ad, xd);
+        sts_w<NW>(aC, xc);
+        sts_w<NW>(aB, xb);
+        sts_w<NW>(aA, xa);
     }
 }
 
@@ -1967,17 +2024,18 @@ __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment
             sqs[tid] = (randdir && neg) ? 0u - stepq : stepq;
         }
         if (kMode == MODE_LATTICE2D) {
-            block_pass_even_q<K>(t.xs, v.wnib, aq << 16, v.Q);
+            const uint32_t pw = both_halves(aq), nw = both_halves(0u - aq);
+            block_pass_even_qw<K>(t.xs, v.wnib, pw, nw, v.Q);
             __syncthreads();
             if (dm == 0)
-                block_pass_odd_q<K, true>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
+                block_pass_odd_qw<K, true>(t.xs, v.wnib, pw, nw, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
             else
-                block_pass_odd_q<K, false>(t.xs, v.wnib, aq << 16, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
+                block_pass_odd_qw<K, false>(t.xs, v.wnib, pw, nw, v.Q, v.Wd, m0, dm, dwt, cq, v.qwin, sqs);
             __syncthreads();
         } else {
             if (kMode == MODE_GENERAL) {
                 for (int c = 0; c < v.C; ++c) {
-                    general_colour_q<K>(v, t.xs, c, aq);
+                    general_colour_qw<K>(v, t.xs, c, aq);
                     __syncthreads();
                 }
                 if (v.hv) {
@@ -2023,14 +2081,16 @@ __device__ __forceinline__ void run_segment_q16(const InstView &v, const Segment
             }
             if (dwt) {
                 if (v.C == 0) __syncthreads();
-                uint32_t sq[K];
-#pragma unroll
-                for (int r = 0; r < K; ++r) sq[r] = sqs[r];
+                constexpr int NW = K / 2;
+                uint32_t chw[NW], ntw[NW], sqw[NW];
+                dwt_qw_consts<NW>(cq, v.qwin, sqs, chw, ntw, sqw);
+                const uint32_t xb = (uint32_t)__cvta_generic_to_shared(t.xs);
                 for (int u = tid; u < n; u += nt) {
-                    uint32_t x[K];
-                    ldq<K>(t.xs + (size_t)u * K, x);
-                    dwt_q<K>(x, cq, v.qwin, sq);
-                    stq<K>(t.xs + (size_t)u * K, x);
+                    uint32_t x[NW];
+                    lds_w<NW>(xb + (uint32_t)u * (K * 2), x);
+#pragma unroll
+                    for (int h = 0; h < NW; ++h) dwt_qw(x[h], chw[h], ntw[h], sqw[h]);
+                    sts_w<NW>(xb + (uint32_t)u * (K * 2), x);
                 }
                 __syncthreads();
             }

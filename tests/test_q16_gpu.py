@@ -91,3 +91,51 @@ def test_q16_batch_and_layouts_bit_exact(cosm, orc):
                 assert np.array_equal(s.get_state(), b.get_state(i))
             finally:
                 del os.environ["COSM_K"]
+
+
+@pytest.mark.parametrize("K", [2, 4, 8])
+@pytest.mark.parametrize("name", ["torus_rect_lattice", "torus16_lattice", "gnm_w3"])
+def test_whole_trials_bit_exact_per_tile_width(cosm, orc, K, name):
+    # the fixed-point passes keep two replicas per 32-bit word: tiles of 2, 4
+    # and 8 replicas hold 1, 2 and 4 words per slot; each against the oracle
+    import os
+    _, make, dims, ratio = next(c for c in CASES if c[0] == name)
+    inst = make()
+    col, C = orc.color_instance(inst)
+    os.environ["COSM_K"] = str(K)
+    try:
+        s = cosm.Solver.from_instance(inst, color=col, n_colors=C, use_dims=dims, storage=cosm.Q16,
+                                      dwt_ratio=ratio)
+        S, R, seed = 120, 2 * K + 1, 17
+        s.run(S, R, seed)
+    finally:
+        del os.environ["COSM_K"]
+    assert s.layout()["K"] == K and (s.layout()["lattice"] == 2) == dims
+    x = s.get_state()
+    cuts, bps = s.replica_cuts()
+    g = orc.ColouredGraph(inst.n, inst.src, inst.dst, inst.w, col, C)
+    for r in range(R):
+        best, xo, _, bp = orc.trial(g, S, alpha0=A14, dwt_ratio=ratio, seed=seed, replica=r,
+                                    storage=orc.STORE_Q16)
+        assert np.array_equal(x[r], xo), (name, K, r)
+        assert cuts[r] == best and bps[r] == bp
+
+
+def test_full_size_fixed_point_sampled(cosm, orc):
+    # the 20k-spin torus in u16 fixed point at the forms' launch configuration
+    # (four replicas per CTA, 1,024 replicas): sampled replicas' whole trials
+    # bit-exact with the oracle's
+    inst = instances.torus2d(100, 200, 0)
+    col, C = orc.color_instance(inst)
+    s = cosm.Solver.from_instance(inst, color=col, n_colors=C, storage=cosm.Q16, dwt_ratio=0.5)
+    S, seed = 45, 23
+    s.run(S, 1024, seed)
+    assert s.layout()["lattice"] == 2 and s.layout()["K"] == 4
+    x = s.get_state()
+    cuts, bps = s.replica_cuts()
+    g = orc.ColouredGraph(inst.n, inst.src, inst.dst, inst.w, col, C)
+    for r in (0, 3, 514, 1023):
+        best, xo, _, bp = orc.trial(g, S, alpha0=A14, dwt_ratio=0.5, seed=seed, replica=r,
+                                    storage=orc.STORE_Q16)
+        assert np.array_equal(x[r], xo), r
+        assert cuts[r] == best and bps[r] == bp
