@@ -1803,47 +1803,77 @@ __device__ __forceinline__ void sts_w(uint32_t a, const uint32_t (&x)[NW])
     }
 }
 
-// One colour of the edge-list sweep on packed words.
+// One batch of B edges per thread of the edge-list sweep on packed words
+// (edges e0, e0 + nt, ...); kTail: the batch may run past the end e1 of its
+// colour (its loads and stores skipped there); kSgn: the records of a.ijs,
+// whose bit 0 is the sign of a +-1 weight (no weight load).
+template <int NW, int B, bool kTail, bool kSgn>
+__device__ __forceinline__ void edge_batch_qw(const InstView &a, uint32_t xb, uint32_t aq, int e0, int e1, int nt)
+{
+    constexpr uint32_t E = NW * 4;  // bytes per slot
+    uint32_t ai[B], aj[B], pw[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int e = e0 + u * nt;
+        uint32_t rec = 0u;
+        int32_t w = 0;
+        if (!kTail || e < e1) {
+            if constexpr (kSgn) {
+                rec = load_rec_sgn(a, e);
+            } else {
+                rec = load_rec(a, e);
+                w = (int32_t)__ldg(a.w + e);
+            }
+        }
+        aj[u] = xb + (rec >> 16) * E;
+        if constexpr (kSgn) {
+            ai[u] = xb + (rec & 0xFFFEu) * (E / 2);
+            pw[u] = (rec & 1u) ? 0u - aq : aq;
+        } else {
+            ai[u] = xb + (rec & 0xFFFFu) * E;
+            pw[u] = (uint32_t)((int32_t)aq * w);
+        }
+    }
+    uint32_t xi[B][NW], xj[B][NW];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        if (!kTail || e0 + u * nt < e1) {
+            lds_w<NW>(ai[u], xi[u]);
+            lds_w<NW>(aj[u], xj[u]);
+        } else {
+#pragma unroll
+            for (int h = 0; h < NW; ++h) xi[u][h] = xj[u][h] = 0u;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) pair_qw<NW>(xi[u], xj[u], both_halves(pw[u]), both_halves(0u - pw[u]));
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        if (!kTail || e0 + u * nt < e1) {
+            sts_w<NW>(ai[u], xi[u]);
+            sts_w<NW>(aj[u], xj[u]);
+        }
+    }
+}
+
+// One colour of the edge-list sweep on packed words: whole batches without
+// bounds checks, then at most one checked batch per thread.
 template <int K>
 __device__ __forceinline__ void general_colour_qw(const InstView &a, uint16_t *xs, int c, uint32_t aq)
 {
-    constexpr int NW = K / 2;
-    constexpr uint32_t E = K * 2;  // bytes per slot
-    const int tid = threadIdx.x, nt = blockDim.x;
+    // 3 edges per thread for tiles of 2 or 4 replicas, 2 for tiles of 8, so
+    // that 1,024 threads fit the 64-register cap
+    constexpr int NW = K / 2, B = K == 8 ? 2 : 3;
+    const int nt = blockDim.x;
     const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
     const int e1 = __ldg(a.off + c + 1);
-    constexpr int kBatch = edge_batch<K>();
-    for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += kBatch * nt) {
-        uint32_t ai[kBatch], aj[kBatch], pw[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int e = e0 + u * nt;
-            const uint32_t rec = e < e1 ? load_rec(a, e) : 0u;
-            const int32_t w = e < e1 ? (int32_t)__ldg(a.w + e) : 0;
-            ai[u] = xb + (rec & 0xFFFFu) * E;
-            aj[u] = xb + (rec >> 16) * E;
-            pw[u] = (uint32_t)((int32_t)aq * w);
-        }
-        uint32_t xi[kBatch][NW], xj[kBatch][NW];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            if (e0 + u * nt < e1) {
-                lds_w<NW>(ai[u], xi[u]);
-                lds_w<NW>(aj[u], xj[u]);
-            } else {
-#pragma unroll
-                for (int h = 0; h < NW; ++h) xi[u][h] = xj[u][h] = 0u;
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) pair_qw<NW>(xi[u], xj[u], both_halves(pw[u]), both_halves(0u - pw[u]));
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            if (e0 + u * nt < e1) {
-                sts_w<NW>(ai[u], xi[u]);
-                sts_w<NW>(aj[u], xj[u]);
-            }
-        }
+    int e0 = __ldg(a.off + c) + threadIdx.x;
+    if (a.ijs) {
+        for (; e0 + (B - 1) * nt < e1; e0 += B * nt) edge_batch_qw<NW, B, false, true>(a, xb, aq, e0, e1, nt);
+        if (e0 < e1) edge_batch_qw<NW, B, true, true>(a, xb, aq, e0, e1, nt);
+    } else {
+        for (; e0 + (B - 1) * nt < e1; e0 += B * nt) edge_batch_qw<NW, B, false, false>(a, xb, aq, e0, e1, nt);
+        if (e0 < e1) edge_batch_qw<NW, B, true, false>(a, xb, aq, e0, e1, nt);
     }
 }
 
@@ -2337,14 +2367,16 @@ __device__ __forceinline__ void run_segment(const InstView &v, const Segment &sg
 // ---------------------------------------------------------------- sweep kernel
 // One instance: CTA b runs its segment list (one whole trial per tile, or
 // the head / tail pieces of the wrap-around schedule).
-// Lattice tiles of up to 4 replicas, and binary32 edge-list tiles of two or
-// four replicas, may take 1024 threads (one CTA per SM holds a large tile; more
+// Lattice tiles of up to 4 replicas, binary32 edge-list tiles of two or four
+// replicas and fixed-point edge-list tiles may take 1024 threads (one CTA per SM holds a large tile; more
 // warps hide the dependency and record-load latency) within 64 registers;
 // the others use at most 512 threads and up to 128 registers.
 template <typename Store, int K, int kMode>
 constexpr int max_threads()
 {
-    return ((kMode == MODE_LATTICE2D && K <= 4) || (kMode == MODE_GENERAL && (K == 2 || K == 4) && sizeof(Store) == 4))
+    return ((kMode == MODE_LATTICE2D && K <= 4) ||
+            (kMode == MODE_GENERAL && (K == 2 || K == 4) && sizeof(Store) == 4) ||
+            (kMode == MODE_GENERAL && std::is_same<Store, uint16_t>::value))
                ? 1024
                : 512;
 }
