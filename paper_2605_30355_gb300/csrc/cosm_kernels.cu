@@ -288,23 +288,11 @@ __host__ __device__ constexpr size_t smem_bytes(int n, int P, bool accum)
 // exactly for |c d| < 2^22, and its last bit is the parity of floor(c d):
 // one instruction for the whole decision, exact at the ties d = k / 2 too.
 // c = -2 evaluates the sign of -d (the other orientation of the pair).
+// Eq. (6) with J = -w is then, with s = sgn_b(x_i - x_j):
+//   x_i <- x_i + alpha w s; x_j <- x_j - alpha w s (wrapped to [-1/2, 1/2]).
 __device__ __forceinline__ uint32_t floor_parity(float c, float d)
 {
     return __float_as_uint(__fmaf_rd(c, d, 12582912.0f)) & 1u;
-}
-
-// Eq. (6) with J = -w: d = x_i - x_j; s = sgn_b(d);
-//   x_i <- wrap(x_i + alpha w s); x_j <- wrap(x_j - alpha w s)
-template <int K>
-__device__ __forceinline__ void pair_update(float (&xi)[K], float (&xj)[K], float aw)
-{
-#pragma unroll
-    for (int r = 0; r < K; ++r) {
-        const float d = __fadd_rn(xi[r], -xj[r]);
-        const float st = floor_parity(2.0f, d) ? -aw : aw;
-        xi[r] = wrap_c(__fadd_rn(xi[r], st));
-        xj[r] = wrap_c(__fadd_rn(xj[r], -st));
-    }
 }
 
 // ---------------------------------------------------------------- DWT
@@ -606,128 +594,13 @@ __device__ void seg_end(const InstView &a, const Segment &sg, const Tile<Store, 
 // General graphs: colour c's edge records [off[c], off[c+1]) map to threads;
 // each thread takes a batch of edges at a time (edges of one colour share no
 // vertex, so all loads of a batch may precede its stores), which keeps
-// several edge-record loads in flight: 8 for tiles of 2 or 4 replicas (a
-// large tile per SM, registers to spare), 4 for single-replica tiles (many
-// small CTAs per SM, where registers bound occupancy) and for 8-replica
-// tiles (whose per-edge state would not fit in registers).
-template <int K>
-__host__ __device__ constexpr int edge_batch() { return (K == 2 || K == 4) ? 8 : 4; }
-
+// several edge-record loads in flight (the batch sizes are given with each
+// edge-list sweep below).
 // An int8 weight as a float without the conversion unit: the bits of
 // 1.5 * 2^23 + w, minus 1.5 * 2^23 (exact for |w| < 2^22).
 __device__ __forceinline__ float weight_f(int8_t w)
 {
     return __fadd_rn(__int_as_float(0x4B400000 + (int)w), -12582912.0f);
-}
-
-template <typename Store, int K>
-__device__ __forceinline__ void general_colour(const InstView &a, Store *xs, int c, float alpha)
-{
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int e1 = __ldg(a.off + c + 1);
-    constexpr int kBatch = edge_batch<K>();
-    for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += kBatch * nt) {
-        uint32_t rec[kBatch];
-        float aw[kBatch];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            const int e = e0 + u * nt;
-            rec[u] = e < e1 ? load_rec(a, e) : 0u;
-            aw[u] = e < e1 ? alpha * weight_f(__ldg(a.w + e)) : 0.0f;
-        }
-        float xi[kBatch][K], xj[kBatch][K];
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            if (e0 + u * nt < e1) {
-                ldk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
-                ldk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) pair_update<K>(xi[u], xj[u], aw[u]);
-#pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-            if (e0 + u * nt < e1) {
-                stk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
-                stk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
-            }
-        }
-    }
-}
-
-// The colours of one sweep with the edge records of each thread's next
-// batch loaded while the current batch is processed, across colour
-// boundaries and into the next sweep too (records do not depend on the
-// phases), so their L2 latency overlaps the shared-memory work. pf carries
-// the prefetched batch between sweeps; pf.e0 names its first edge (-1: none).
-template <int B>
-struct EdgePrefetch {
-    uint32_t rec[B];
-    int32_t w[B];
-    int e0;
-};
-
-template <int B>
-__device__ __forceinline__ void fetch_edges(const InstView &a, int e0, int e1, uint32_t (&rec)[B],
-                                            int32_t (&w)[B])
-{
-    const int nt = blockDim.x;
-#pragma unroll
-    for (int u = 0; u < B; ++u) {
-        const int e = e0 + u * nt;
-        rec[u] = e < e1 ? load_rec(a, e) : 0u;
-        w[u] = e < e1 ? (int32_t)__ldg(a.w + e) : 0;
-    }
-}
-
-template <typename Store, int K, int B>
-__device__ __forceinline__ void general_colours_pf(const InstView &a, Store *xs, float alpha, EdgePrefetch<B> &pf)
-{
-    const int tid = threadIdx.x, nt = blockDim.x, step = B * nt;
-    for (int c = 0; c < a.C; ++c) {
-        const int e1 = __ldg(a.off + c + 1);
-        for (int e0 = __ldg(a.off + c) + tid; e0 < e1; e0 += step) {
-            uint32_t rec[B];
-            int32_t wv[B];
-            if (pf.e0 == e0) {
-#pragma unroll
-                for (int u = 0; u < B; ++u) {
-                    rec[u] = pf.rec[u];
-                    wv[u] = pf.w[u];
-                }
-            } else {
-                fetch_edges<B>(a, e0, e1, rec, wv);
-            }
-            // the next batch: further in this colour, else the first batch
-            // of the next colour (of colour 0 for the next sweep)
-            int n0 = e0 + step, n1 = e1;
-            if (n0 >= e1) {
-                const int nc = (c + 1 < a.C) ? c + 1 : 0;
-                n0 = __ldg(a.off + nc) + tid;
-                n1 = __ldg(a.off + nc + 1);
-            }
-            fetch_edges<B>(a, n0, n1, pf.rec, pf.w);
-            pf.e0 = n0;
-            float xi[B][K], xj[B][K];
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-                if (e0 + u * nt < e1) {
-                    ldk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
-                    ldk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < B; ++u) pair_update<K>(xi[u], xj[u], alpha * weight_f((int8_t)wv[u]));
-#pragma unroll
-            for (int u = 0; u < B; ++u) {
-                if (e0 + u * nt < e1) {
-                    stk<K>(xs + (size_t)(rec[u] & 0xFFFFu) * K, xi[u]);
-                    stk<K>(xs + (size_t)(rec[u] >> 16) * K, xj[u]);
-                }
-            }
-        }
-        __syncthreads();
-    }
 }
 
 // Pair update inside a 2x2 block. x1, x2 are the block's slots; eq. (6)
@@ -1699,6 +1572,82 @@ __device__ __forceinline__ void block_pass_odd_h2(H *xs, const uint8_t *wnib, fl
     }
 }
 
+// 16-bit storage (binary16, bfloat16) on edge lists: one batch of B edges
+// per thread, each slot's NW words widened to f32x2 pairs (two replicas a
+// pair), eq. (6) as in the binary32 sweep, and every updated phase wrapped
+// and rounded to the storage type when stored -- after every update, as
+// the oracle's per-update rounding for edge lists has it. kTail and kSgn as
+// in edge_batch_x2.
+template <typename H, int NW, int B, bool kTail, bool kSgn>
+__device__ __forceinline__ void edge_batch_h2(const InstView &a, uint32_t xb, float alpha, int e0, int e1, int nt)
+{
+    constexpr uint32_t E = NW * 4;  // bytes per slot
+    uint32_t ai[B], aj[B];
+    float aw[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const int e = e0 + u * nt;
+        uint32_t rec = 0;
+        int w = 0;
+        if (!kTail || e < e1) {
+            if constexpr (kSgn) {
+                rec = load_rec_sgn(a, e);
+            } else {
+                rec = load_rec(a, e);
+                w = __ldg(a.w + e);
+            }
+        }
+        aj[u] = xb + (rec >> 16) * E;
+        if constexpr (kSgn) {
+            ai[u] = xb + (rec & 0xFFFEu) * (E / 2);
+            aw[u] = __uint_as_float(flip_if_odd(__float_as_uint(alpha), rec));
+        } else {
+            ai[u] = xb + (rec & 0xFFFFu) * E;
+            aw[u] = alpha * weight_f((int8_t)w);
+        }
+    }
+    f32x2 xi[B][NW], xj[B][NW];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        lds_h<H, NW>(ai[u], xi[u]);
+        lds_h<H, NW>(aj[u], xj[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        const f32x2 aw2 = p_pack(aw[u], aw[u]);
+#pragma unroll
+        for (int h = 0; h < NW; ++h) {
+            pair_x2<kAlu16<H>()>(xi[u][h], xj[u][h], aw2, kTwo2);
+            xi[u][h] = p_wrap(xi[u][h]);
+            xj[u][h] = p_wrap(xj[u][h]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+        if (!kTail || e0 + u * nt < e1) {
+            sts_h<H, NW>(ai[u], xi[u]);
+            sts_h<H, NW>(aj[u], xj[u]);
+        }
+    }
+}
+
+// The colours of one sweep of a 16-bit edge-list tile: whole batches
+// without bounds checks, then at most one checked batch per thread.
+template <typename H, int K, bool kSgn>
+__device__ __forceinline__ void general_colours_h2(const InstView &a, H *xs, float alpha)
+{
+    constexpr int NW = K / 2, B = K == 8 ? 2 : 3;
+    const int nt = blockDim.x;
+    const uint32_t xb = (uint32_t)__cvta_generic_to_shared(xs);
+    for (int c = 0; c < a.C; ++c) {
+        const int e1 = __ldg(a.off + c + 1);
+        int e0 = __ldg(a.off + c) + threadIdx.x;
+        for (; e0 + (B - 1) * nt < e1; e0 += B * nt) edge_batch_h2<H, NW, B, false, kSgn>(a, xb, alpha, e0, e1, nt);
+        if (e0 < e1) edge_batch_h2<H, NW, B, true, kSgn>(a, xb, alpha, e0, e1, nt);
+        __syncthreads();
+    }
+}
+
 // ---------------------------------------------------------------- fixed point sweep
 // Eq. (6) on the 2^-16-turn grid: with a phase held as q << 16, d = x_i - x_j
 // read as int32 is the minimum angular difference (times 2^32) and the
@@ -2153,8 +2102,6 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
     if (!seg_begin<Store, K>(v, sg, t, s_skip, ready, err, wait_limit_ns)) return;
     const uint32_t rep0 = (uint32_t)sg.tile * K;
     int phase = dwt_on ? (int)(sg.s_begin % v.dwt_period) : 1;
-    EdgePrefetch<4> pf;
-    pf.e0 = -1;
     int stage_cur = 0;  // staged edge records: the buffer holding colour 0
     for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
         const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));
@@ -2243,10 +2190,9 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
             }
         } else {
             if (kMode == MODE_GENERAL) {
-                // sequential conflict-free search: colours in order (eq. (11));
-                // tiles of 2 or 4 replicas prefetch their next edge batch,
-                // single- and 8-replica tiles keep registers for occupancy
-                if constexpr (sizeof(Store) == 4 && (K == 1 || K == 2 || K == 4)) {
+                // sequential conflict-free search: colours in order (eq. (11))
+                if constexpr (sizeof(Store) == 4) {
+                    static_assert(K == 1 || K == 2 || K == 4, "binary32 tiles hold 1, 2 or 4 replicas");
                     // binary32: f32x2 lanes (replica pairs, or edge pairs for
                     // single-replica tiles); batches of 3 edges for tiles of
                     // two replicas (4 and 5 were 1-5 % slower: the last,
@@ -2269,13 +2215,10 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
                     } else {
                         general_colours_x2<K, kB, false>(v, xf, at.x);
                     }
-                } else if constexpr (K == 2 || K == 4) {
-                    general_colours_pf<Store, K, 4>(v, t.xs, at.x, pf);
                 } else {
-                    for (int c = 0; c < v.C; ++c) {
-                        general_colour<Store, K>(v, t.xs, c, at.x);
-                        __syncthreads();
-                    }
+                    // 16-bit storage: f32x2 lanes over the replica pairs of a word
+                    if (v.ijs) general_colours_h2<Store, K, true>(v, t.xs, at.x);
+                    else general_colours_h2<Store, K, false>(v, t.xs, at.x);
                 }
                 if (v.hv) {
                     field_pass<Store, K>(v, t.xs, at.x);
@@ -2367,8 +2310,8 @@ __device__ __forceinline__ void run_segment(const InstView &v, const Segment &sg
 // ---------------------------------------------------------------- sweep kernel
 // One instance: CTA b runs its segment list (one whole trial per tile, or
 // the head / tail pieces of the wrap-around schedule).
-// Lattice tiles of up to 4 replicas, binary32 edge-list tiles of two or four
-// replicas and fixed-point edge-list tiles may take 1024 threads (one CTA per SM holds a large tile; more
+// Lattice tiles of up to 4 replicas, edge-list tiles of two or four replicas
+// and fixed-point edge-list tiles of eight may take 1024 threads (one CTA per SM holds a large tile; more
 // warps hide the dependency and record-load latency) within 64 registers;
 // the others use at most 512 threads and up to 128 registers.
 template <typename Store, int K, int kMode>
@@ -2376,7 +2319,8 @@ constexpr int max_threads()
 {
     return ((kMode == MODE_LATTICE2D && K <= 4) ||
             (kMode == MODE_GENERAL && (K == 2 || K == 4) && sizeof(Store) == 4) ||
-            (kMode == MODE_GENERAL && std::is_same<Store, uint16_t>::value))
+            (kMode == MODE_GENERAL && std::is_same<Store, uint16_t>::value) ||
+            (kMode == MODE_GENERAL && sizeof(Store) == 2 && (K == 2 || K == 4)))
                ? 1024
                : 512;
 }

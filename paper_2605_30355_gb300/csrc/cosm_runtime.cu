@@ -513,9 +513,9 @@ int cosm::choose_layout(cosm_handle *h, int replicas, bool narrow_ties)
             if (cand[1] == cand[0]) cand[1] = 0;
         } else {
             cand[0] = std::min(512, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
-            // binary32 tiles of two or four replicas and fixed-point tiles
+            // tiles of two or four replicas (and fixed-point tiles of eight)
             // may also take 1,024 threads
-            if (mode == MODE_GENERAL_ && ((p.storage == COSM_F32 && (K == 2 || K == 4)) || p.storage == COSM_Q16))
+            if (mode == MODE_GENERAL_ && (K == 2 || K == 4 || p.storage == COSM_Q16))
                 cand[1] = std::min(1024, std::max(64, ((max_ec + 1) / 2 + 31) / 32 * 32));
             if (cand[1] == cand[0]) cand[1] = 0;
         }
