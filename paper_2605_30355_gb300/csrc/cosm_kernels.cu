@@ -2102,15 +2102,13 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
     if (!seg_begin<Store, K>(v, sg, t, s_skip, ready, err, wait_limit_ns)) return;
     const uint32_t rep0 = (uint32_t)sg.tile * K;
     int phase = dwt_on ? (int)(sg.s_begin % v.dwt_period) : 1;
-    // s mod wrap_p, counted along the sweeps (no 64-bit division per sweep)
-    int wphase = v.wrap_p > 0 ? (int)(sg.s_begin % v.wrap_p) : 0;
     int stage_cur = 0;  // staged edge records: the buffer holding colour 0
     for (int64_t s = sg.s_begin; s <= sg.s_end; ++s) {
         const float2 at = __ldg(v.alpha_tab + (s - v.alpha_base));
         const bool dwt = dwt_on && phase == 0;
         // binary32 lattice phases are wrapped on every wrap_p-th sweep of the
         // trial (16-bit storage: every sweep)
-        const bool wrap = sizeof(Store) == 2 || v.wrap_p <= 1 || wphase == 0;
+        const bool wrap = sizeof(Store) == 2 || v.wrap_p <= 1 || (s % v.wrap_p) == 0;
         if (dwt && tid < K) {
             bool neg = false;
             const float c = 2.0f * (hw - dwt_theta(v.seed, rep0 + tid, s, &neg));
@@ -2268,7 +2266,7 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
             // wrap_p-th sweep, or with every twist when each update is
             // wrapped) in one pass of f32x2 words
             constexpr bool kGenF32 = kMode == MODE_GENERAL && sizeof(Store) == 4 && K <= 4;
-            const bool wrap_sweep = kGenF32 && (v.wrap_p == 0 ? dwt : wphase == 0);
+            const bool wrap_sweep = kGenF32 && (v.wrap_p == 0 ? dwt : (s % v.wrap_p) == 0);
             if (kGenF32 && (dwt || wrap_sweep)) {
                 if constexpr (kGenF32) {
                     if (v.C == 0) __syncthreads();
@@ -2294,7 +2292,6 @@ __device__ __forceinline__ void run_segment_fp(const InstView &v, const Segment 
         }
         if (readout_due(v, s)) tile_readout<Store, K>(v, sg.tile, t, (int)((s - 1) / v.track), true);
         if (dwt_on && ++phase == v.dwt_period) phase = 0;
-        if (v.wrap_p > 0 && ++wphase == v.wrap_p) wphase = 0;
     }
     seg_end<Store, K>(v, sg, t, ready);
 }
