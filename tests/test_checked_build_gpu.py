@@ -74,6 +74,8 @@ def _cases(cosm):
         ("edges_f32_k4", single(gnm, 150, 8, 17, env={"COSM_K": "4"}, dwt_ratio=1.0)),
         ("edges_signed_k2", single(reg3, 150, 8, 25, env={"COSM_K": "2"}, dwt_ratio=1.0)),
         ("edges_signed_k1", single(reg3, 150, 7, 26, env={"COSM_K": "1"}, dwt_ratio=1.0)),
+        ("edges_signed_f16", single(reg3, 150, 8, 27, storage=cosm.F16, dwt_ratio=1.0)),
+        ("edges_signed_q16", single(reg3, 150, 8, 28, storage=cosm.Q16, dwt_ratio=1.0)),
         ("edges_f16", single(gnm, 150, 8, 18, storage=cosm.F16, dwt_ratio=1.0)),
         ("edges_q16", single(gnm, 150, 8, 19, storage=cosm.Q16, dwt_ratio=1.0)),
         ("no_scs_f32", single(gnm, 100, 6, 20, flags=cosm.NO_SCS, dwt_ratio=1.0)),

@@ -401,6 +401,32 @@ def test_edge_list_tails_and_signed_records(cosm, orc, K, threads, wmax):
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("storage", [1, 2, 3])
+@pytest.mark.parametrize("K", [2, 4, 8])
+def test_signed_records_equal_split_16bit(cosm, orc, storage, K):
+    # binary16, fixed point and bfloat16 edge lists read the records carrying
+    # a +-1 weight's sign too: whole trials equal those with split records
+    # and weights bit for bit, at every tile width and with checked batches
+    # of every fill (96 threads against colours of every size)
+    inst = instances.sparse_gnm(700, 2100, 5, wmax=1)
+    col, C = orc.color_greedy(inst.n, inst.src, inst.dst)
+    env = {"COSM_K": str(K), "COSM_THREADS": "96"}
+    out = []
+    for split in (False, True):
+        os.environ.update(env)
+        if split:
+            os.environ["COSM_SPLIT_W"] = "1"
+        try:
+            s, _ = _solver(cosm, orc, inst, storage=storage, use_dims=False, color=col, C=C, dwt_ratio=1.0)
+            s.run(201, 2 * K + 1, seed=9)
+            assert s.layout()["K"] == K and s.layout()["threads"] == 96
+            out.append((s.get_state(), s.replica_cuts()[0]))
+        finally:
+            for k in list(env) + ["COSM_SPLIT_W"]:
+                os.environ.pop(k, None)
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
 def test_edge_cases(cosm, orc):
     # single edge, odd n, one replica, one bisector, weights up to 127
     s = cosm.Solver(3, [0], [2], [127], n_bisectors=1)
