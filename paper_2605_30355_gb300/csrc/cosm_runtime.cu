@@ -640,6 +640,7 @@ InstView cosm::inst_view(cosm_handle *h)
     v.off = h->d_off.p;
     v.ij = h->d_ij.p;
     v.w = h->d_w.p;
+    // test hook: COSM_SPLIT_W keeps the split records and weights
     v.ijs = std::getenv("COSM_SPLIT_W") ? nullptr : h->d_ijs.p;
     v.orig_of = h->d_orig.p;
     v.wnib = h->d_wnib.p;
