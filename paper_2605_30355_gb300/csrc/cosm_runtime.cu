@@ -497,9 +497,10 @@ int cosm::choose_layout(cosm_handle *h, int replicas, bool narrow_ties)
         const size_t smem = sweep_smem_bytes(p.storage, K, h->g.n, P, mode);
         if (smem > 227 * 1024) continue;
         // thread counts to try: edge-list kernels half a colour class's edges
-        // (at most 512, or 1,024 for binary32 tiles of two or four replicas); lattice
-        // kernels the 2x2 blocks of a sublattice, up to 512 or, for tiles of
-        // at most 4 replicas, 1024 threads
+        // (at most 512, or 1,024 for tiles of two or four replicas and for
+        // fixed-point tiles of eight); lattice kernels the 2x2 blocks of a
+        // sublattice, up to 512 or, for tiles of at most 4 replicas, 1024
+        // threads
         int cand[2] = {0, 0};
         if (forceT) {
             cand[0] = forceT;
